@@ -1,0 +1,652 @@
+/*
+ * vc_oracle.c -- plain FP64 CPU oracle for value iteration on the vehicular-cloud
+ * task-placement MDP (arxiv 2012.12419, Section V, Eq. 18 and Algorithm 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the CUDA
+ * path is checked against.  Only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark may load it.  It shares no code, header, table or helper with the
+ * CUDA library: it enumerates every successor with nested loops, merges duplicates
+ * by linear search and runs plain Jacobi sweeps, all in double precision.
+ *
+ * Model (Section V-A..V-G; the paper leaves the concrete instance open, so the
+ * readings below are the ones this project fixes and lists in its design notes):
+ *   state  s = ph + 2*(q + (Q+1)*sum_k occ_k*(C+1)^k)            (Eq. 10, mixed radix)
+ *          ph = 1 in the service-channel interval (SCHI), 0 in CCHI
+ *   action a in 0..H-1 places the head task on host a, a = H defers (Eq. 11 widened)
+ *          placement feasible iff q >= 1, occ_a < C and (a == H-1 (the RSU) or ph == 1)
+ *   post-decision state x: occ_a + 1, q - 1 for a placement; x = s for defer
+ *   one uniformised event fires from x (Eq. 12-13 read as a CTMC), all rates / Lam,
+ *          Lam = lambda + C*sum(mu) + sum(delta) + 1:
+ *          completion on host k   rate mu_k*occ_k     -> occ_k - 1
+ *          departure of host k    rate delta_k        -> occ_k = 0 (its tasks are lost)
+ *          arrival                rate lambda         -> q + 1, or blocked (lost) if q == Q
+ *          phase flip             rate f (CCHI->SCHI), 1-f (SCHI->CCHI)
+ *          self-loop              the remaining probability
+ *   reward R(s,a) = w_occ*sum occ(x) + w_q*q(x)
+ *                 + w_loss*(sum_k delta_k*occ_k(x)/Lam + [q(x)==Q]*lambda/Lam)   (Eq. 14-16 replaced)
+ *   Bellman      V(s) = max_{a feasible} [ R(s,a) + gamma * sum_s' P(s'|s,a) V(s') ]  (Eq. 18,
+ *                max taken over actions, expected reward, discount gamma)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXH 16
+#define OR_MAXSUCC (2 * OR_MAXH + 4)
+#define OR_NTHETA (2 * OR_MAXH + 5)
+
+typedef struct {
+    int32_t H, C, Q, pad_;
+    double lambda, f, gamma, w_occ, w_loss, w_q;
+    double mu[OR_MAXH];
+    double delta[OR_MAXH];
+} or_params;
+
+/* ---------------------------------------------------------------- state codes */
+
+int64_t or_num_states(const or_params* p) {
+    int64_t n = 2 * (int64_t)(p->Q + 1);
+    for (int k = 0; k < p->H; k++) n *= (p->C + 1);
+    return n;
+}
+
+static void decode(const or_params* p, int64_t s, int* occ, int* q, int* ph) {
+    *ph = (int)(s % 2);
+    int64_t rest = s / 2;
+    *q = (int)(rest % (p->Q + 1));
+    rest = rest / (p->Q + 1);
+    for (int k = 0; k < p->H; k++) {
+        occ[k] = (int)(rest % (p->C + 1));
+        rest = rest / (p->C + 1);
+    }
+}
+
+static int64_t encode(const or_params* p, const int* occ, int q, int ph) {
+    int64_t code = 0;
+    for (int k = p->H - 1; k >= 0; k--) code = code * (p->C + 1) + occ[k];
+    return ph + 2 * (q + (int64_t)(p->Q + 1) * code);
+}
+
+void or_decode(const or_params* p, int64_t s, int32_t* occ, int32_t* q, int32_t* ph) {
+    int o[OR_MAXH], qq, pp;
+    decode(p, s, o, &qq, &pp);
+    for (int k = 0; k < p->H; k++) occ[k] = o[k];
+    *q = qq;
+    *ph = pp;
+}
+
+int64_t or_encode(const or_params* p, const int32_t* occ, int32_t q, int32_t ph) {
+    int o[OR_MAXH];
+    for (int k = 0; k < p->H; k++) o[k] = occ[k];
+    return encode(p, o, q, ph);
+}
+
+double or_uniformisation(const or_params* p) {
+    double sum_mu = 0.0, sum_delta = 0.0;
+    for (int k = 0; k < p->H; k++) {
+        sum_mu += p->mu[k];
+        sum_delta += p->delta[k];
+    }
+    return p->lambda + p->C * sum_mu + sum_delta + 1.0;
+}
+
+/* Is action a allowed in state s?  (placement rule and defer, see header) */
+int or_feasible(const or_params* p, int64_t s, int a) {
+    int occ[OR_MAXH], q, ph;
+    if (a < 0 || a > p->H) return 0;
+    if (a == p->H) return 1;
+    decode(p, s, occ, &q, &ph);
+    if (q < 1) return 0;
+    if (occ[a] >= p->C) return 0;
+    if (a != p->H - 1 && ph != 1) return 0;
+    return 1;
+}
+
+/* Adds probability pr for target t into a small merged list (linear search). */
+static void add_succ(int64_t* cols, double* probs, int* n, int64_t t, double pr) {
+    for (int i = 0; i < *n; i++) {
+        if (cols[i] == t) {
+            probs[i] += pr;
+            return;
+        }
+    }
+    cols[*n] = t;
+    probs[*n] = pr;
+    (*n)++;
+}
+
+/* Sorts the merged list by target index (insertion sort; lists are tiny). */
+static void sort_succ(int64_t* cols, double* probs, int n) {
+    for (int i = 1; i < n; i++) {
+        int64_t c = cols[i];
+        double v = probs[i];
+        int j = i - 1;
+        while (j >= 0 && cols[j] > c) {
+            cols[j + 1] = cols[j];
+            probs[j + 1] = probs[j];
+            j--;
+        }
+        cols[j + 1] = c;
+        probs[j + 1] = v;
+    }
+}
+
+/*
+ * Transition row of (s, a): merged successor list sorted by target, zero-probability
+ * entries dropped, plus the expected one-step reward.  Returns the number of
+ * successors, or -1 if a is not feasible in s.
+ */
+int or_transitions(const or_params* p, int64_t s, int a, int64_t* cols, double* probs, double* R) {
+    int occ[OR_MAXH] = {0}, q = 0, ph = 0;
+    if (!or_feasible(p, s, a)) return -1;
+    decode(p, s, occ, &q, &ph);
+    /* post-decision state */
+    if (a < p->H) {
+        occ[a] += 1;
+        q -= 1;
+    }
+    const int64_t x = encode(p, occ, q, ph);
+    const double Lam = or_uniformisation(p);
+
+    int64_t ec[OR_MAXSUCC];
+    double ep[OR_MAXSUCC];
+    int ne = 0;
+    double total = 0.0;
+    for (int k = 0; k < p->H; k++) {
+        /* completion on host k */
+        if (occ[k] > 0) {
+            int o2[OR_MAXH];
+            memcpy(o2, occ, sizeof(int) * p->H);
+            o2[k] -= 1;
+            ec[ne] = encode(p, o2, q, ph);
+            ep[ne] = p->mu[k] * occ[k] / Lam;
+            total += ep[ne];
+            ne++;
+        }
+        /* departure of host k: empties it */
+        {
+            int o2[OR_MAXH];
+            memcpy(o2, occ, sizeof(int) * p->H);
+            o2[k] = 0;
+            ec[ne] = encode(p, o2, q, ph);
+            ep[ne] = p->delta[k] / Lam;
+            total += ep[ne];
+            ne++;
+        }
+    }
+    /* arrival: joins the queue, or is blocked (self-transition) when it is full */
+    ec[ne] = (q < p->Q) ? encode(p, occ, q + 1, ph) : x;
+    ep[ne] = p->lambda / Lam;
+    total += ep[ne];
+    ne++;
+    /* phase flip */
+    ec[ne] = encode(p, occ, q, 1 - ph);
+    ep[ne] = (ph == 0 ? p->f : 1.0 - p->f) / Lam;
+    total += ep[ne];
+    ne++;
+    /* self-loop: what is left */
+    ec[ne] = x;
+    ep[ne] = 1.0 - total;
+    ne++;
+
+    int n = 0;
+    for (int e = 0; e < ne; e++) add_succ(cols, probs, &n, ec[e], ep[e]);
+    /* drop exact zeros */
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        if (probs[i] != 0.0) {
+            cols[m] = cols[i];
+            probs[m] = probs[i];
+            m++;
+        }
+    }
+    sort_succ(cols, probs, m);
+
+    double occ_sum = 0.0, lost = 0.0;
+    for (int k = 0; k < p->H; k++) {
+        occ_sum += occ[k];
+        lost += p->delta[k] * occ[k] / Lam;
+    }
+    if (q == p->Q) lost += p->lambda / Lam;
+    *R = p->w_occ * occ_sum + p->w_q * q + p->w_loss * lost;
+    return m;
+}
+
+/*
+ * Derivatives of one transition row with respect to
+ *   theta = (lambda, mu_0..mu_{H-1}, delta_0..delta_{H-1}, f, w_occ, w_loss, w_q),
+ * nt = 2H+5 entries.  dprobs is n x nt (row-major, aligned with the merged, sorted
+ * successor list that or_transitions returns for the same (s, a)); dR has nt entries.
+ * Each event probability is rate/Lam, so d(rate/Lam) = drate/Lam - rate*dLam/Lam^2;
+ * the self-loop takes minus the sum of the others.  Returns n, or -1 if infeasible.
+ */
+int or_transition_grads(const or_params* p, int64_t s, int a, int64_t* cols, double* dprobs, double* dR) {
+    int occ[OR_MAXH] = {0}, q = 0, ph = 0;
+    double probs_unused[OR_MAXSUCC], Rv;
+    const int H = p->H, nt = 2 * H + 5;
+    const int i_lam = 0, i_mu = 1, i_del = 1 + H, i_f = 1 + 2 * H;
+    const int i_wocc = 2 + 2 * H, i_wloss = 3 + 2 * H, i_wq = 4 + 2 * H;
+
+    int n = or_transitions(p, s, a, cols, probs_unused, &Rv);
+    if (n < 0) return -1;
+    decode(p, s, occ, &q, &ph);
+    if (a < H) {
+        occ[a] += 1;
+        q -= 1;
+    }
+    const int64_t x = encode(p, occ, q, ph);
+    const double Lam = or_uniformisation(p);
+    double dLam[OR_NTHETA];
+    for (int i = 0; i < nt; i++) dLam[i] = 0.0;
+    dLam[i_lam] = 1.0;
+    for (int k = 0; k < H; k++) {
+        dLam[i_mu + k] = p->C;
+        dLam[i_del + k] = 1.0;
+    }
+
+    /* unmerged events with rate and d(rate)/d(theta) */
+    int64_t ec[OR_MAXSUCC];
+    double er[OR_MAXSUCC];
+    double edr[OR_MAXSUCC][OR_NTHETA];
+    int ne = 0;
+    memset(edr, 0, sizeof(edr));
+    for (int k = 0; k < H; k++) {
+        if (occ[k] > 0) {
+            int o2[OR_MAXH];
+            memcpy(o2, occ, sizeof(int) * H);
+            o2[k] -= 1;
+            ec[ne] = encode(p, o2, q, ph);
+            er[ne] = p->mu[k] * occ[k];
+            edr[ne][i_mu + k] = occ[k];
+            ne++;
+        }
+        {
+            int o2[OR_MAXH];
+            memcpy(o2, occ, sizeof(int) * H);
+            o2[k] = 0;
+            ec[ne] = encode(p, o2, q, ph);
+            er[ne] = p->delta[k];
+            edr[ne][i_del + k] = 1.0;
+            ne++;
+        }
+    }
+    ec[ne] = (q < p->Q) ? encode(p, occ, q + 1, ph) : x;
+    er[ne] = p->lambda;
+    edr[ne][i_lam] = 1.0;
+    ne++;
+    ec[ne] = encode(p, occ, q, 1 - ph);
+    er[ne] = (ph == 0) ? p->f : 1.0 - p->f;
+    edr[ne][i_f] = (ph == 0) ? 1.0 : -1.0;
+    ne++;
+
+    for (int j = 0; j < n * nt; j++) dprobs[j] = 0.0;
+    double dself[OR_NTHETA];
+    for (int i = 0; i < nt; i++) dself[i] = 0.0;
+    for (int e = 0; e < ne; e++) {
+        int row = -1;
+        for (int j = 0; j < n; j++)
+            if (cols[j] == ec[e]) row = j;
+        for (int i = 0; i < nt; i++) {
+            double dp = edr[e][i] / Lam - er[e] * dLam[i] / (Lam * Lam);
+            dself[i] -= dp;
+            if (row >= 0) dprobs[row * nt + i] += dp;
+        }
+    }
+    {
+        int row = -1;
+        for (int j = 0; j < n; j++)
+            if (cols[j] == x) row = j;
+        if (row >= 0)
+            for (int i = 0; i < nt; i++) dprobs[row * nt + i] += dself[i];
+    }
+
+    /* reward derivatives */
+    double occ_sum = 0.0, Lnum = 0.0;
+    for (int k = 0; k < H; k++) {
+        occ_sum += occ[k];
+        Lnum += p->delta[k] * occ[k];
+    }
+    const int blocked = (q == p->Q);
+    if (blocked) Lnum += p->lambda;
+    for (int i = 0; i < nt; i++) dR[i] = 0.0;
+    dR[i_wocc] = occ_sum;
+    dR[i_wq] = q;
+    dR[i_wloss] = Lnum / Lam;
+    dR[i_lam] = p->w_loss * ((blocked ? 1.0 : 0.0) / Lam - Lnum / (Lam * Lam));
+    for (int k = 0; k < H; k++) {
+        dR[i_mu + k] = p->w_loss * (-Lnum * p->C / (Lam * Lam));
+        dR[i_del + k] = p->w_loss * (occ[k] / Lam - Lnum / (Lam * Lam));
+    }
+    dR[i_f] = 0.0;
+    return n;
+}
+
+/* ------------------------------------------------------------ explicit CSR form */
+
+/*
+ * Row r = s*A + a.  Canonical form (padded == 0): merged non-zero successors sorted by
+ * column; infeasible rows are empty with R = -inf.  Padded form: every row holds exactly
+ * 2H+3 entries: the successors, then probability-0 entries that repeat the row's last
+ * column (so columns stay sorted); an infeasible row holds 2H+3 zeros at column s.
+ * Returns nnz.  Pass NULL arrays to count only.
+ */
+int64_t or_build_csr(const or_params* p, int padded, int64_t* row_ptr, int32_t* col, double* val, double* R) {
+    const int64_t S = or_num_states(p);
+    const int A = p->H + 1;
+    const int width = 2 * p->H + 3;
+    int64_t nnz = 0;
+    int64_t cols[OR_MAXSUCC];
+    double probs[OR_MAXSUCC];
+    if (row_ptr) row_ptr[0] = 0;
+    for (int64_t s = 0; s < S; s++) {
+        for (int a = 0; a < A; a++) {
+            double Rv;
+            int n = or_transitions(p, s, a, cols, probs, &Rv);
+            int64_t r = s * A + a;
+            if (n < 0) {
+                if (R) R[r] = -INFINITY;
+                if (padded) {
+                    for (int j = 0; j < width; j++) {
+                        if (col) col[nnz + j] = (int32_t)s;
+                        if (val) val[nnz + j] = 0.0;
+                    }
+                    nnz += width;
+                }
+            } else {
+                if (R) R[r] = Rv;
+                for (int j = 0; j < n; j++) {
+                    if (col) col[nnz + j] = (int32_t)cols[j];
+                    if (val) val[nnz + j] = probs[j];
+                }
+                if (padded) {
+                    for (int j = n; j < width; j++) {
+                        if (col) col[nnz + j] = (int32_t)cols[n - 1];
+                        if (val) val[nnz + j] = 0.0;
+                    }
+                    nnz += width;
+                } else {
+                    nnz += n;
+                }
+            }
+            if (row_ptr) row_ptr[r + 1] = nnz;
+        }
+    }
+    return nnz;
+}
+
+/* ------------------------------------------------------------- value iteration */
+
+/* Q(s,a) = R(s,a) + gamma * sum_s' P(s'|s,a) V(s'); returns 0 and -inf if infeasible. */
+static int q_value(const or_params* p, const double* V, int64_t s, int a, double* out) {
+    int64_t cols[OR_MAXSUCC];
+    double probs[OR_MAXSUCC], Rv;
+    int n = or_transitions(p, s, a, cols, probs, &Rv);
+    if (n < 0) {
+        *out = -INFINITY;
+        return 0;
+    }
+    double acc = 0.0;
+    for (int j = 0; j < n; j++) acc += probs[j] * V[cols[j]];
+    *out = Rv + p->gamma * acc;
+    return 1;
+}
+
+/*
+ * One Bellman backup of state s from V (Algorithm 3, step 2).  best = max over feasible
+ * actions, arg = the lowest action attaining it, gap = best minus the second-largest
+ * Q value (+inf when only one action is feasible).
+ */
+void or_backup(const or_params* p, const double* V, int64_t s, double* best, int32_t* arg, double* gap) {
+    double b = -INFINITY, second = -INFINITY;
+    int ba = -1;
+    for (int a = 0; a <= p->H; a++) {
+        double qv;
+        if (!q_value(p, V, s, a, &qv)) continue;
+        if (qv > b) {
+            second = b;
+            b = qv;
+            ba = a;
+        } else if (qv > second) {
+            second = qv;
+        }
+    }
+    *best = b;
+    *arg = ba;
+    *gap = (second == -INFINITY) ? INFINITY : b - second;
+}
+
+/*
+ * Jacobi value iteration (Algorithm 3): V holds V^0 on entry (zeros for the paper's
+ * step 1) and the last iterate on exit.  Stops after the first sweep with
+ * max_s |V^{k+1}(s) - V^k(s)| < tol.  residuals (nullable, length max_sweeps) receives
+ * every sweep's residual.  Returns 0 on convergence, 1 if max_sweeps ran out.
+ */
+int or_value_iteration(const or_params* p, double tol, int64_t max_sweeps, double* V, int64_t* sweeps_out,
+                       double* residual_out, double* residuals) {
+    const int64_t S = or_num_states(p);
+    double* Vn = (double*)malloc(sizeof(double) * S);
+    int64_t k = 0;
+    double res = INFINITY;
+    int status = 1;
+    while (k < max_sweeps) {
+        res = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            double b, g;
+            int32_t a;
+            or_backup(p, V, s, &b, &a, &g);
+            Vn[s] = b;
+            double d = fabs(Vn[s] - V[s]);
+            if (d > res) res = d;
+        }
+        memcpy(V, Vn, sizeof(double) * S);
+        if (residuals) residuals[k] = res;
+        k++;
+        if (res < tol) {
+            status = 0;
+            break;
+        }
+    }
+    free(Vn);
+    *sweeps_out = k;
+    *residual_out = res;
+    return status;
+}
+
+/* Greedy policy of Algorithm 2 read on this MDP: place the head task on the feasible
+ * host with the largest service rate (lowest index on ties), else defer. */
+void or_greedy_policy(const or_params* p, int32_t* pi) {
+    const int64_t S = or_num_states(p);
+    for (int64_t s = 0; s < S; s++) {
+        int best = p->H;
+        double best_mu = -1.0;
+        for (int a = 0; a < p->H; a++) {
+            if (or_feasible(p, s, a) && p->mu[a] > best_mu) {
+                best_mu = p->mu[a];
+                best = a;
+            }
+        }
+        pi[s] = best;
+    }
+}
+
+/* Policy from V: pi(s) = argmax_a Q(s,a) (Algorithm 3, step 4), qgap as in or_backup. */
+void or_policy(const or_params* p, const double* V, int32_t* pi, double* qgap) {
+    const int64_t S = or_num_states(p);
+    for (int64_t s = 0; s < S; s++) {
+        double b, g;
+        int32_t a;
+        or_backup(p, V, s, &b, &a, &g);
+        pi[s] = a;
+        if (qgap) qgap[s] = g;
+    }
+}
+
+/*
+ * Policy evaluation by Jacobi iteration: V <- R_pi + gamma P_pi V until the sweep change
+ * is below tol.  Returns 0 on convergence, 1 if max_sweeps ran out, 2 if pi is not
+ * feasible somewhere.
+ */
+int or_policy_eval_iter(const or_params* p, const int32_t* pi, double tol, int64_t max_sweeps, double* V,
+                        int64_t* sweeps_out) {
+    const int64_t S = or_num_states(p);
+    double* Vn = (double*)malloc(sizeof(double) * S);
+    int64_t k = 0;
+    int status = 1;
+    while (k < max_sweeps) {
+        double res = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            double qv;
+            if (!q_value(p, V, s, pi[s], &qv)) {
+                free(Vn);
+                return 2;
+            }
+            Vn[s] = qv;
+            double d = fabs(Vn[s] - V[s]);
+            if (d > res) res = d;
+        }
+        memcpy(V, Vn, sizeof(double) * S);
+        k++;
+        if (res < tol) {
+            status = 0;
+            break;
+        }
+    }
+    free(Vn);
+    *sweeps_out = k;
+    return status;
+}
+
+/* ------------------------------------------------------- generic explicit MDP */
+
+/*
+ * Jacobi value iteration on an explicit CSR MDP with S states and A actions per state:
+ * row s*A+a spans [row_ptr[r], row_ptr[r+1]), R[r] = -inf marks an infeasible action.
+ * Same stopping rule as or_value_iteration.  pi / qgap (nullable) receive the argmax
+ * of the final backup.
+ */
+int or_vi_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const double* val,
+              const double* R, double gamma, double tol, int64_t max_sweeps, double* V, int64_t* sweeps_out,
+              double* residual_out) {
+    double* Vn = (double*)malloc(sizeof(double) * S);
+    int64_t k = 0;
+    double res = INFINITY;
+    int status = 1;
+    while (k < max_sweeps) {
+        res = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            double b = -INFINITY;
+            for (int a = 0; a < A; a++) {
+                int64_t r = s * A + a;
+                if (R[r] == -INFINITY) continue;
+                double acc = 0.0;
+                for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) acc += val[j] * V[col[j]];
+                double qv = R[r] + gamma * acc;
+                if (qv > b) b = qv;
+            }
+            Vn[s] = b;
+            double d = fabs(Vn[s] - V[s]);
+            if (d > res) res = d;
+        }
+        memcpy(V, Vn, sizeof(double) * S);
+        k++;
+        if (res < tol) {
+            status = 0;
+            break;
+        }
+    }
+    free(Vn);
+    *sweeps_out = k;
+    *residual_out = res;
+    return status;
+}
+
+void or_policy_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const double* val,
+                   const double* R, double gamma, const double* V, int32_t* pi, double* qgap) {
+    for (int64_t s = 0; s < S; s++) {
+        double b = -INFINITY, second = -INFINITY;
+        int ba = -1;
+        for (int a = 0; a < A; a++) {
+            int64_t r = s * A + a;
+            if (R[r] == -INFINITY) continue;
+            double acc = 0.0;
+            for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) acc += val[j] * V[col[j]];
+            double qv = R[r] + gamma * acc;
+            if (qv > b) {
+                second = b;
+                b = qv;
+                ba = a;
+            } else if (qv > second) {
+                second = qv;
+            }
+        }
+        pi[s] = ba;
+        if (qgap) qgap[s] = (second == -INFINITY) ? INFINITY : b - second;
+    }
+}
+
+/* ------------------------------------------------------------------- bfloat16 */
+
+/*
+ * Round a double to the nearest bfloat16 (8 exponent bits, 7 stored mantissa bits),
+ * ties to even, directly from the double's bits (no intermediate float rounding).
+ * Finite, non-negative inputs below the bf16 overflow threshold only (probabilities).
+ * Returns the 16-bit pattern.
+ */
+uint16_t or_bf16_rne(double x) {
+    if (x == 0.0) return 0;
+    /* exact decomposition x = m * 2^e with m in [1, 2) */
+    int e;
+    double m = frexp(x, &e); /* m in [0.5, 1) */
+    m *= 2.0;
+    e -= 1;
+    if (e < -126) {
+        /* bf16 subnormal: value = k * 2^-133, k in [0, 127] */
+        double k = ldexp(x, 133);
+        double kr = nearbyint(k); /* default rounding mode: ties to even */
+        return (uint16_t)kr;
+    }
+    /* normal: 7 fraction bits -> scale mantissa to [128, 256) and round */
+    double t = ldexp(m, 7);
+    double tr = nearbyint(t);
+    if (tr == 256.0) {
+        tr = 128.0;
+        e += 1;
+    }
+    uint32_t frac = (uint32_t)tr - 128u;
+    uint32_t bexp = (uint32_t)(e + 127);
+    return (uint16_t)((bexp << 7) | frac);
+}
+
+double or_bf16_to_double(uint16_t b) {
+    uint32_t exp = (b >> 7) & 0xFF;
+    uint32_t frac = b & 0x7F;
+    double sign = (b & 0x8000) ? -1.0 : 1.0;
+    if (exp == 0) return sign * ldexp((double)frac, -133);
+    return sign * ldexp(1.0 + frac / 128.0, (int)exp - 127);
+}
+
+/* Elementwise bf16 rounding of an array (bit patterns out). */
+void or_bf16_round_array(int64_t n, const double* x, uint16_t* bits) {
+    for (int64_t i = 0; i < n; i++) bits[i] = or_bf16_rne(x[i]);
+}
+
+/*
+ * The matrix the BF16 storage form actually solves: each stored entry is bf16(p) and each
+ * row is scaled by scale = 1 / sum_j bf16(p_j), the sum taken in FP64 in column order and
+ * the reciprocal rounded to FP32.  Writes the bit patterns, the effective FP64 values
+ * bf16(p_j) * scale and the FP32 scales (0 for an empty row).
+ */
+void or_bf16_renormalise_csr(int64_t nrows, const int64_t* row_ptr, const double* val, uint16_t* bits,
+                             double* val_out, float* scale_out) {
+    for (int64_t r = 0; r < nrows; r++) {
+        double tot = 0.0;
+        for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) {
+            bits[j] = or_bf16_rne(val[j]);
+            tot += or_bf16_to_double(bits[j]);
+        }
+        float sc = (tot > 0.0) ? (float)(1.0 / tot) : 0.0f;
+        scale_out[r] = sc;
+        for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) val_out[j] = or_bf16_to_double(bits[j]) * (double)sc;
+    }
+}
