@@ -1,0 +1,384 @@
+#!/usr/bin/env python3
+"""Benchmark: value iteration on the large vehicular-cloud placement MDP.
+
+One step = one solve of the resident instance from V = 0 to a certified 1e-6 residual
+(Algorithm 3): FP32 Jacobi Bellman sweeps with fused residual, argmax policy, FP64
+policy-evaluation refinement and the FP64 Bellman residual check.  The headline form is
+the explicit CSR with FP32 probabilities (the HBM-streaming sweep); the implicit
+register-generated form is timed beside it.
+
+value  = state-action-successor updates per second = logical nnz per sweep x FP32 sweeps
+         / step time (device events on the launching stream, L2 flushed between steps).
+e2e    = the same through the public API from host parameters to host results (build,
+         solve, copy of V64 and pi back), wall clock.
+roofline: the CSR sweep kernel, algorithmic bytes per launch / average launch time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "state-action-successor updates/s and time to 1e-6 residual; % of HBM roofline"
+UNIT = "updates/s"
+WORKLOAD_DESC = {
+    "large": "large single MDP: H=7 C=4 Q=15, S=2,500,000 states, A=8 actions, gamma=0.95",
+    "tiny": "tiny MDP: H=3 C=3 Q=4, S=640, A=4, gamma=0.95",
+    "precision": "precision MDP: H=8 C=4 Q=15, S=12,500,000, A=9, gamma=0.95",
+    "grad": "differentiation MDP: H=6 C=4 Q=10, S=343,750, A=7, gamma=0.95",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(WORKLOAD_DESC))
+    ap.add_argument("--form", default="csr_f32", choices=["csr_f32", "csr_bf16", "implicit"])
+    ap.add_argument("--padded", action="store_true")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and the variants")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- native arm
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2012_12419_gb300 import inputs, native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    native.load(build_if_missing=(rank == 0))
+    if world > 1:
+        dist.barrier()
+        native.load()
+
+    p = inputs.workload(args.workload)
+    t0 = time.perf_counter()
+    m = native.MDP.build(p, fmt=args.form, padded=args.padded)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    info = m.info()
+    S = int(info["S"])
+    nnz = int(info["nnz_logical"])
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    V = torch.zeros(S, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+
+    def step():
+        V.zero_()  # Algorithm 3, step 1
+        _, V64, pi, st = m.value_iterate(V, tol=args.tol)
+        return st
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = native.kernel_launches()
+    times, stats = [], []
+    region0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        stats.append(st)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    region_s = time.perf_counter() - region0
+    launches = native.kernel_launches() - launches0
+    ck = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in times]
+    total_ms = sum(ms)
+    sweeps = [s["sweeps"] for s in stats]
+    units = float(nnz) * float(sum(sweeps))
+    if world > 1:
+        t = torch.tensor([total_ms, units], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms_all, units_all = float(tmax[0]), float(t[1])
+        dist.barrier()
+    else:
+        total_ms_all, units_all = total_ms, units
+    value = units_all / (total_ms_all / 1e3)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD_DESC[args.workload], "form": args.form + ("+padded" if args.padded else ""),
+            "tol": args.tol, "nnz_logical_per_sweep": nnz, "nnz_stored_per_sweep": int(info["nnz_stored"]),
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "256 MiB buffer written between steps, outside the step events",
+            "step": "V=0 -> FP32 sweeps -> argmax -> FP64 policy evaluation -> FP64 Bellman certificate",
+        },
+        "time_to_residual_ms": statistics.median(ms),
+        "sweeps_per_step": statistics.median(sweeps),
+        "fp64_eval_sweeps_per_step": statistics.median([s["eval_sweeps"] for s in stats]),
+        "certified": all(s["certified"] == 1 for s in stats),
+        "residual64": max(s["residual64"] for s in stats),
+        "build_ms": build_ms,
+        "gpu_launches": int(launches),
+        "region_wall_s": region_s,
+        "clocks": ck,
+    }
+    if rank == 0:
+        out["roofline"] = roofline(m, info, args, V, dev, stream)
+        if not args.no_extras:
+            out["e2e"] = e2e(args, p, native, torch, nnz)
+            if world == 1:
+                out["cpu_baseline"] = cpu_baseline(p, args)
+            out["variants"] = variants(args, p, native, torch, dev, stream)
+        print(json.dumps(out))
+    m.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(m, info, args, V, dev, stream):
+    """Average launch time of the FP32 sweep kernel, timed with events on its stream."""
+    import torch
+
+    hbm, src = peaks()
+    A = torch.rand(info["S"], dtype=torch.float32, device=dev) * 50
+    B = torch.empty_like(A)
+    for _ in range(5):
+        m.bellman32(A, B, stream=stream)
+    n = 50
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n):
+        if i % 2 == 0:
+            m.bellman32(A, B, stream=stream)
+        else:
+            m.bellman32(B, A, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    avg_s = e0.elapsed_time(e1) / 1e3 / n
+    traffic = None
+    achieved = info["sweep_bytes"] / avg_s / 1e9
+    implicit = args.form == "implicit"
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_post+k_max" if implicit else "k_csr32",
+            "bytes_per_launch": int(info["sweep_bytes"]), "launch_us": avg_s * 1e6}
+
+
+def e2e(args, p, native, torch, nnz):
+    """Public API from host parameters to host results, every step: build (H2D of the
+    parameters), solve, D2H of V64 and pi into pinned buffers."""
+    reps = min(3, args.steps)
+    S = None
+    ms, sw, h2d, d2h = [], [], 0, 0
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = native.MDP.build(p, fmt=args.form, padded=args.padded)
+        V, V64, pi, st = m.value_iterate(tol=args.tol)
+        S = V64.numel()
+        hv = torch.empty(S, dtype=torch.float64, pin_memory=True)
+        hp = torch.empty(S, dtype=torch.int32, pin_memory=True)
+        hv.copy_(V64, non_blocking=True)
+        hp.copy_(pi, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        m.close()
+        ms.append((t1 - t0) * 1e3)
+        sw.append(st["sweeps"])
+    ms, sw = ms[1:], sw[1:]  # first call warms allocator and module
+    h2d = 8 * (2 * int(p["H"]) + 8)  # parameter struct and rate arrays
+    d2h = S * (8 + 4)
+    return {"value": nnz * sum(sw) / (sum(ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": statistics.median(ms)}
+
+
+def variants(args, p, native, torch, dev, stream):
+    """The other storage forms of the same workload, same step, device-timed."""
+    out = {}
+    forms = [("implicit", False), ("csr_f32", True), ("csr_bf16", False)]
+    for form, padded in forms:
+        if form == args.form and padded == args.padded:
+            continue
+        m = native.MDP.build(p, fmt=form, padded=padded)
+        info = m.info()
+        V = torch.zeros(info["S"], dtype=torch.float32, device=dev)
+        for _ in range(2):
+            V.zero_()
+            m.value_iterate(V, tol=args.tol)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        sweeps = 0
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            V.zero_()
+            _, _, _, st = m.value_iterate(V, tol=args.tol)
+            sweeps += st["sweeps"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        out[form + ("+padded" if padded else "")] = {
+            "time_to_residual_ms": t, "updates_per_s": info["nnz_logical"] * sweeps / reps / (t / 1e3),
+            "sweeps": sweeps // reps, "nnz_stored": int(info["nnz_stored"]),
+            "sweep_bytes": int(info["sweep_bytes"])}
+        m.close()
+    return out
+
+
+def cpu_baseline(p, args, min_seconds: float = 10.0):
+    """The FP64 oracle's Bellman sweeps over the same instance, single thread."""
+    import numpy as np
+
+    import oracle
+
+    S = oracle.num_states(p)
+    V = np.zeros(S)
+    Vn = np.zeros(S)
+    updates, sweeps = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < min_seconds and sweeps < 3:
+        updates += oracle.sweep_states(p, V, Vn, 0, S, 1)
+        V, Vn = Vn, V
+        sweeps += 1
+    dt = time.perf_counter() - t0
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} full Jacobi sweep(s) of the {args.workload} instance from V=0 "
+                      f"({updates} updates, {dt:.1f} s)"}
+
+
+# ------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    import numpy as np
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2012_12419_gb300 import inputs
+
+    p = inputs.workload(args.workload)
+    S = oracle.num_states(p)
+    V = np.zeros(S)
+    Vn = np.zeros(S)
+    stride = 16  # one step: backups of every 16th state (about 1/16 of a sweep)
+    for _ in range(max(3, args.warmup)):
+        oracle.sweep_states(p, V, Vn, 0, S, stride * 4)
+    ups, secs = 0, 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        ups += oracle.sweep_states(p, V, Vn, k % stride, S, stride)
+        secs += time.perf_counter() - t0
+    value = ups / secs
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "form": "oracle enumeration (FP64, single thread)",
+                   "tol": args.tol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: Jacobi backups of every {stride}th state of the instance"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

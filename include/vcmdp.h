@@ -1,0 +1,212 @@
+/*
+ * vcmdp.h -- C ABI of the GB300 value-iteration library for the vehicular-cloud
+ * task-placement MDP of arxiv 2012.12419 (Section V).
+ *
+ * The method: value iteration (Algorithm 3) on the Bellman equation (Eq. 18), read as
+ *     V(s) = max_{a feasible in s} [ R(s,a) + gamma * sum_s' P(s'|s,a) V(s') ],
+ * Jacobi sweeps from V = 0 (or a warm start) until max_s |V^{k+1}(s) - V^k(s)| < tol,
+ * then pi(s) = argmax_a (ties to the lowest action).
+ *
+ * The instance (Eq. 10-16 under the readings this library fixes):
+ *   state  s = ph + 2*(q + (Q+1)*sum_k occ_k*(C+1)^k), S = 2(Q+1)(C+1)^H   (Eq. 10)
+ *          occ_k in 0..C tasks on host k (hosts 0..H-2 vehicles, H-1 the RSU),
+ *          q in 0..Q queued tasks, ph = 1 in the service-channel interval (SCHI)
+ *   action a < H places the head task on host a (needs q >= 1, occ_a < C, and a == H-1
+ *          or ph == 1); a = H defers.  A = H+1.                             (Eq. 11)
+ *   one uniformised event then fires from the post-decision state, rates over
+ *          Lam = lambda + C*sum(mu) + sum(delta) + 1: completion mu_k*occ_k, departure
+ *          delta_k (host emptied, tasks lost), arrival lambda (blocked and lost when
+ *          q == Q), phase flip f (CCHI->SCHI) / 1-f (SCHI->CCHI), self-loop the rest.
+ *                                                                           (Eq. 12-13)
+ *   reward R = w_occ*sum occ + w_q*q + w_loss*(sum_k delta_k occ_k + [q==Q] lambda)/Lam,
+ *          all on the post-decision state.                                  (Eq. 14-16)
+ *
+ * Conventions for every entry point:
+ *   - Returns VC_OK (0) or a VC_ERR_* code; vc_last_error() then describes the failure
+ *     (thread-local string, valid until the next call on the same thread).
+ *   - Array arguments are DEVICE pointers unless the comment says host.  They are
+ *     borrowed for the duration of the call; the library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is enqueued
+ *     on it; calls that return statistics or a convergence verdict synchronise it.
+ *   - The library allocates device memory only inside handles it owns (vc_mdp,
+ *     vc_batch); vc_destroy / vc_batch_destroy release it.
+ *   - States are indexed with int32 (S < 2^31); CSR offsets are int64.
+ */
+#ifndef VCMDP_H
+#define VCMDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VC_MAX_HOSTS 16
+
+/* status codes */
+#define VC_OK 0
+#define VC_ERR_ARG 1                /* bad argument (size, pointer, range) */
+#define VC_ERR_NOT_STOCHASTIC 2     /* a CSR row does not sum to 1 or has a negative entry */
+#define VC_ERR_NO_FEASIBLE_ACTION 3 /* a state has no feasible action (R = -inf on all rows) */
+#define VC_ERR_NOT_CONVERGED 4      /* max_sweeps ran out before the tolerance was met */
+#define VC_ERR_TIMEOUT 5            /* a bounded device-side wait gave up */
+#define VC_ERR_OOM 6                /* device allocation failed */
+#define VC_ERR_CUDA 7               /* any other CUDA runtime error */
+
+/* storage formats for vc_build_mdp (one of the first three, optionally | VC_PADDED) */
+#define VC_IMPLICIT 0  /* successors generated in registers from the mixed-radix state code */
+#define VC_CSR_F32 1   /* explicit CSR, FP32 probabilities, int32 columns, int64 row offsets */
+#define VC_CSR_BF16 2  /* explicit CSR, BF16 probabilities + FP32 per-row renormalising scale */
+#define VC_PADDED 16   /* CSR rows padded to exactly 2H+3 entries, infeasible rows included */
+
+/* value types for vc_build_mdp_csr */
+#define VC_VAL_F32 0
+#define VC_VAL_BF16 1
+
+/* flags for vc_value_iterate */
+#define VC_ITER_FP32_ONLY 1  /* stop after the FP32 sweeps: no FP64 refinement / certificate */
+
+/* Model parameters (host struct; mu and delta are HOST arrays of length H). */
+typedef struct vc_params {
+    int32_t H, C, Q;      /* hosts, VM slots per host, queue capacity */
+    int32_t reserved;
+    double lambda;        /* task arrival rate */
+    double f;             /* SCHI fraction of the sync interval (stationary phase law) */
+    double gamma;         /* discount factor in (0, 1) */
+    double w_occ, w_loss, w_q; /* reward weights */
+    const double* mu;     /* host, [H] service rate per occupied slot */
+    const double* delta;  /* host, [H] departure rate of each host */
+} vc_params;
+
+/* Sizes of a built instance. */
+typedef struct vc_info {
+    int64_t S;              /* states */
+    int32_t A;              /* actions per state */
+    int32_t fmt;            /* VC_IMPLICIT / VC_CSR_F32 / VC_CSR_BF16 (| VC_PADDED) */
+    int64_t nnz_logical;    /* successor updates per sweep: non-zero entries of feasible rows */
+    int64_t nnz_stored;     /* CSR entries streamed per sweep (0 for VC_IMPLICIT) */
+    int64_t feasible_rows;  /* (s, a) pairs with a feasible */
+    int64_t device_bytes;   /* device memory owned by the handle */
+    int64_t sweep_bytes;    /* algorithmic HBM bytes of one FP32 sweep */
+    int32_t has_model;      /* 1 if built from vc_params (exact FP64 P available) */
+    int32_t reserved;
+} vc_info;
+
+/* Statistics of vc_value_iterate (host struct, filled on return). */
+typedef struct vc_stats {
+    int64_t sweeps;         /* FP32 Bellman sweeps performed */
+    double residual;        /* last FP32 residual max|V^{k+1}-V^k| */
+    int64_t eval_sweeps;    /* FP64 policy-evaluation sweeps */
+    int64_t bellman64;      /* FP64 full Bellman backups (certification checks) */
+    int32_t policy_rounds;  /* policy-improvement rounds inside the refinement */
+    int32_t certified;      /* 1 if residual64 < tol */
+    double residual64;      /* FP64 max|T V - V| of the returned V64 (Algorithm 3, step 3) */
+    double ms_fp32;         /* device time of the FP32 sweeps (ms) */
+    double ms_fp64;         /* device time of refinement + certification (ms) */
+} vc_stats;
+
+typedef struct vc_mdp vc_mdp;
+typedef struct vc_batch vc_batch;
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char* vc_last_error(void);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded (all threads). */
+int64_t vc_kernel_launches(void);
+
+/*
+ * Build an instance from model parameters (Eq. 10-16).  fmt selects the storage of the
+ * FP32/BF16 sweeps; VC_IMPLICIT stores nothing per transition.  CSR builds run a count,
+ * an exclusive scan and a fill kernel on `stream`.  Rows hold the merged non-zero
+ * successors sorted by column (VC_PADDED: exactly 2H+3 entries, zero-padded).  BF16
+ * entries are bf16(p) rounded to nearest even from the FP64 probability; each row
+ * carries scale = 1/sum_j bf16(p_j) (FP64 sum, rounded to FP32).  Every handle built
+ * here also keeps the FP64 model for refinement, certification and gradients.
+ * Errors: VC_ERR_ARG for H outside 1..16, C < 1, Q < 0, S >= 2^31, rates <= 0 (mu,
+ * lambda; delta >= 0), f outside (0,1), gamma outside (0,1); VC_ERR_OOM.
+ */
+int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out);
+
+/*
+ * Build an instance from an arbitrary explicit MDP in CSR form (device pointers, copied
+ * into the handle): row r = s*A + a spans [row_ptr[r], row_ptr[r+1]) of col/val; R[r]
+ * is its expected reward, -INFINITY marking an infeasible action.  val_dtype is
+ * VC_VAL_F32 (float) or VC_VAL_BF16 (uint16 bf16 bit patterns); row_scale (nullable,
+ * [S*A] float) multiplies a row's sum (BF16 only; NULL = 1/sum of the stored values).
+ * Validated on the device: columns in [0, S), entries >= 0, each feasible row summing
+ * to 1 within 1e-5 after scaling (VC_ERR_NOT_STOCHASTIC), each state with at least one
+ * feasible action (VC_ERR_NO_FEASIBLE_ACTION), row_ptr non-decreasing (VC_ERR_ARG).
+ * The FP64 refinement of such a handle uses the stored (scaled) values in FP64.
+ */
+int vc_build_mdp_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
+                     int val_dtype, const float* row_scale, const float* R, double gamma, void* stream,
+                     vc_mdp** out);
+
+/* Sizes of a handle (host struct out). */
+int vc_mdp_info(const vc_mdp* m, vc_info* out);
+
+/*
+ * Copy the stored CSR of a handle out (device pointers, each nullable): row_ptr
+ * [S*A+1] int64, col [nnz_stored] int32, val [nnz_stored] float (VC_CSR_F32) or uint16
+ * bf16 bits (VC_CSR_BF16), row_scale [S*A] float (BF16 only), R [S*A] float.
+ * VC_ERR_ARG for a VC_IMPLICIT handle, which stores no transitions.
+ */
+int vc_mdp_export_csr(const vc_mdp* m, int64_t* row_ptr, int32_t* col, void* val, float* row_scale, float* R,
+                      void* stream);
+
+/*
+ * Value iteration (Algorithm 3).  V: [S] float, in: V^0 (zeros = the paper's step 1,
+ * anything else = warm start / resume), out: the last FP32 iterate.  FP32 Jacobi sweeps
+ * run until the sweep residual is below max(tol, 4 ulp(max|V|)), stops improving for
+ * 64 sweeps (FP32 floor), or max_sweeps is reached.  Then, unless VC_ITER_FP32_ONLY,
+ * the FP64 refinement: pi = argmax of the FP32 values, FP64 Jacobi evaluation of pi
+ * until its sweep change is below tol, and an FP64 full Bellman backup V64 = T(V)
+ * whose residual max|T V - V| is the certificate (policy improvement repeats if the
+ * backup changes pi).  V64_out ([S] double, nullable) receives that backup, pi_out
+ * ([S] int32, nullable) its argmax.  Synchronises `stream`.
+ * Errors: VC_ERR_NOT_CONVERGED if max_sweeps ran out (outputs still written),
+ * VC_ERR_ARG for tol <= 0 or max_sweeps < 1.
+ */
+int vc_value_iterate(vc_mdp* m, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
+                     int flags, vc_stats* stats, void* stream);
+
+/*
+ * Policy extraction from FP32 values (Algorithm 3, step 4): pi[s] = argmax_a Q(s,a)
+ * (lowest action on ties, FP32 arithmetic), qgap[s] (nullable) = best Q minus the
+ * second-best (+INFINITY with one feasible action).  V: [S] float.
+ */
+int vc_extract_policy(vc_mdp* m, const float* V, int32_t* pi, float* qgap, void* stream);
+
+/*
+ * One FP32 Bellman sweep (Algorithm 3, step 2) without bookkeeping: V_out[s] = max_a Q(s,a)
+ * from V ([S] float), each output nullable (pi int32, qgap float).  Repeated calls give a
+ * fixed number of Jacobi sweeps; kernels are only enqueued on `stream`.
+ */
+int vc_bellman32(vc_mdp* m, const float* V, float* V_out, int32_t* pi, float* qgap, void* stream);
+
+/*
+ * FP64 Bellman backup of V ([S] double): V_out[s] = max_a Q(s,a) in FP64 (nullable),
+ * pi (nullable) the argmax, qgap (nullable, double) the gap, and *residual (host,
+ * nullable) = max_s |V_out(s) - V(s)|, the check of Algorithm 3, step 3.  Synchronises
+ * `stream` when residual is requested.
+ */
+int vc_bellman64(vc_mdp* m, const double* V, double* V_out, int32_t* pi, double* qgap, double* residual,
+                 void* stream);
+
+/*
+ * FP64 policy evaluation V_pi = R_pi + gamma P_pi V_pi by Jacobi sweeps over the chosen
+ * rows only.  pi: [S] int32 (must be feasible everywhere, else VC_ERR_ARG); V_pi: [S]
+ * double, in: initial guess, out: result once the sweep change is below tol.
+ * *sweeps_out (host, nullable) receives the sweep count.  Synchronises `stream`.
+ */
+int vc_evaluate_policy(vc_mdp* m, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
+                       int64_t* sweeps_out, void* stream);
+
+/* Release a handle and all device memory it owns (NULL is a no-op). */
+int vc_destroy(vc_mdp* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VCMDP_H */

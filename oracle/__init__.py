@@ -457,3 +457,12 @@ def bf16_renormalised(row_ptr, val, nrows):
     scale = np.zeros(nrows, np.float32)
     lib().or_bf16_renormalise_csr(int(nrows), _ptr(row_ptr), _ptr(val), _ptr(bits), _ptr(out), _ptr(scale))
     return bits, out, scale
+
+
+def sweep_states(p: dict, V: np.ndarray, Vn: np.ndarray, s0: int, s1: int, step: int = 1) -> int:
+    """Backups of states s0, s0+step, ... < s1 from V into Vn; returns the updates done."""
+    L = lib()
+    L.or_sweep_states.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int64]
+    L.or_sweep_states.restype = ctypes.c_int64
+    return int(L.or_sweep_states(ctypes.byref(_params(p)), _ptr(V), _ptr(Vn), int(s0), int(s1), int(step)))

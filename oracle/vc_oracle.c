@@ -650,3 +650,28 @@ void or_bf16_renormalise_csr(int64_t nrows, const int64_t* row_ptr, const double
         for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) val_out[j] = or_bf16_to_double(bits[j]) * (double)sc;
     }
 }
+
+/*
+ * One Jacobi backup (Algorithm 3, step 2) of the states s0, s0+step, ... < s1 from V into
+ * Vn (Vn indexed like V).  Returns the number of successor terms summed (the logical
+ * state-action-successor updates), used to time the oracle on a sample of a workload.
+ */
+int64_t or_sweep_states(const or_params* p, const double* V, double* Vn, int64_t s0, int64_t s1, int64_t step) {
+    int64_t updates = 0;
+    int64_t cols[OR_MAXSUCC];
+    double probs[OR_MAXSUCC], Rv;
+    for (int64_t s = s0; s < s1; s += step) {
+        double b = -INFINITY;
+        for (int a = 0; a <= p->H; a++) {
+            int n = or_transitions(p, s, a, cols, probs, &Rv);
+            if (n < 0) continue;
+            double acc = 0.0;
+            for (int j = 0; j < n; j++) acc += probs[j] * V[cols[j]];
+            updates += n;
+            double qv = Rv + p->gamma * acc;
+            if (qv > b) b = qv;
+        }
+        Vn[s] = b;
+    }
+    return updates;
+}

@@ -1,0 +1,432 @@
+// vc_api.cu -- the extern "C" entry points declared in include/vcmdp.h: handle
+// construction, the value-iteration driver (Algorithm 3: FP32 Jacobi sweeps until the
+// residual test of step 3, argmax policy of step 4) and the FP64 refinement and
+// certification that follow it.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <string>
+
+#include "vc_internal.cuh"
+
+namespace vc {
+
+static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? VC_ERR_OOM : VC_ERR_CUDA;
+}
+
+static void free_mdp(Mdp* m) {
+    if (!m) return;
+    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64,
+                    m->V64a, m->V64b, m->pi, m->pi2, m->ctl};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (m->ctl_host) cudaFreeHost(m->ctl_host);
+    delete m;
+}
+
+static int alloc_work(Mdp* m) {
+    int rc;
+    const size_t S = (size_t)m->S;
+    if ((rc = alloc_dev(m, (void**)&m->Vb, 4 * S))) return rc;
+    if ((m->fmt & 0xF) == VC_IMPLICIT && (rc = alloc_dev(m, (void**)&m->U32, 4 * S))) return rc;
+    if (m->has_model && (rc = alloc_dev(m, (void**)&m->U64, 8 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->V64a, 8 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->V64b, 8 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->pi, 4 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->pi2, 4 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->ctl, sizeof(Ctl)))) return rc;
+    VC_CUDA(cudaMallocHost((void**)&m->ctl_host, sizeof(Ctl)));
+    memset(m->ctl_host, 0, sizeof(Ctl));
+    VC_CUDA(cudaMemset(m->ctl, 0, sizeof(Ctl)));
+    return VC_OK;
+}
+
+static int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return n;
+}
+
+// ------------------------------------------------------------------ loop drivers
+static void reset_ctl(Ctl& h, double tol, long long max_sweeps) {
+    memset(&h, 0, sizeof(Ctl));
+    h.tol = tol;
+    h.max_sweeps = max_sweeps;
+    h.best_res = INFINITY;
+}
+
+static int read_ctl(Mdp* m, cudaStream_t st) {
+    VC_CUDA(cudaMemcpyAsync(m->ctl_host, m->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    return VC_OK;
+}
+
+// Sweeps still needed for a residual r to fall below tol at contraction rate gamma.
+static long long predict_sweeps(double r, double tol, double gamma) {
+    if (!(r > tol)) return 1;
+    const double n = ceil(log(tol / r) / log(gamma));
+    if (!(n < 1e6)) return 1000000;
+    return (long long)n + 1;
+}
+
+// FP32 value iteration with device-side termination.  Sweeps are enqueued in chunks;
+// once the device flags convergence the rest of a chunk returns immediately, so the
+// sweep count is exactly that of Algorithm 3.  On return buf[final] holds the iterate.
+static int loop32(Mdp* m, float* V, double tol, long long max_sweeps, cudaStream_t st, int* final_idx) {
+    Ctl& h = *m->ctl_host;
+    reset_ctl(h, tol, max_sweeps);
+    VC_CUDA(cudaMemcpyAsync(m->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    float* buf[2] = {V, m->Vb};
+    long long launched = 0, chunk = 16;
+    int rc;
+    for (;;) {
+        for (long long i = 0; i < chunk; i++) {
+            const int in = (int)(launched & 1);
+            SweepCtl sc{m->ctl, kModeLoop32, 1 - in, nullptr};
+            if ((rc = launch_sweep32(m, buf[in], buf[1 - in], nullptr, nullptr, sc, st))) return rc;
+            launched++;
+        }
+        if ((rc = read_ctl(m, st))) return rc;
+        if (h.done) break;
+        const int slot = (int)((h.sweeps - 1) % kRing);
+        float r, vm;
+        memcpy(&r, &h.res32[slot], 4);
+        memcpy(&vm, &h.vmax32[slot], 4);
+        int e = 0;
+        frexpf(vm, &e);
+        const double tol_eff = std::max(tol, vm > 0 ? 4.0 * ldexp(1.0, e - 24) : 0.0);
+        chunk = predict_sweeps(r, tol_eff, m->gamma);
+        chunk = std::min<long long>(std::max<long long>(chunk, 4), 1024);
+        chunk = std::min<long long>(chunk, max_sweeps - h.sweeps + 1);
+    }
+    *final_idx = h.final_buf;
+    return VC_OK;
+}
+
+// FP64 policy evaluation V <- R_pi + gamma P_pi V until the sweep change is below tol.
+static int loop_eval64(Mdp* m, const int32_t* pi, double* buf0, double* buf1, double tol, long long max_sweeps,
+                       cudaStream_t st, int* final_idx, long long* sweeps, int* error) {
+    Ctl& h = *m->ctl_host;
+    reset_ctl(h, tol, max_sweeps);
+    VC_CUDA(cudaMemcpyAsync(m->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    double* buf[2] = {buf0, buf1};
+    long long launched = 0, chunk = 16;
+    int rc;
+    for (;;) {
+        for (long long i = 0; i < chunk; i++) {
+            const int in = (int)(launched & 1);
+            SweepCtl sc{m->ctl, kModeLoop64, 1 - in, nullptr};
+            if ((rc = launch_eval64(m, pi, buf[in], buf[1 - in], sc, st))) return rc;
+            launched++;
+        }
+        if ((rc = read_ctl(m, st))) return rc;
+        if (h.done || h.error) break;
+        const int slot = (int)((h.sweeps - 1) % kRing);
+        double r;
+        memcpy(&r, &h.res64[slot], 8);
+        chunk = predict_sweeps(r, tol, m->gamma);
+        chunk = std::min<long long>(std::max<long long>(chunk, 4), 1024);
+        chunk = std::min<long long>(chunk, max_sweeps - h.sweeps + 1);
+    }
+    *final_idx = h.final_buf;
+    *sweeps = h.sweeps;
+    *error = h.error;
+    return VC_OK;
+}
+
+// One FP64 Bellman backup V_in -> V_out with argmax pi_out; returns max|V_out - V_in| and
+// the number of states whose argmax differs from pi_ref (if given).
+static int cert64(Mdp* m, const double* V_in, double* V_out, int32_t* pi_out, double* qgap,
+                  const int32_t* pi_ref, cudaStream_t st, double* residual, unsigned long long* changes) {
+    VC_CUDA(cudaMemsetAsync(&m->ctl->changes, 0, 2 * sizeof(unsigned long long), st));
+    SweepCtl sc{m->ctl, kModeCert64, 0, pi_ref};
+    int rc = launch_bellman64(m, V_in, V_out, pi_out, qgap, sc, st);
+    if (rc) return rc;
+    if ((rc = read_ctl(m, st))) return rc;
+    memcpy(residual, &m->ctl_host->cert64, 8);
+    if (changes) *changes = m->ctl_host->changes;
+    return VC_OK;
+}
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+}  // namespace vc
+
+using namespace vc;
+
+// =================================================================== extern "C" ABI
+extern "C" {
+
+const char* vc_last_error(void) { return g_err.c_str(); }
+
+int64_t vc_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
+    g_err.clear();
+    if (!out) return fail(VC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const int base = fmt & 0xF;
+    if (base != VC_IMPLICIT && base != VC_CSR_F32 && base != VC_CSR_BF16)
+        return fail(VC_ERR_ARG, "unknown format");
+    if ((fmt & ~(0xF | VC_PADDED)) != 0) return fail(VC_ERR_ARG, "unknown format flag");
+    if (base == VC_IMPLICIT && (fmt & VC_PADDED)) return fail(VC_ERR_ARG, "VC_PADDED needs a CSR format");
+    Mdp* m = new Mdp();
+    m->fmt = fmt;
+    m->num_sms = device_sms();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = build_model(p, m);
+    if (!rc && base != VC_IMPLICIT) rc = build_csr_from_model(m, st);
+    if (!rc && base == VC_IMPLICIT) rc = count_model_rows(m, st);  // logical nnz, nothing stored
+    if (!rc) rc = alloc_work(m);
+    if (rc) {
+        free_mdp(m);
+        return rc;
+    }
+    *out = (vc_mdp*)m;
+    return VC_OK;
+}
+
+int vc_build_mdp_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const void* val,
+                     int val_dtype, const float* row_scale, const float* R, double gamma, void* stream,
+                     vc_mdp** out) {
+    g_err.clear();
+    if (!out) return fail(VC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (S < 1 || S >= 2147483647LL || A < 1 || A > 1024 || S * (int64_t)A >= (1LL << 40))
+        return fail(VC_ERR_ARG, "S must be in [1, 2^31) and A in [1, 1024]");
+    if (!row_ptr || !R) return fail(VC_ERR_ARG, "row_ptr / R is NULL");
+    if (val_dtype != VC_VAL_F32 && val_dtype != VC_VAL_BF16) return fail(VC_ERR_ARG, "unknown val_dtype");
+    if (!(gamma > 0.0 && gamma < 1.0)) return fail(VC_ERR_ARG, "gamma must be in (0, 1)");
+    Mdp* m = new Mdp();
+    m->fmt = val_dtype == VC_VAL_BF16 ? VC_CSR_BF16 : VC_CSR_F32;
+    m->has_model = false;
+    m->S = (int)S;
+    m->A = A;
+    m->gamma = gamma;
+    m->num_sms = device_sms();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = build_csr_user(m, row_ptr, col, val, val_dtype, row_scale, R, st);
+    if (!rc) rc = alloc_work(m);
+    if (rc) {
+        free_mdp(m);
+        return rc;
+    }
+    *out = (vc_mdp*)m;
+    return VC_OK;
+}
+
+int vc_mdp_info(const vc_mdp* mh, vc_info* out) {
+    g_err.clear();
+    if (!mh || !out) return fail(VC_ERR_ARG, "NULL argument");
+    const Mdp* m = (const Mdp*)mh;
+    memset(out, 0, sizeof(*out));
+    out->S = m->S;
+    out->A = m->A;
+    out->fmt = m->fmt;
+    out->nnz_logical = m->nnz_logical;
+    out->nnz_stored = m->nnz_stored;
+    out->feasible_rows = m->feasible_rows;
+    out->device_bytes = m->device_bytes;
+    out->has_model = m->has_model ? 1 : 0;
+    const int64_t rows = (int64_t)m->S * m->A;
+    const int base = m->fmt & 0xF;
+    if (base == VC_IMPLICIT)
+        out->sweep_bytes = 8 * (int64_t)m->S;
+    else
+        out->sweep_bytes = m->nnz_stored * ((base == VC_CSR_BF16 ? 2 : 4) + 4) + rows * (8 + 4) +
+                           (base == VC_CSR_BF16 ? rows * 4 : 0) + 8 * (int64_t)m->S;
+    return VC_OK;
+}
+
+int vc_mdp_export_csr(const vc_mdp* mh, int64_t* row_ptr, int32_t* col, void* val, float* row_scale, float* R,
+                      void* stream) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    const Mdp* m = (const Mdp*)mh;
+    const int base = m->fmt & 0xF;
+    if (base == VC_IMPLICIT) return fail(VC_ERR_ARG, "an implicit handle stores no CSR");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t rows = (size_t)m->S * m->A;
+    const size_t nnz = (size_t)m->nnz_stored;
+    if (row_ptr) VC_CUDA(cudaMemcpyAsync(row_ptr, m->row_ptr, 8 * (rows + 1), cudaMemcpyDeviceToDevice, st));
+    if (col && nnz) VC_CUDA(cudaMemcpyAsync(col, m->col, 4 * nnz, cudaMemcpyDeviceToDevice, st));
+    if (val && nnz)
+        VC_CUDA(cudaMemcpyAsync(val, m->val, (base == VC_CSR_BF16 ? 2 : 4) * nnz, cudaMemcpyDeviceToDevice, st));
+    if (row_scale && m->scale) VC_CUDA(cudaMemcpyAsync(row_scale, m->scale, 4 * rows, cudaMemcpyDeviceToDevice, st));
+    if (R) VC_CUDA(cudaMemcpyAsync(R, m->R, 4 * rows, cudaMemcpyDeviceToDevice, st));
+    return VC_OK;
+}
+
+int vc_destroy(vc_mdp* mh) {
+    g_err.clear();
+    free_mdp((Mdp*)mh);
+    return VC_OK;
+}
+
+int vc_extract_policy(vc_mdp* mh, const float* V, int32_t* pi, float* qgap, void* stream) {
+    g_err.clear();
+    if (!mh || !V || !pi) return fail(VC_ERR_ARG, "NULL argument");
+    Mdp* m = (Mdp*)mh;
+    SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+    return launch_sweep32(m, V, nullptr, pi, qgap, sc, (cudaStream_t)stream);
+}
+
+int vc_bellman32(vc_mdp* mh, const float* V, float* V_out, int32_t* pi, float* qgap, void* stream) {
+    g_err.clear();
+    if (!mh || !V) return fail(VC_ERR_ARG, "NULL argument");
+    Mdp* m = (Mdp*)mh;
+    SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+    return launch_sweep32(m, V, V_out, pi, qgap, sc, (cudaStream_t)stream);
+}
+
+int vc_bellman64(vc_mdp* mh, const double* V, double* V_out, int32_t* pi, double* qgap, double* residual,
+                 void* stream) {
+    g_err.clear();
+    if (!mh || !V) return fail(VC_ERR_ARG, "NULL argument");
+    Mdp* m = (Mdp*)mh;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (residual) {
+        double r = 0;
+        int rc = cert64(m, V, V_out, pi, qgap, nullptr, st, &r, nullptr);
+        if (rc) return rc;
+        *residual = r;
+        return VC_OK;
+    }
+    SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+    return launch_bellman64(m, V, V_out, pi, qgap, sc, st);
+}
+
+int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
+                       int64_t* sweeps_out, void* stream) {
+    g_err.clear();
+    if (!mh || !pi || !V_pi) return fail(VC_ERR_ARG, "NULL argument");
+    if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
+    Mdp* m = (Mdp*)mh;
+    cudaStream_t st = (cudaStream_t)stream;
+    int fin = 0, err = 0;
+    long long sw = 0;
+    int rc = loop_eval64(m, pi, V_pi, m->V64b, tol, max_sweeps, st, &fin, &sw, &err);
+    if (rc) return rc;
+    if (fin == 1) VC_CUDA(cudaMemcpyAsync(V_pi, m->V64b, 8 * (size_t)m->S, cudaMemcpyDeviceToDevice, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    if (sweeps_out) *sweeps_out = sw;
+    if (err & kErrInfeasiblePolicy) return fail(VC_ERR_ARG, "the policy picks an infeasible action");
+    if (m->ctl_host->done != 1) return fail(VC_ERR_NOT_CONVERGED, "policy evaluation hit max_sweeps");
+    return VC_OK;
+}
+
+int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
+                     int flags, vc_stats* stats, void* stream) {
+    g_err.clear();
+    if (!mh || !V) return fail(VC_ERR_ARG, "NULL argument");
+    if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
+    Mdp* m = (Mdp*)mh;
+    cudaStream_t st = (cudaStream_t)stream;
+    vc_stats sx;
+    memset(&sx, 0, sizeof(sx));
+    cudaEvent_t ev[3];
+    for (auto& e : ev) VC_CUDA(cudaEventCreate(&e));
+    int rc = VC_OK;
+    int fin = 0;
+    const size_t S = (size_t)m->S;
+
+    VC_CUDA(cudaEventRecord(ev[0], st));
+    if ((rc = loop32(m, V, tol, max_sweeps, st, &fin))) goto out;
+    if (fin == 1) VC_CUDA(cudaMemcpyAsync(V, m->Vb, 4 * S, cudaMemcpyDeviceToDevice, st));
+    VC_CUDA(cudaEventRecord(ev[1], st));
+    sx.sweeps = m->ctl_host->sweeps;
+    {
+        float r;
+        memcpy(&r, &m->ctl_host->res32[(sx.sweeps - 1) % kRing], 4);
+        sx.residual = r;
+    }
+    {
+        const int done32 = m->ctl_host->done;
+        if (flags & VC_ITER_FP32_ONLY) {
+            if (pi_out) {
+                SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+                if ((rc = launch_sweep32(m, V, nullptr, pi_out, nullptr, sc, st))) goto out;
+            }
+            if (V64_out) {
+                if ((rc = launch_f32_to_f64(V, V64_out, m->S, st))) goto out;
+            }
+            VC_CUDA(cudaEventRecord(ev[2], st));
+            VC_CUDA(cudaStreamSynchronize(st));
+            if (done32 == 2) rc = fail(VC_ERR_NOT_CONVERGED, "max_sweeps reached before the FP32 tolerance");
+            goto out;
+        }
+        // ---- FP64 refinement (Algorithm 3 step 4 policy, then exact evaluation) ----
+        int32_t* pcur = m->pi;
+        int32_t* pnew = m->pi2;
+        {
+            SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+            if ((rc = launch_sweep32(m, V, nullptr, pcur, nullptr, sc, st))) goto out;
+        }
+        if ((rc = launch_f32_to_f64(V, m->V64a, m->S, st))) goto out;
+        double* cur = m->V64a;
+        double* other = m->V64b;
+        const long long eval_max = std::max<long long>(100000, max_sweeps);
+        bool certified = false;
+        double r64 = INFINITY;
+        for (int round = 0; round < 50; round++) {
+            int efin = 0, err = 0;
+            long long esw = 0;
+            if ((rc = loop_eval64(m, pcur, cur, other, tol, eval_max, st, &efin, &esw, &err))) goto out;
+            sx.eval_sweeps += esw;
+            if (err) {
+                rc = fail(VC_ERR_CUDA, "internal: refinement policy infeasible");
+                goto out;
+            }
+            if (efin == 1) std::swap(cur, other);  // cur = latest evaluation iterate
+            unsigned long long changes = 0;
+            if ((rc = cert64(m, cur, other, pnew, nullptr, pcur, st, &r64, &changes))) goto out;
+            sx.bellman64++;
+            sx.residual64 = r64;
+            std::swap(cur, other);  // cur = T(previous), Algorithm 3's V^{k+1}
+            std::swap(pcur, pnew);  // pcur = argmax of that backup
+            if (r64 < tol) {
+                certified = true;
+                break;
+            }
+            sx.policy_rounds++;
+        }
+        sx.certified = certified ? 1 : 0;
+        if (V64_out) VC_CUDA(cudaMemcpyAsync(V64_out, cur, 8 * S, cudaMemcpyDeviceToDevice, st));
+        if (pi_out) VC_CUDA(cudaMemcpyAsync(pi_out, pcur, 4 * S, cudaMemcpyDeviceToDevice, st));
+        VC_CUDA(cudaEventRecord(ev[2], st));
+        VC_CUDA(cudaStreamSynchronize(st));
+        if (!certified) rc = fail(VC_ERR_NOT_CONVERGED, "FP64 certificate not reached");
+    }
+out:
+    if (!rc || rc == VC_ERR_NOT_CONVERGED) {
+        sx.ms_fp32 = elapsed(ev[0], ev[1]);
+        sx.ms_fp64 = elapsed(ev[1], ev[2]);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (stats) *stats = sx;
+    return rc;
+}
+
+}  // extern "C"

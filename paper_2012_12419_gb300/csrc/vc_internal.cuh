@@ -1,0 +1,234 @@
+// vc_internal.cuh -- shared device/host definitions of the vcmdp library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/vcmdp.h"
+
+namespace vc {
+
+constexpr int kMaxH = VC_MAX_HOSTS;
+constexpr int kRing = 64;          // residual slots, indexed by sweep number mod kRing
+constexpr int kStallSweeps = 64;   // FP32 sweeps without a new best residual = FP32 floor
+
+// ------------------------------------------------------------------ error plumbing
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define VC_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return vc::cuda_fail(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------- division by a runtime constant
+// q = n / d for 0 <= n < 2^31 and 1 <= d < 2^16 as one 64-bit multiply and a shift:
+// with l = ceil(log2 d), sh = 31 + l and m = floor(2^sh / d) + 1 (m <= 2^32), the error
+// term m*d - 2^sh <= d <= 2^(sh-31) keeps floor(n*m / 2^sh) exact for every n < 2^31
+// (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994).
+struct FastDiv {
+    uint64_t m;
+    uint32_t sh;
+    uint32_t d;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1u << l) < d) l++;
+    FastDiv f;
+    f.sh = 31 + l;
+    f.m = ((uint64_t)1 << f.sh) / d + 1;
+    f.d = d;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+    return (uint32_t)(((uint64_t)n * f.m) >> f.sh);
+}
+
+// --------------------------------------------------------------------- model descriptor
+// Per-precision coefficients of the uniformised model (all probabilities already / Lam).
+template <typename T>
+struct Coef {
+    T gamma;
+    T pc[kMaxH];     // mu_k / Lam          (completion, times occ_k)
+    T pd[kMaxH];     // delta_k / Lam       (departure)
+    T lossd[kMaxH];  // w_loss * delta_k / Lam
+    T pa;            // lambda / Lam        (arrival)
+    T lossa;         // w_loss * lambda / Lam (blocked arrival)
+    T pf0, pf1;      // f / Lam (CCHI -> SCHI), (1 - f) / Lam (SCHI -> CCHI)
+    T w_occ, w_q;
+};
+
+struct Model {
+    int H, C, Q, A;
+    int S;
+    int stride[kMaxH];  // 2 (Q+1) (C+1)^k: code step of occ_k
+    FastDiv div_q;      // by Q+1
+    FastDiv div_c;      // by C+1
+};
+
+// Raw FP64 rates, used where probabilities are formed once (explicit CSR construction).
+struct Rates {
+    double mu[kMaxH], delta[kMaxH];
+    double lambda, f, Lam;
+    double w_occ, w_loss, w_q;
+};
+
+// Digits of a state code.
+struct Digits {
+    int occ[kMaxH];
+    int q, ph;
+};
+
+__device__ __forceinline__ void decode(const Model& md, int s, Digits& d) {
+    d.ph = s & 1;
+    uint32_t rest = (uint32_t)s >> 1;
+    uint32_t t = fdiv(rest, md.div_q);
+    d.q = (int)(rest - t * md.div_q.d);
+    rest = t;
+#pragma unroll
+    for (int k = 0; k < kMaxH; k++) {
+        if (k < md.H) {
+            uint32_t t2 = fdiv(rest, md.div_c);
+            d.occ[k] = (int)(rest - t2 * md.div_c.d);
+            rest = t2;
+        } else {
+            d.occ[k] = 0;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- control
+// Device-side loop control shared by the sweep kernels of one handle.
+struct Ctl {
+    unsigned int res32[kRing];          // FP32 residual bits per sweep (atomicMax on >= 0 floats)
+    unsigned int vmax32[kRing];         // max |V'| bits per sweep
+    unsigned long long res64[kRing];    // FP64 residual bits per sweep
+    unsigned int ticket;                // arrival counter of the last-block pattern
+    int done;                           // 0 running, 1 converged, 2 max sweeps, 3 stalled at the FP32 floor
+    long long sweeps;                   // sweeps completed
+    long long max_sweeps;
+    int final_buf;                      // ping-pong buffer holding the latest iterate
+    int since_best;
+    float best_res;
+    float pad_;
+    double tol;
+    unsigned long long changes;         // policy entries that differ from a reference policy
+    unsigned long long cert64;          // FP64 residual bits of a standalone Bellman backup
+    int error;                          // bit flags raised by kernels (infeasible policy, bad input)
+    int pad2_;
+};
+
+// Error flags raised on the device.
+constexpr int kErrInfeasiblePolicy = 1;
+constexpr int kErrBadColumn = 2;
+constexpr int kErrNegative = 4;
+constexpr int kErrRowSum = 8;
+constexpr int kErrNoFeasible = 16;
+constexpr int kErrRowPtr = 32;
+
+// Bookkeeping mode of a sweep kernel.
+enum SweepMode : int {
+    kModeNone = 0,     // plain backup (policy extraction)
+    kModeLoop32 = 1,   // FP32 value-iteration loop: skip when done, residual ring, tolerance / stall
+    kModeLoop64 = 2,   // FP64 policy-evaluation loop: skip when done, FP64 residual ring
+    kModeCert64 = 3,   // FP64 standalone backup: residual into cert64, policy changes vs pi_ref
+};
+
+struct SweepCtl {
+    Ctl* ctl;
+    int mode;
+    int out_index;
+    const int32_t* pi_ref;
+};
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide max of a non-negative value; result valid in thread 0.
+template <typename T, int NT>
+__device__ __forceinline__ T block_max(T v) {
+    __shared__ T part[NT / 32];
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) part[w] = v;
+    __syncthreads();
+    T r = 0;
+    if (threadIdx.x < 32) {
+        r = (l < NT / 32) ? part[l] : T(0);
+        r = warp_max(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ unsigned int fbits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// ---------------------------------------------------------------------------- handle
+struct Mdp {
+    int fmt;              // VC_IMPLICIT / VC_CSR_F32 / VC_CSR_BF16 (| VC_PADDED)
+    bool has_model;
+    int S, A;
+    double gamma;
+    Model md;
+    Rates rates;
+    Coef<float> c32;
+    Coef<double> c64;
+    // explicit CSR (owned)
+    int64_t nnz_stored = 0, nnz_logical = 0, feasible_rows = 0;
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    void* val = nullptr;        // float or uint16 (bf16)
+    float* scale = nullptr;     // BF16 per-row scale
+    float* R = nullptr;         // [S*A], -inf = infeasible
+    // work buffers (owned)
+    float* Vb = nullptr;        // FP32 ping-pong partner
+    float* U32 = nullptr;       // FP32 post-decision values (implicit)
+    double* U64 = nullptr;      // FP64 post-decision values
+    double* V64a = nullptr;     // FP64 ping-pong pair
+    double* V64b = nullptr;
+    int32_t* pi = nullptr;      // policy under refinement
+    int32_t* pi2 = nullptr;
+    Ctl* ctl = nullptr;         // device control block
+    Ctl* ctl_host = nullptr;    // pinned mirror
+    int64_t device_bytes = 0;
+    int num_sms = 0;
+};
+
+// Process-wide count of kernels this library has enqueued.
+void count_launches(int n);
+
+// Kernels / launchers implemented in the .cu files.
+int alloc_dev(Mdp* m, void** p, size_t bytes);
+int build_model(const vc_params* p, Mdp* m);
+int build_csr_from_model(Mdp* m, cudaStream_t st);
+int count_model_rows(Mdp* m, cudaStream_t st);
+int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
+                   const float* row_scale, const float* R, cudaStream_t st);
+
+// One FP32 Bellman backup V_in -> V_out (implicit or CSR), optional policy / gap.
+int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc,
+                   cudaStream_t st);
+// One FP64 full Bellman backup (exact model when available, else the stored CSR in FP64).
+int launch_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double* qgap, SweepCtl sc,
+                     cudaStream_t st);
+// One FP64 policy-evaluation sweep over the chosen rows.
+int launch_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st);
+// Elementwise helpers.
+int launch_f32_to_f64(const float* in, double* out, int n, cudaStream_t st);
+
+}  // namespace vc

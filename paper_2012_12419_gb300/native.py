@@ -1,0 +1,319 @@
+"""ctypes binding of ``libvcmdp.so`` (declared in ``include/vcmdp.h``).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current stream.  Without the built library (or
+without a CUDA device) every call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+VC_OK = 0
+VC_ERR_ARG = 1
+VC_ERR_NOT_STOCHASTIC = 2
+VC_ERR_NO_FEASIBLE_ACTION = 3
+VC_ERR_NOT_CONVERGED = 4
+VC_ERR_TIMEOUT = 5
+VC_ERR_OOM = 6
+VC_ERR_CUDA = 7
+
+VC_IMPLICIT = 0
+VC_CSR_F32 = 1
+VC_CSR_BF16 = 2
+VC_PADDED = 16
+VC_VAL_F32 = 0
+VC_VAL_BF16 = 1
+VC_ITER_FP32_ONLY = 1
+
+FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF16}
+
+EXPORTS = [
+    "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
+    "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches",
+]
+
+
+class VcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"vcmdp error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int32), ("C", ctypes.c_int32), ("Q", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("lam", ctypes.c_double), ("f", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("w_occ", ctypes.c_double), ("w_loss", ctypes.c_double), ("w_q", ctypes.c_double),
+        ("mu", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("S", ctypes.c_int64), ("A", ctypes.c_int32), ("fmt", ctypes.c_int32),
+        ("nnz_logical", ctypes.c_int64), ("nnz_stored", ctypes.c_int64), ("feasible_rows", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64), ("sweep_bytes", ctypes.c_int64),
+        ("has_model", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int64), ("residual", ctypes.c_double), ("eval_sweeps", ctypes.c_int64),
+        ("bellman64", ctypes.c_int64), ("policy_rounds", ctypes.c_int32), ("certified", ctypes.c_int32),
+        ("residual64", ctypes.c_double), ("ms_fp32", ctypes.c_double), ("ms_fp64", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load the library (optionally building it first).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.vc_last_error.restype = ctypes.c_char_p
+        L.vc_last_error.argtypes = []
+        L.vc_build_mdp.argtypes = [ctypes.POINTER(Params), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.vc_build_mdp_csr.argtypes = [i64, i32, vp, vp, vp, ctypes.c_int, vp, vp, dbl, vp, ctypes.POINTER(vp)]
+        L.vc_mdp_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.vc_value_iterate.argtypes = [vp, vp, vp, vp, dbl, i64, ctypes.c_int, ctypes.POINTER(Stats), vp]
+        L.vc_extract_policy.argtypes = [vp, vp, vp, vp, vp]
+        L.vc_bellman64.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(dbl), vp]
+        L.vc_evaluate_policy.argtypes = [vp, vp, vp, dbl, i64, ctypes.POINTER(i64), vp]
+        L.vc_destroy.argtypes = [vp]
+        L.vc_mdp_export_csr.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.vc_bellman32.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.vc_kernel_launches.argtypes = []
+        for name in EXPORTS:
+            if name not in ("vc_last_error", "vc_kernel_launches"):
+                getattr(L, name).restype = ctypes.c_int
+        L.vc_kernel_launches.restype = ctypes.c_int64
+        _lib = L
+        return _lib
+
+
+def _check(rc: int, allow=()):
+    if rc != VC_OK and rc not in allow:
+        msg = load().vc_last_error().decode(errors="replace")
+        raise VcError(rc, msg)
+    return rc
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _params(p: dict):
+    H = int(p["H"])
+    mu = (ctypes.c_double * H)(*[float(v) for v in p["mu"][:H]])
+    delta = (ctypes.c_double * H)(*[float(v) for v in p["delta"][:H]])
+    c = Params(H, int(p["C"]), int(p["Q"]), 0, float(p["lam"]), float(p["f"]), float(p["gamma"]),
+               float(p["w_occ"]), float(p["w_loss"]), float(p["w_q"]),
+               ctypes.cast(mu, ctypes.POINTER(ctypes.c_double)), ctypes.cast(delta, ctypes.POINTER(ctypes.c_double)))
+    return c, (mu, delta)
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        raise RuntimeError("vcmdp needs a CUDA device")
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+class MDP:
+    """An instance on the device (a ``vc_mdp`` handle)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        self._info = None
+
+    # ------------------------------------------------------------------ construction
+    @classmethod
+    def build(cls, params: dict, fmt: str = "implicit", padded: bool = False, stream=None) -> "MDP":
+        L = load()
+        _dev()
+        code = FORMATS[fmt] | (VC_PADDED if padded else 0)
+        cp, keep = _params(params)
+        h = ctypes.c_void_p()
+        _check(L.vc_build_mdp(ctypes.byref(cp), code, _stream(stream), ctypes.byref(h)))
+        del keep
+        return cls(h)
+
+    @classmethod
+    def from_csr(cls, S: int, A: int, row_ptr, col, val, R, gamma: float, row_scale=None, stream=None) -> "MDP":
+        """Arbitrary explicit MDP: CUDA tensors int64 row_ptr[S*A+1], int32 col, float32 or
+        bfloat16 val, float32 R[S*A] (-inf = infeasible), optional float32 row_scale."""
+        L = load()
+        if val.dtype == torch.float32:
+            vdt = VC_VAL_F32
+        elif val.dtype == torch.bfloat16:
+            vdt = VC_VAL_BF16
+        else:
+            raise ValueError("val must be float32 or bfloat16")
+        assert row_ptr.dtype == torch.int64 and col.dtype == torch.int32 and R.dtype == torch.float32
+        h = ctypes.c_void_p()
+        _check(L.vc_build_mdp_csr(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), vdt, _ptr(row_scale),
+                                  _ptr(R), float(gamma), _stream(stream), ctypes.byref(h)))
+        return cls(h)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().vc_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------------ queries
+    def info(self) -> dict:
+        if self._info is None:
+            inf = Info()
+            _check(load().vc_mdp_info(self._h, ctypes.byref(inf)))
+            self._info = {k: getattr(inf, k) for k, _ in Info._fields_ if k != "reserved"}
+        return self._info
+
+    @property
+    def S(self) -> int:
+        return int(self.info()["S"])
+
+    @property
+    def A(self) -> int:
+        return int(self.info()["A"])
+
+    # ------------------------------------------------------------------------- solve
+    def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
+                      want_v64: bool = True, want_pi: bool = True, stream=None, raise_on_nonconvergence=True):
+        """Algorithm 3 on the device.  Returns (V fp32, V64 fp64 or None, pi int32 or None, stats dict)."""
+        dev = _dev()
+        S = self.S
+        if V is None:
+            V = torch.zeros(S, dtype=torch.float32, device=dev)
+        V64 = torch.empty(S, dtype=torch.float64, device=dev) if want_v64 else None
+        pi = torch.empty(S, dtype=torch.int32, device=dev) if want_pi else None
+        st = Stats()
+        rc = load().vc_value_iterate(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
+                                     VC_ITER_FP32_ONLY if fp32_only else 0, ctypes.byref(st), _stream(stream))
+        _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
+        d = st.as_dict()
+        d["status"] = rc
+        return V, V64, pi, d
+
+    def extract_policy(self, V, stream=None):
+        dev = _dev()
+        pi = torch.empty(self.S, dtype=torch.int32, device=dev)
+        gap = torch.empty(self.S, dtype=torch.float32, device=dev)
+        _check(load().vc_extract_policy(self._h, _ptr(V), _ptr(pi), _ptr(gap), _stream(stream)))
+        return pi, gap
+
+    def bellman32(self, V, V_out=None, pi=None, qgap=None, stream=None):
+        """One FP32 Bellman sweep (outputs optional, preallocated CUDA tensors)."""
+        _check(load().vc_bellman32(self._h, _ptr(V), _ptr(V_out), _ptr(pi), _ptr(qgap), _stream(stream)))
+        return V_out
+
+    def bellman64(self, V64, stream=None):
+        dev = _dev()
+        out = torch.empty(self.S, dtype=torch.float64, device=dev)
+        pi = torch.empty(self.S, dtype=torch.int32, device=dev)
+        gap = torch.empty(self.S, dtype=torch.float64, device=dev)
+        r = ctypes.c_double()
+        _check(load().vc_bellman64(self._h, _ptr(V64), _ptr(out), _ptr(pi), _ptr(gap), ctypes.byref(r),
+                                   _stream(stream)))
+        return out, pi, gap, r.value
+
+    def export_csr(self, stream=None):
+        """Copies of the stored CSR: (row_ptr, col, val, row_scale or None, R) CUDA tensors."""
+        dev = _dev()
+        inf = self.info()
+        rows = int(inf["S"]) * int(inf["A"])
+        nnz = int(inf["nnz_stored"])
+        bf16 = (inf["fmt"] & 0xF) == VC_CSR_BF16
+        row_ptr = torch.empty(rows + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+        val = torch.empty(max(nnz, 1), dtype=torch.int16 if bf16 else torch.float32, device=dev)
+        scale = torch.empty(rows, dtype=torch.float32, device=dev) if bf16 else None
+        R = torch.empty(rows, dtype=torch.float32, device=dev)
+        _check(load().vc_mdp_export_csr(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(scale), _ptr(R),
+                                        _stream(stream)))
+        torch.cuda.synchronize()
+        return row_ptr, col[:nnz], val[:nnz], scale, R
+
+    def evaluate_policy(self, pi, V0=None, tol: float = 1e-10, max_sweeps: int = 1_000_000, stream=None):
+        dev = _dev()
+        V = torch.zeros(self.S, dtype=torch.float64, device=dev) if V0 is None else V0.clone()
+        n = ctypes.c_int64()
+        _check(load().vc_evaluate_policy(self._h, _ptr(pi), _ptr(V), float(tol), int(max_sweeps), ctypes.byref(n),
+                                         _stream(stream)))
+        return V, n.value
+
+
+def solve(params: dict, fmt: str = "implicit", padded: bool = False, tol: float = 1e-6,
+          max_sweeps: int = 1_000_000):
+    """End-to-end call from host inputs to host results: build, iterate, certify.
+
+    Returns numpy (V64, pi) and the stats dict.  The instance is built and solved on the
+    current CUDA device; the results are copied back to the host.
+    """
+    m = MDP.build(params, fmt=fmt, padded=padded)
+    try:
+        V, V64, pi, st = m.value_iterate(tol=tol, max_sweeps=max_sweeps)
+        return V64.cpu().numpy(), pi.cpu().numpy(), st
+    finally:
+        m.close()
+
+
+def kernel_launches() -> int:
+    """Kernels the library has enqueued since it was loaded (process-wide)."""
+    return int(load().vc_kernel_launches())
+
+
+def exported_symbols(path: str | None = None):
+    """Names of the vc_* symbols the shared object exports (no CUDA needed)."""
+    L = ctypes.CDLL(path or _build.LIB)
+    return [n for n in EXPORTS if hasattr(L, n)]
+
+
+def fmt_name(code: int) -> str:
+    inv = {v: k for k, v in FORMATS.items()}
+    return inv[code & 0xF] + ("+padded" if code & VC_PADDED else "")
+
+
+__all__ = ["MDP", "solve", "VcError", "load", "exported_symbols", "np"]
