@@ -202,6 +202,8 @@ def run_native(args):
         "time_to_residual_ms": statistics.median(ms),
         "sweeps_per_step": statistics.median(sweeps),
         "fp64_eval_sweeps_per_step": statistics.median([s["eval_sweeps"] for s in stats]),
+        "ms_fp32_sweeps": statistics.median([s["ms_fp32"] for s in stats]),
+        "ms_fp64_refine": statistics.median([s["ms_fp64"] for s in stats]),
         "certified": all(s["certified"] == 1 for s in stats),
         "residual64": max(s["residual64"] for s in stats),
         "build_ms": build_ms,
@@ -308,6 +310,7 @@ def variants(args, p, native, torch, dev, stream):
         t = e0.elapsed_time(e1) / reps
         out[form + ("+padded" if padded else "")] = {
             "time_to_residual_ms": t, "updates_per_s": info["nnz_logical"] * sweeps / reps / (t / 1e3),
+            "ms_fp32_sweeps": st["ms_fp32"], "ms_fp64_refine": st["ms_fp64"],
             "sweeps": sweeps // reps, "nnz_stored": int(info["nnz_stored"]),
             "sweep_bytes": int(info["sweep_bytes"])}
         m.close()

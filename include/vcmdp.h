@@ -58,6 +58,8 @@ extern "C" {
 #define VC_CSR_F32 1   /* explicit CSR, FP32 probabilities, int32 columns, int64 row offsets */
 #define VC_CSR_BF16 2  /* explicit CSR, BF16 probabilities + FP32 per-row renormalising scale */
 #define VC_PADDED 16   /* CSR rows padded to exactly 2H+3 entries, infeasible rows included */
+#define VC_DIRECT 32   /* CSR sweeps read rows straight from global memory (no shared-memory
+                          pipeline); same arithmetic and results, for comparison */
 
 /* value types for vc_build_mdp_csr */
 #define VC_VAL_F32 0

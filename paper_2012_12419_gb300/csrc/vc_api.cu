@@ -33,8 +33,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 static void free_mdp(Mdp* m) {
     if (!m) return;
-    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64,
-                    m->V64a, m->V64b, m->pi, m->pi2, m->ctl};
+    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64, m->V64a,
+                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->ctl_host) cudaFreeHost(m->ctl_host);
@@ -49,6 +49,9 @@ static int alloc_work(Mdp* m) {
     if (m->has_model && (rc = alloc_dev(m, (void**)&m->U64, 8 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->V64a, 8 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->V64b, 8 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->E0, 4 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->E1, 4 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->Rres, 4 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->pi, 4 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->pi2, 4 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->ctl, sizeof(Ctl)))) return rc;
@@ -87,24 +90,30 @@ static long long predict_sweeps(double r, double tol, double gamma) {
     return (long long)n + 1;
 }
 
-// FP32 value iteration with device-side termination.  Sweeps are enqueued in chunks;
-// once the device flags convergence the rest of a chunk returns immediately, so the
-// sweep count is exactly that of Algorithm 3.  On return buf[final] holds the iterate.
-static int loop32(Mdp* m, float* V, double tol, long long max_sweeps, cudaStream_t st, int* final_idx) {
+// An FP32 fixed-point loop with device-side termination (value iteration, or the
+// correction solve of the refinement).  Sweeps are enqueued in chunks sized from the
+// observed residual; once the device flags termination the rest of a chunk returns
+// immediately, so the sweep count is exactly the first sweep meeting the test.  On
+// return buf[*final_idx] holds the iterate.
+template <typename Launch>
+static int loop32(Mdp* m, float* buf0, float* buf1, double tol, long long max_sweeps, cudaStream_t st,
+                  int* final_idx, Launch&& launch) {
     Ctl& h = *m->ctl_host;
     reset_ctl(h, tol, max_sweeps);
     VC_CUDA(cudaMemcpyAsync(m->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    float* buf[2] = {V, m->Vb};
+    float* buf[2] = {buf0, buf1};
     long long launched = 0, chunk = 16;
     int rc;
     for (;;) {
         for (long long i = 0; i < chunk; i++) {
             const int in = (int)(launched & 1);
             SweepCtl sc{m->ctl, kModeLoop32, 1 - in, nullptr};
-            if ((rc = launch_sweep32(m, buf[in], buf[1 - in], nullptr, nullptr, sc, st))) return rc;
+            if ((rc = launch(buf[in], buf[1 - in], sc))) return rc;
             launched++;
         }
         if ((rc = read_ctl(m, st))) return rc;
+        if (h.error & kErrTimeout) return fail(VC_ERR_TIMEOUT, "a bounded device-side wait expired");
+        if (h.error) return fail(VC_ERR_ARG, "a kernel flagged invalid input (infeasible policy)");
         if (h.done) break;
         const int slot = (int)((h.sweeps - 1) % kRing);
         float r, vm;
@@ -190,8 +199,9 @@ int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
     const int base = fmt & 0xF;
     if (base != VC_IMPLICIT && base != VC_CSR_F32 && base != VC_CSR_BF16)
         return fail(VC_ERR_ARG, "unknown format");
-    if ((fmt & ~(0xF | VC_PADDED)) != 0) return fail(VC_ERR_ARG, "unknown format flag");
-    if (base == VC_IMPLICIT && (fmt & VC_PADDED)) return fail(VC_ERR_ARG, "VC_PADDED needs a CSR format");
+    if ((fmt & ~(0xF | VC_PADDED | VC_DIRECT)) != 0) return fail(VC_ERR_ARG, "unknown format flag");
+    if (base == VC_IMPLICIT && (fmt & (VC_PADDED | VC_DIRECT)))
+        return fail(VC_ERR_ARG, "VC_PADDED / VC_DIRECT need a CSR format");
     Mdp* m = new Mdp();
     m->fmt = fmt;
     m->num_sms = device_sms();
@@ -353,7 +363,10 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
     const size_t S = (size_t)m->S;
 
     VC_CUDA(cudaEventRecord(ev[0], st));
-    if ((rc = loop32(m, V, tol, max_sweeps, st, &fin))) goto out;
+    rc = loop32(m, V, m->Vb, tol, max_sweeps, st, &fin, [&](const float* in, float* o, SweepCtl sc) {
+        return launch_sweep32(m, in, o, nullptr, nullptr, sc, st);
+    });
+    if (rc) goto out;
     if (fin == 1) VC_CUDA(cudaMemcpyAsync(V, m->Vb, 4 * S, cudaMemcpyDeviceToDevice, st));
     VC_CUDA(cudaEventRecord(ev[1], st));
     sx.sweeps = m->ctl_host->sweeps;
@@ -377,7 +390,14 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
             if (done32 == 2) rc = fail(VC_ERR_NOT_CONVERGED, "max_sweeps reached before the FP32 tolerance");
             goto out;
         }
-        // ---- FP64 refinement (Algorithm 3 step 4 policy, then exact evaluation) ----
+        // ---- refinement: the argmax policy of the FP32 values (Algorithm 3, step 4) is
+        // evaluated by mixed-precision iterative refinement -- policy residual
+        // r = T_pi V64 - V64 in FP64, correction (I - gamma P_pi) e = r solved by FP32
+        // Jacobi sweeps, V64 += e -- and certified by one FP64 Bellman backup whose
+        // residual is the step-3 test.  If the backup's argmax differs, the loop repeats
+        // with it (a policy-improvement step).  Since T_pi(V64 + e_k) - (V64 + e_k) equals
+        // the next correction change, stopping the correction at tol/2 leaves a policy
+        // residual below tol.
         int32_t* pcur = m->pi;
         int32_t* pnew = m->pi2;
         {
@@ -391,15 +411,20 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
         bool certified = false;
         double r64 = INFINITY;
         for (int round = 0; round < 50; round++) {
-            int efin = 0, err = 0;
-            long long esw = 0;
-            if ((rc = loop_eval64(m, pcur, cur, other, tol, eval_max, st, &efin, &esw, &err))) goto out;
-            sx.eval_sweeps += esw;
-            if (err) {
-                rc = fail(VC_ERR_CUDA, "internal: refinement policy infeasible");
-                goto out;
+            {
+                SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+                VC_CUDA(cudaMemsetAsync(&m->ctl->error, 0, sizeof(int), st));
+                if ((rc = launch_resid64(m, pcur, cur, m->Rres, sc, st))) goto out;
             }
-            if (efin == 1) std::swap(cur, other);  // cur = latest evaluation iterate
+            VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * S, st));
+            int efin = 0;
+            rc = loop32(m, m->E0, m->E1, 0.5 * tol, eval_max, st, &efin,
+                        [&](const float* in, float* o, SweepCtl sc) {
+                            return launch_correct32(m, pcur, m->Rres, in, o, sc, st);
+                        });
+            if (rc) goto out;
+            sx.eval_sweeps += m->ctl_host->sweeps;
+            if ((rc = launch_axpy64(cur, efin == 1 ? m->E1 : m->E0, m->S, st))) goto out;
             unsigned long long changes = 0;
             if ((rc = cert64(m, cur, other, pnew, nullptr, pcur, st, &r64, &changes))) goto out;
             sx.bellman64++;

@@ -415,11 +415,11 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     m->nnz_logical = (int64_t)th[1];
     m->nnz_stored = padded ? nrows * width : m->nnz_logical;
 
-    if ((rc = alloc_dev(m, (void**)&m->row_ptr, sizeof(int64_t) * (nrows + 1)))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->col, sizeof(int32_t) * m->nnz_stored))) return rc;
-    if ((rc = alloc_dev(m, &m->val, (bf16 ? 2 : 4) * (size_t)m->nnz_stored))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->R, sizeof(float) * nrows))) return rc;
-    if (bf16 && (rc = alloc_dev(m, (void**)&m->scale, sizeof(float) * nrows))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->row_ptr, sizeof(int64_t) * (nrows + 3)))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->col, sizeof(int32_t) * (m->nnz_stored + 16)))) return rc;
+    if ((rc = alloc_dev(m, &m->val, (bf16 ? 2 : 4) * (size_t)(m->nnz_stored + 16)))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->R, sizeof(float) * (nrows + 8)))) return rc;
+    if (bf16 && (rc = alloc_dev(m, (void**)&m->scale, sizeof(float) * (nrows + 8)))) return rc;
 
     if (padded) {
         count_launches(1);
@@ -438,7 +438,7 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     VC_CUDA(cudaFreeAsync(cnt, st));
     VC_CUDA(cudaFreeAsync(tallies, st));
     VC_CUDA(cudaStreamSynchronize(st));
-    return VC_OK;
+    return plan_csr(m, st);
 }
 
 // ------------------------------------------------------------------------ user CSR
@@ -507,11 +507,11 @@ int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const voi
     const bool bf16 = val_dtype == VC_VAL_BF16;
     int rc;
     m->nnz_stored = nnz;
-    if ((rc = alloc_dev(m, (void**)&m->row_ptr, sizeof(int64_t) * (nrows + 1)))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->col, sizeof(int32_t) * nnz))) return rc;
-    if ((rc = alloc_dev(m, &m->val, (bf16 ? 2 : 4) * (size_t)nnz))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->R, sizeof(float) * nrows))) return rc;
-    if (bf16 && (rc = alloc_dev(m, (void**)&m->scale, sizeof(float) * nrows))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->row_ptr, sizeof(int64_t) * (nrows + 3)))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->col, sizeof(int32_t) * (nnz + 16)))) return rc;
+    if ((rc = alloc_dev(m, &m->val, (bf16 ? 2 : 4) * (size_t)(nnz + 16)))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->R, sizeof(float) * (nrows + 8)))) return rc;
+    if (bf16 && (rc = alloc_dev(m, (void**)&m->scale, sizeof(float) * (nrows + 8)))) return rc;
     VC_CUDA(cudaMemcpyAsync(m->row_ptr, row_ptr, sizeof(int64_t) * (nrows + 1), cudaMemcpyDeviceToDevice, st));
     if (nnz > 0) {
         VC_CUDA(cudaMemcpyAsync(m->col, col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
@@ -544,7 +544,7 @@ int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const voi
     if (herr & kErrNegative) return fail(VC_ERR_NOT_STOCHASTIC, "negative or non-finite probability / reward");
     if (herr & kErrRowSum) return fail(VC_ERR_NOT_STOCHASTIC, "a feasible row does not sum to 1 (tolerance 1e-5)");
     if (herr & kErrNoFeasible) return fail(VC_ERR_NO_FEASIBLE_ACTION, "a state has no feasible action");
-    return VC_OK;
+    return plan_csr(m, st);
 }
 
 }  // namespace vc

@@ -1,0 +1,755 @@
+// vc_csr.cu -- explicit-CSR Bellman sweep (Algorithm 3, step 2; Eq. 18 backup from stored
+// rows r = s*A + a) and the FP64 / correction kernels of handles without a model.
+//
+// Main kernel, k_csr_tma: the CSR streams (row_ptr, R, scale, col, val) are the only
+// HBM-bound data, so each CTA runs a producer/consumer pipeline over tiles of `ts`
+// consecutive states.  One producer lane stages the tile's contiguous slices into shared
+// memory with bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier,
+// L2 evict-first so the streamed matrix does not push V out of L2); NW consumer warps
+// compute from shared memory.  Consumer lanes map to rows: APAD lanes per state (APAD =
+// next power of two >= A), lane a sums row (s, a) in column order and the state's Q values
+// are reduced across its APAD lanes with xor shuffles to (max, lowest argmax, second max).
+// Consecutive states of a tile share successor offsets, so the V gathers of one warp touch
+// few cache lines.  Every wait is bounded: on expiry the kernel flags kErrTimeout, drains
+// its own copies (again bounded) and returns normally.
+//
+// Fallback, k_csr_direct: the same row mapping reading rows straight from global memory,
+// for tiles that do not fit in shared memory (very long rows) or A > 32.
+#include <math.h>
+
+#include "vc_internal.cuh"
+
+namespace vc {
+
+constexpr int kNW = 8;                      // consumer warps of the pipelined kernel
+constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier polling (~0.5-2 s worst case)
+
+// --------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Polls the barrier phase with a hard iteration limit; false if it never completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it >= 8) __nanosleep(128);
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// ----------------------------------------------------------------------- tile layout
+struct StageLayout {
+    int off_rp, off_R, off_scale, off_col, off_val, bytes;
+};
+
+__host__ __device__ inline int round16(long long x) { return (int)((x + 15) & ~15LL); }
+
+__host__ __device__ inline StageLayout stage_layout(int ts, int A, long long cap, int vt_size, bool has_scale) {
+    StageLayout L;
+    const long long rows = (long long)ts * A;
+    L.off_rp = 0;
+    L.off_R = L.off_rp + round16(8 * (rows + 2));
+    L.off_scale = L.off_R + round16(4 * (rows + 4));
+    L.off_col = L.off_scale + (has_scale ? round16(4 * (rows + 4)) : 0);
+    L.off_val = L.off_col + round16(4 * (cap + 8));
+    L.bytes = L.off_val + round16((long long)vt_size * (cap + 8));
+    return L;
+}
+
+template <typename VT>
+__device__ __forceinline__ float ldv(const VT* p, int j);
+template <>
+__device__ __forceinline__ float ldv<float>(const float* p, int j) {
+    return p[j];
+}
+template <>
+__device__ __forceinline__ float ldv<uint16_t>(const uint16_t* p, int j) {
+    return __uint_as_float((uint32_t)p[j] << 16);
+}
+template <typename VT>
+__device__ __forceinline__ float ldg_v(const VT* p, int64_t j);
+template <>
+__device__ __forceinline__ float ldg_v<float>(const float* p, int64_t j) {
+    return __ldg(p + j);
+}
+template <>
+__device__ __forceinline__ float ldg_v<uint16_t>(const uint16_t* p, int64_t j) {
+    return __uint_as_float((uint32_t)__ldg(p + j) << 16);
+}
+
+// Top-2 merge over xor partners: (best, lowest index of best, second best).
+template <int WIDTH>
+__device__ __forceinline__ void top2_reduce(float& b1, int& ia, float& b2) {
+#pragma unroll
+    for (int o = 1; o < WIDTH; o <<= 1) {
+        const float ob1 = __shfl_xor_sync(0xffffffffu, b1, o);
+        const float ob2 = __shfl_xor_sync(0xffffffffu, b2, o);
+        const int oia = __shfl_xor_sync(0xffffffffu, ia, o);
+        const bool take = (ob1 > b1) || (ob1 == b1 && oia < ia);
+        const float nb2 = fmaxf(fmaxf(b2, ob2), take ? b1 : ob1);
+        b1 = take ? ob1 : b1;
+        ia = take ? oia : ia;
+        b2 = nb2;
+    }
+}
+
+// Dot product of one stored row with V, in column order.  Entries go in batches of
+// kBatch: every gather of a batch is issued before the first multiply-add, so a row of up
+// to kBatch successors costs one L2 round trip instead of one per entry; the adds stay in
+// column order (identical results to the sequential loop).
+constexpr int kBatch = 16;
+
+template <typename VT>
+__device__ __forceinline__ float row_dot_smem(const int32_t* cp, const VT* vp, int n, const float* __restrict__ V) {
+    float acc = 0.0f;
+    for (int j0 = 0; j0 < n; j0 += kBatch) {
+        float w[kBatch], g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (j0 + u < n) {
+                w[u] = ldv<VT>(vp, j0 + u);
+                g[u] = __ldg(V + cp[j0 + u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (j0 + u < n) acc = fmaf(w[u], g[u], acc);
+    }
+    return acc;
+}
+
+template <typename VT>
+__device__ __forceinline__ float row_dot_global(const int32_t* __restrict__ col, const VT* __restrict__ val, int64_t lo,
+                                                int n, const float* __restrict__ V) {
+    float acc = 0.0f;
+    for (int j0 = 0; j0 < n; j0 += kBatch) {
+        float w[kBatch], g[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (j0 + u < n) {
+                w[u] = ldg_v<VT>(val, lo + j0 + u);
+                g[u] = __ldg(V + __ldg(col + lo + j0 + u));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (j0 + u < n) acc = fmaf(w[u], g[u], acc);
+    }
+    return acc;
+}
+
+struct CsrArgs {
+    int S, A, ts, stages;
+    int64_t ntiles;
+    float gamma;
+    StageLayout L;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+    const float* scale;
+    const float* R;
+    const float* V_in;
+    float* V_out;
+    int32_t* pi;
+    float* qgap;
+};
+
+// ------------------------------------------------------------------ pipelined sweep
+template <typename VT, int APAD>
+__global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepCtl sc) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    constexpr int SPW = 32 / APAD;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + a.stages;
+    unsigned char* stage0 = smem + ((16 * a.stages + 127) & ~127);
+    __shared__ int s_fail;
+    __shared__ int s_consumed;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < a.stages; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kNW);
+        }
+        fence_mbar_init();
+        s_fail = 0;
+        s_consumed = 0x7fffffff;
+    }
+    __syncthreads();
+
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    float res = 0.0f, vabs = 0.0f;
+    int issued = 0;
+    if (warp == kNW) {
+        // ---------------- producer: one lane issues the bulk copies of each tile
+        if (lane == 0) {
+            const uint64_t pol = l2_evict_first();
+            int i = 0;
+            for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
+                const int stg = i % a.stages;
+                if (i >= a.stages && !mbar_wait(&empty[stg], (uint32_t)(((i / a.stages) - 1) & 1))) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                if (*((volatile int*)&s_fail)) break;
+                const int64_t s0 = t * a.ts;
+                const int64_t s1 = (s0 + a.ts < a.S) ? s0 + a.ts : a.S;
+                const int64_t r0 = s0 * a.A, r1 = s1 * a.A;
+                const int64_t e0 = a.row_ptr[r0], e1 = a.row_ptr[r1];
+                unsigned char* base = stage0 + (size_t)stg * a.L.bytes;
+                const uint32_t b_rp = (uint32_t)(((r1 - r0 + 1) + 1) & ~1LL) * 8u;
+                const uint32_t b_R = (uint32_t)(((r1 - r0) + 3) & ~3LL) * 4u;
+                const int64_t c0 = e0 & ~3LL, c1 = (e1 + 3) & ~3LL;
+                const int64_t v0 = (sizeof(VT) == 4) ? c0 : (e0 & ~7LL);
+                const int64_t v1 = (sizeof(VT) == 4) ? c1 : ((e1 + 7) & ~7LL);
+                const uint32_t b_col = (uint32_t)(c1 - c0) * 4u;
+                const uint32_t b_val = (uint32_t)(v1 - v0) * (uint32_t)sizeof(VT);
+                const uint32_t total = b_rp + b_R + (a.scale ? b_R : 0u) + b_col + b_val;
+                mbar_arrive_expect_tx(&full[stg], total);
+                bulk_g2s(base + a.L.off_rp, a.row_ptr + r0, b_rp, &full[stg], pol);
+                bulk_g2s(base + a.L.off_R, a.R + r0, b_R, &full[stg], pol);
+                if (a.scale) bulk_g2s(base + a.L.off_scale, a.scale + r0, b_R, &full[stg], pol);
+                if (b_col) bulk_g2s(base + a.L.off_col, a.col + c0, b_col, &full[stg], pol);
+                if (b_val) bulk_g2s(base + a.L.off_val, val + v0, b_val, &full[stg], pol);
+                issued = i + 1;
+            }
+        }
+    } else {
+        // ---------------- consumers: lanes = rows, APAD lanes per state
+        const int grp = lane / APAD, act = lane % APAD;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
+            const int stg = i % a.stages;
+            if (!mbar_wait(&full[stg], (uint32_t)((i / a.stages) & 1))) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            const unsigned char* base = stage0 + (size_t)stg * a.L.bytes;
+            const int64_t* rp = reinterpret_cast<const int64_t*>(base + a.L.off_rp);
+            const float* Rs = reinterpret_cast<const float*>(base + a.L.off_R);
+            const float* Ss = a.scale ? reinterpret_cast<const float*>(base + a.L.off_scale) : nullptr;
+            const int32_t* cs = reinterpret_cast<const int32_t*>(base + a.L.off_col);
+            const VT* vs = reinterpret_cast<const VT*>(base + a.L.off_val);
+            const int64_t e0 = rp[0];
+            const int64_t c0 = e0 & ~3LL;
+            const int64_t v0 = (sizeof(VT) == 4) ? c0 : (e0 & ~7LL);
+            const int s0 = (int)(t * a.ts);
+            const int ns = (a.S - s0 < a.ts) ? a.S - s0 : a.ts;
+            for (int sb = warp * SPW; sb < ns; sb += kNW * SPW) {
+                const int sl = sb + grp;
+                float q = -INFINITY;
+                if (sl < ns && act < a.A) {
+                    const int rl = sl * a.A + act;
+                    const float rr = Rs[rl];
+                    if (rr != -INFINITY) {
+                        const int64_t lo = rp[rl], hi = rp[rl + 1];
+                        const float acc = row_dot_smem<VT>(cs + (lo - c0), vs + (lo - v0), (int)(hi - lo), a.V_in);
+                        q = rr + a.gamma * (Ss ? Ss[rl] * acc : acc);
+                    }
+                }
+                float b1 = q, b2 = -INFINITY;
+                int ia = (act < a.A) ? act : 0x7fffffff;
+                top2_reduce<APAD>(b1, ia, b2);
+                if (act == 0 && sl < ns) {
+                    const int s = s0 + sl;
+                    if (a.V_out) a.V_out[s] = b1;
+                    if (a.pi) a.pi[s] = ia;
+                    if (a.qgap) a.qgap[s] = (b2 == -INFINITY) ? INFINITY : b1 - b2;
+                    res = fmaxf(res, fabsf(b1 - __ldg(a.V_in + s)));
+                    vabs = fmaxf(vabs, fabsf(b1));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[stg]);
+        }
+        if (lane == 0) atomicMin(&s_consumed, i);
+    }
+    __syncthreads();
+    if (s_fail) {
+        // drain this CTA's copies still in flight before shared memory is released
+        if (warp == kNW && lane == 0) {
+            for (int j = (s_consumed < issued ? s_consumed : issued); j < issued; ++j)
+                mbar_wait(&full[j % a.stages], (uint32_t)((j / a.stages) & 1));
+            atomicOr(&sc.ctl->error, kErrTimeout);
+        }
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<float, (kNW + 1) * 32>(res);
+    vabs = block_max<float, (kNW + 1) * 32>(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
+// ------------------------------------------------------------------- direct fallback
+// Same lane-per-row mapping, rows read from global memory; grid-stride over state groups.
+template <typename VT, int APAD>
+__global__ void __launch_bounds__(kThreads) k_csr_direct(CsrArgs a, SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    constexpr int SPW = 32 / APAD;
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / APAD, act = lane % APAD;
+    const int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * kThreads) >> 5;
+    float res = 0.0f, vabs = 0.0f;
+    for (int sb = warp * SPW; sb < a.S; sb += nwarps * SPW) {
+        const int s = sb + grp;
+        float q = -INFINITY;
+        if (s < a.S && act < a.A) {
+            const int64_t r = (int64_t)s * a.A + act;
+            const float rr = __ldg(a.R + r);
+            if (rr != -INFINITY) {
+                const int64_t lo = __ldg(a.row_ptr + r), hi = __ldg(a.row_ptr + r + 1);
+                const float acc = row_dot_global<VT>(a.col, val, lo, (int)(hi - lo), a.V_in);
+                q = rr + a.gamma * (a.scale ? __ldg(a.scale + r) * acc : acc);
+            }
+        }
+        float b1 = q, b2 = -INFINITY;
+        int ia = (act < a.A) ? act : 0x7fffffff;
+        top2_reduce<APAD>(b1, ia, b2);
+        if (act == 0 && s < a.S) {
+            if (a.V_out) a.V_out[s] = b1;
+            if (a.pi) a.pi[s] = ia;
+            if (a.qgap) a.qgap[s] = (b2 == -INFINITY) ? INFINITY : b1 - b2;
+            res = fmaxf(res, fabsf(b1 - __ldg(a.V_in + s)));
+            vabs = fmaxf(vabs, fabsf(b1));
+        }
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<float, kThreads>(res);
+    vabs = block_max<float, kThreads>(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
+// Very wide action sets (A > 32): warp per state, rows in sequence, warp-reduced sums.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_csr_wide(CsrArgs a, SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * kThreads) >> 5;
+    float res = 0.0f, vabs = 0.0f;
+    for (int s = warp; s < a.S; s += nwarps) {
+        float best = -INFINITY, second = -INFINITY;
+        int arg = -1;
+        for (int act = 0; act < a.A; ++act) {
+            const int64_t r = (int64_t)s * a.A + act;
+            const int64_t lo = __ldg(a.row_ptr + r), hi = __ldg(a.row_ptr + r + 1);
+            float acc = 0.0f;
+            for (int64_t j = lo + lane; j < hi; j += 32) acc = fmaf(ldg_v<VT>(val, j), __ldg(a.V_in + __ldg(a.col + j)), acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            const float rr = __ldg(a.R + r);
+            if (rr == -INFINITY) continue;
+            const float q = rr + a.gamma * (a.scale ? __ldg(a.scale + r) * acc : acc);
+            if (q > best) {
+                second = best;
+                best = q;
+                arg = act;
+            } else if (q > second) {
+                second = q;
+            }
+        }
+        if (lane == 0) {
+            if (a.V_out) a.V_out[s] = best;
+            if (a.pi) a.pi[s] = arg;
+            if (a.qgap) a.qgap[s] = (second == -INFINITY) ? INFINITY : best - second;
+        }
+        res = fmaxf(res, fabsf(best - __ldg(a.V_in + s)));
+        vabs = fmaxf(vabs, fabsf(best));
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<float, kThreads>(res);
+    vabs = block_max<float, kThreads>(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
+// --------------------------------------------------- FP64 / correction kernels (no model)
+template <typename VT>
+__device__ __forceinline__ double row_dot64(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                            const VT* __restrict__ val, const float* __restrict__ scale, int64_t r,
+                                            const double* __restrict__ V) {
+    double acc = 0.0;
+    for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) acc += (double)ldg_v<VT>(val, j) * V[col[j]];
+    if (scale) acc *= (double)scale[r];
+    return acc;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_csr_bellman64(CsrArgs a, double gamma, const double* __restrict__ V_in,
+                                                            double* __restrict__ V_out, int32_t* __restrict__ pi,
+                                                            double* __restrict__ qgap, SweepCtl sc) {
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    double res = 0.0;
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
+        double best = -INFINITY, second = -INFINITY;
+        int arg = -1;
+        for (int act = 0; act < a.A; act++) {
+            const int64_t r = (int64_t)s * a.A + act;
+            const float rr = a.R[r];
+            if (rr == -INFINITY) continue;
+            const double qv = (double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V_in);
+            if (qv > best) {
+                second = best;
+                best = qv;
+                arg = act;
+            } else if (qv > second) {
+                second = qv;
+            }
+        }
+        if (V_out) V_out[s] = best;
+        if (pi) pi[s] = arg;
+        if (qgap) qgap[s] = (second == -INFINITY) ? INFINITY : best - second;
+        res = fmax(res, fabs(best - V_in[s]));
+        if (sc.mode == kModeCert64 && sc.pi_ref && sc.pi_ref[s] != arg) atomicAdd(&sc.ctl->changes, 1ull);
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<double, kThreads>(res);
+    finish_block<double>(sc, res, 0.0, 0);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_csr_eval64(CsrArgs a, double gamma, const int32_t* __restrict__ pi,
+                                                         const double* __restrict__ V_in, double* __restrict__ V_out,
+                                                         SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    double res = 0.0;
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
+        const int act = pi[s];
+        const int64_t r = (int64_t)s * a.A + act;
+        const float rr = (act >= 0 && act < a.A) ? a.R[r] : -INFINITY;
+        if (rr == -INFINITY) {
+            atomicOr(&sc.ctl->error, kErrInfeasiblePolicy);
+            V_out[s] = V_in[s];
+            continue;
+        }
+        const double v = (double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V_in);
+        V_out[s] = v;
+        res = fmax(res, fabs(v - V_in[s]));
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<double, kThreads>(res);
+    finish_block<double>(sc, res, 0.0, sweep);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_csr_resid64(CsrArgs a, double gamma, const int32_t* __restrict__ pi,
+                                                          const double* __restrict__ V, float* __restrict__ r_out,
+                                                          SweepCtl sc) {
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
+        const int act = pi[s];
+        const int64_t r = (int64_t)s * a.A + act;
+        const float rr = (act >= 0 && act < a.A) ? a.R[r] : -INFINITY;
+        if (rr == -INFINITY) {
+            atomicOr(&sc.ctl->error, kErrInfeasiblePolicy);
+            r_out[s] = 0.0f;
+            continue;
+        }
+        r_out[s] = (float)((double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V) - V[s]);
+    }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_csr_correct32(CsrArgs a, const int32_t* __restrict__ pi,
+                                                            const float* __restrict__ rres,
+                                                            const float* __restrict__ e_in, float* __restrict__ e_out,
+                                                            SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    float res = 0.0f, vabs = 0.0f;
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
+        const int act = pi[s];
+        if (act < 0 || act >= a.A) {
+            atomicOr(&sc.ctl->error, kErrInfeasiblePolicy);
+            e_out[s] = e_in[s];
+            continue;
+        }
+        const int64_t r = (int64_t)s * a.A + act;
+        float acc = 0.0f;
+        for (int64_t j = a.row_ptr[r]; j < a.row_ptr[r + 1]; j++) acc = fmaf(ldg_v<VT>(val, j), e_in[a.col[j]], acc);
+        if (a.scale) acc *= a.scale[r];
+        const float v = rres[s] + a.gamma * acc;
+        e_out[s] = v;
+        res = fmaxf(res, fabsf(v - e_in[s]));
+        vabs = fmaxf(vabs, fabsf(v));
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<float, kThreads>(res);
+    vabs = block_max<float, kThreads>(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
+// ------------------------------------------------------------------------- planning
+__global__ void k_tile_cap(const int64_t* __restrict__ row_ptr, int S, int A, int ts, int64_t ntiles,
+                           unsigned long long* out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int64_t s0 = t * ts;
+    const int64_t s1 = (s0 + ts < S) ? s0 + ts : S;
+    atomicMax(out, (unsigned long long)(row_ptr[s1 * A] - row_ptr[s0 * A]));
+}
+
+static int pow2_at_least(int a) {
+    int p = 1;
+    while (p < a) p <<= 1;
+    return p;
+}
+
+// Sets the kernel's dynamic shared memory and returns how many CTAs of it fit on an SM.
+template <typename VT, int APAD>
+static cudaError_t set_tma_smem(int bytes, int* per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_csr_tma<VT, APAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_csr_tma<VT, APAD>, (kNW + 1) * 32, bytes);
+}
+
+template <typename VT>
+static cudaError_t set_tma_smem_any(int apad, int bytes, int* per_sm) {
+    switch (apad) {
+        case 1: return set_tma_smem<VT, 1>(bytes, per_sm);
+        case 2: return set_tma_smem<VT, 2>(bytes, per_sm);
+        case 4: return set_tma_smem<VT, 4>(bytes, per_sm);
+        case 8: return set_tma_smem<VT, 8>(bytes, per_sm);
+        case 16: return set_tma_smem<VT, 16>(bytes, per_sm);
+        default: return set_tma_smem<VT, 32>(bytes, per_sm);
+    }
+}
+
+// Chooses tile size / stages / CTAs per SM of the pipelined sweep: the largest tile that
+// lets two CTAs per SM keep at least two stages each (else one CTA with up to four),
+// measuring the largest tile on the device so any CSR fits.
+int plan_csr(Mdp* m, cudaStream_t st) {
+    CsrPlan& P = m->plan;
+    P = CsrPlan();
+    if (m->A > 32 || (m->fmt & VC_DIRECT)) return VC_OK;
+    P.apad = pow2_at_least(m->A);
+    const int spw = 32 / P.apad;
+    const bool bf16 = (m->fmt & 0xF) == VC_CSR_BF16;
+    const int vt = bf16 ? 2 : 4;
+    int dev = 0, smem_sm = 0, smem_blk = 0;
+    VC_CUDA(cudaGetDevice(&dev));
+    VC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    VC_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    unsigned long long* dcap = nullptr;
+    VC_CUDA(cudaMallocAsync((void**)&dcap, 8, st));
+    struct Cand {
+        int ts;
+        long long cap;
+    };
+    Cand cands[8];
+    int nc = 0;
+    for (int k = 8; k >= 1; k >>= 1) {
+        const int ts = k * kNW * spw;
+        const int64_t nt = ((int64_t)m->S + ts - 1) / ts;
+        VC_CUDA(cudaMemsetAsync(dcap, 0, 8, st));
+        count_launches(1);
+        k_tile_cap<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(m->row_ptr, m->S, m->A, ts, nt, dcap);
+        VC_CUDA(cudaGetLastError());
+        unsigned long long cap = 0;
+        VC_CUDA(cudaMemcpyAsync(&cap, dcap, 8, cudaMemcpyDeviceToHost, st));
+        VC_CUDA(cudaStreamSynchronize(st));
+        cands[nc++] = {ts, (long long)cap + 16};
+    }
+    VC_CUDA(cudaFreeAsync(dcap, st));
+    const int hdr = 128;  // barriers
+    // preference: (CTAs per SM, stages) pairs, most consumer warps and copies in flight first
+    const int prefs[][2] = {{3, 3}, {3, 2}, {2, 3}, {2, 2}, {1, 4}, {1, 3}, {1, 2}};
+    for (auto& pr : prefs) {
+        const int ctas = pr[0], stages = pr[1];
+        const int budget = (smem_sm - 1024 * ctas) / ctas;
+        for (int c = 0; c < nc; c++) {
+            const StageLayout L = stage_layout(cands[c].ts, m->A, cands[c].cap, vt, bf16);
+            const long long need = hdr + (long long)stages * L.bytes;
+            if (need <= budget && need <= smem_blk) {
+                P.tma = true;
+                P.ts = cands[c].ts;
+                P.cap = cands[c].cap;
+                P.stages = stages;
+                P.ctas_per_sm = ctas;
+                P.smem = (int)need;
+                P.ntiles = ((int64_t)m->S + P.ts - 1) / P.ts;
+                int per_sm = 0;
+                cudaError_t e = bf16 ? set_tma_smem_any<uint16_t>(P.apad, P.smem, &per_sm)
+                                     : set_tma_smem_any<float>(P.apad, P.smem, &per_sm);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_csr_tma)");
+                if (per_sm < 1) {
+                    P.tma = false;
+                    return VC_OK;
+                }
+                P.ctas_per_sm = per_sm < ctas ? per_sm : ctas;
+                return VC_OK;
+            }
+        }
+    }
+    return VC_OK;  // nothing fits: the direct kernel is used
+}
+
+// ------------------------------------------------------------------------ launchers
+static CsrArgs args_of(const Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap) {
+    CsrArgs a;
+    a.S = m->S;
+    a.A = m->A;
+    a.ts = m->plan.ts;
+    a.stages = m->plan.stages;
+    a.ntiles = m->plan.ntiles;
+    a.gamma = (float)m->gamma;
+    a.L = stage_layout(m->plan.ts, m->A, m->plan.cap, (m->fmt & 0xF) == VC_CSR_BF16 ? 2 : 4,
+                       (m->fmt & 0xF) == VC_CSR_BF16);
+    a.row_ptr = m->row_ptr;
+    a.col = m->col;
+    a.val = m->val;
+    a.scale = m->scale;
+    a.R = m->R;
+    a.V_in = V_in;
+    a.V_out = V_out;
+    a.pi = pi;
+    a.qgap = qgap;
+    return a;
+}
+
+template <typename VT>
+static void launch_tma(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStream_t st) {
+    const long long cap = (long long)m->num_sms * m->plan.ctas_per_sm;
+    const int grid = (int)(m->plan.ntiles < cap ? m->plan.ntiles : cap);
+    const dim3 blk((kNW + 1) * 32);
+    switch (m->plan.apad) {
+        case 1: k_csr_tma<VT, 1><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 2: k_csr_tma<VT, 2><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 4: k_csr_tma<VT, 4><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 8: k_csr_tma<VT, 8><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 16: k_csr_tma<VT, 16><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        default: k_csr_tma<VT, 32><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+    }
+}
+
+template <typename VT>
+static void launch_direct(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStream_t st) {
+    const int g = state_grid(m);
+    if (m->A > 32) {
+        k_csr_wide<VT><<<g, kThreads, 0, st>>>(a, sc);
+        return;
+    }
+    switch (pow2_at_least(m->A)) {
+        case 1: k_csr_direct<VT, 1><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 2: k_csr_direct<VT, 2><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 4: k_csr_direct<VT, 4><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 8: k_csr_direct<VT, 8><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 16: k_csr_direct<VT, 16><<<g, kThreads, 0, st>>>(a, sc); break;
+        default: k_csr_direct<VT, 32><<<g, kThreads, 0, st>>>(a, sc); break;
+    }
+}
+
+int csr_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st) {
+    const CsrArgs a = args_of(m, V_in, V_out, pi, qgap);
+    const bool bf16 = (m->fmt & 0xF) == VC_CSR_BF16;
+    count_launches(1);
+    if (m->plan.tma) {
+        if (bf16)
+            launch_tma<uint16_t>(m, a, sc, st);
+        else
+            launch_tma<float>(m, a, sc, st);
+    } else {
+        if (bf16)
+            launch_direct<uint16_t>(m, a, sc, st);
+        else
+            launch_direct<float>(m, a, sc, st);
+    }
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+int csr_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double* qgap, SweepCtl sc,
+                  cudaStream_t st) {
+    const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
+    count_launches(1);
+    if ((m->fmt & 0xF) == VC_CSR_BF16)
+        k_csr_bellman64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc);
+    else
+        k_csr_bellman64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc);
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+int csr_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st) {
+    const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
+    count_launches(1);
+    if ((m->fmt & 0xF) == VC_CSR_BF16)
+        k_csr_eval64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V_in, V_out, sc);
+    else
+        k_csr_eval64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V_in, V_out, sc);
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+int csr_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl sc, cudaStream_t st) {
+    const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
+    count_launches(1);
+    if ((m->fmt & 0xF) == VC_CSR_BF16)
+        k_csr_resid64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc);
+    else
+        k_csr_resid64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc);
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+int csr_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_in, float* e_out, SweepCtl sc,
+                  cudaStream_t st) {
+    const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
+    count_launches(1);
+    if ((m->fmt & 0xF) == VC_CSR_BF16)
+        k_csr_correct32<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, pi, r, e_in, e_out, sc);
+    else
+        k_csr_correct32<float><<<state_grid(m), kThreads, 0, st>>>(a, pi, r, e_in, e_out, sc);
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+}  // namespace vc

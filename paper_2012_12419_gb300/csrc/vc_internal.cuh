@@ -13,41 +13,50 @@ namespace vc {
 constexpr int kMaxH = VC_MAX_HOSTS;
 constexpr int kRing = 64;          // residual slots, indexed by sweep number mod kRing
 constexpr int kStallSweeps = 64;   // FP32 sweeps without a new best residual = FP32 floor
+constexpr int kThreads = 256;      // block size of the state-parallel kernels
 
 // ------------------------------------------------------------------ error plumbing
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
-#define VC_CUDA(call)                                  \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
+#define VC_CUDA(call)                                           \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
         if (e_ != cudaSuccess) return vc::cuda_fail(e_, #call); \
     } while (0)
 
 // ------------------------------------------------------- division by a runtime constant
-// q = n / d for 0 <= n < 2^31 and 1 <= d < 2^16 as one 64-bit multiply and a shift:
-// with l = ceil(log2 d), sh = 31 + l and m = floor(2^sh / d) + 1 (m <= 2^32), the error
-// term m*d - 2^sh <= d <= 2^(sh-31) keeps floor(n*m / 2^sh) exact for every n < 2^31
+// q = n / d for 0 <= n < 2^31 and 1 <= d < 2^16 as a multiply-high and a shift: with
+// l = ceil(log2 d), sh = 31 + l and m = floor(2^sh / d) + 1, the error term
+// m*d - 2^sh <= d <= 2^(sh-31) keeps floor(n*m / 2^sh) exact for every n < 2^31
 // (Granlund & Montgomery, "Division by invariant integers using multiplication", 1994).
+// For d >= 2, m < 2^32 and sh >= 32, so the quotient is the high word of the 32x32
+// product shifted by sh - 32; d = 1 returns n.
 struct FastDiv {
-    uint64_t m;
-    uint32_t sh;
+    uint32_t m;
+    uint32_t sh;  // sh - 32
     uint32_t d;
 };
 
 inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    if (d <= 1) {
+        f.m = 0;
+        f.sh = 0;
+        return f;
+    }
     uint32_t l = 0;
     while ((1u << l) < d) l++;
-    FastDiv f;
-    f.sh = 31 + l;
-    f.m = ((uint64_t)1 << f.sh) / d + 1;
-    f.d = d;
+    const uint32_t sh = 31 + l;
+    f.m = (uint32_t)((((uint64_t)1) << sh) / d + 1);
+    f.sh = sh - 32;
     return f;
 }
 
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
-    return (uint32_t)(((uint64_t)n * f.m) >> f.sh);
+    return f.d <= 1 ? n : (__umulhi(n, f.m) >> f.sh);
 }
 
 // --------------------------------------------------------------------- model descriptor
@@ -85,6 +94,8 @@ struct Digits {
     int q, ph;
 };
 
+// MH: a compile-time bound on H (kernels are instantiated for H <= 4, 8, 16).
+template <int MH = kMaxH>
 __device__ __forceinline__ void decode(const Model& md, int s, Digits& d) {
     d.ph = s & 1;
     uint32_t rest = (uint32_t)s >> 1;
@@ -92,7 +103,7 @@ __device__ __forceinline__ void decode(const Model& md, int s, Digits& d) {
     d.q = (int)(rest - t * md.div_q.d);
     rest = t;
 #pragma unroll
-    for (int k = 0; k < kMaxH; k++) {
+    for (int k = 0; k < MH; k++) {
         if (k < md.H) {
             uint32_t t2 = fdiv(rest, md.div_c);
             d.occ[k] = (int)(rest - t2 * md.div_c.d);
@@ -101,6 +112,31 @@ __device__ __forceinline__ void decode(const Model& md, int s, Digits& d) {
             d.occ[k] = 0;
         }
     }
+}
+
+// Post-decision state of action a in s (digits updated in place, static indexing only).
+// Returns false if a is not feasible in s.
+template <int MH = kMaxH>
+__device__ __forceinline__ bool apply_action(const Model& md, int s, int a, Digits& d, int& x) {
+    if (a == md.H) {
+        x = s;
+        return true;
+    }
+    if (a < 0 || a > md.H || d.q < 1) return false;
+    bool ok = false;
+    int step = 0;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k == a && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1)) {
+            d.occ[k] += 1;
+            step = md.stride[k];
+            ok = true;
+        }
+    }
+    if (!ok) return false;
+    d.q -= 1;
+    x = s + step - 2;
+    return true;
 }
 
 // --------------------------------------------------------------------------- control
@@ -131,11 +167,12 @@ constexpr int kErrNegative = 4;
 constexpr int kErrRowSum = 8;
 constexpr int kErrNoFeasible = 16;
 constexpr int kErrRowPtr = 32;
+constexpr int kErrTimeout = 64;
 
 // Bookkeeping mode of a sweep kernel.
 enum SweepMode : int {
     kModeNone = 0,     // plain backup (policy extraction)
-    kModeLoop32 = 1,   // FP32 value-iteration loop: skip when done, residual ring, tolerance / stall
+    kModeLoop32 = 1,   // FP32 loop: skip when done, residual ring, tolerance / stall test
     kModeLoop64 = 2,   // FP64 policy-evaluation loop: skip when done, FP64 residual ring
     kModeCert64 = 3,   // FP64 standalone backup: residual into cert64, policy changes vs pi_ref
 };
@@ -159,7 +196,8 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// Block-wide max of a non-negative value; result valid in thread 0.
+// Block-wide max of a non-negative value over NT threads; result valid in thread 0.
+// Every thread of the block must call it.
 template <typename T, int NT>
 __device__ __forceinline__ T block_max(T v) {
     __shared__ T part[NT / 32];
@@ -172,13 +210,96 @@ __device__ __forceinline__ T block_max(T v) {
         r = (l < NT / 32) ? part[l] : T(0);
         r = warp_max(r);
     }
+    __syncthreads();
     return r;
 }
 
 __device__ __forceinline__ unsigned int fbits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+__device__ __forceinline__ bool loop_done(const SweepCtl& sc) {
+    if (sc.mode != kModeLoop32 && sc.mode != kModeLoop64) return false;
+    return *((volatile int*)&sc.ctl->done) != 0;
+}
+
+__device__ __forceinline__ long long loop_sweep(const SweepCtl& sc) {
+    if (sc.mode != kModeLoop32 && sc.mode != kModeLoop64) return 0;
+    return *((volatile long long*)&sc.ctl->sweeps);
+}
+
+// Residual bookkeeping, called by thread 0 of every block once its block maximum is known.
+// Loop modes: one atomicMax per block into the sweep's ring slot, then the last block to
+// arrive (ticket counter) closes the sweep: advances the sweep count, records the output
+// buffer, clears the next slot and decides termination (tolerance max(tol, 4 ulp(max|V|))
+// for FP32, tol for FP64, FP32 stall, or max_sweeps).  Order independent, so every run
+// takes the same decisions.
+template <typename T>
+__device__ void finish_block(const SweepCtl& sc, T res, T vmax, long long sweep) {
+    if (threadIdx.x != 0 || sc.mode == kModeNone) return;
+    Ctl* c = sc.ctl;
+    if (sc.mode == kModeCert64) {
+        atomicMax(&c->cert64, dbits((double)res));
+        return;
+    }
+    const int slot = (int)(sweep % kRing);
+    if (sc.mode == kModeLoop32) {
+        atomicMax(&c->res32[slot], fbits((float)res));
+        atomicMax(&c->vmax32[slot], fbits((float)vmax));
+    } else {
+        atomicMax(&c->res64[slot], dbits((double)res));
+    }
+    __threadfence();
+    const unsigned int t = atomicAdd(&c->ticket, 1u);
+    if (t != gridDim.x - 1) return;
+    __threadfence();
+    const long long k = sweep + 1;
+    c->ticket = 0;
+    c->sweeps = k;
+    c->final_buf = sc.out_index;
+    const int next = (int)(k % kRing);
+    int done = 0;
+    if (sc.mode == kModeLoop32) {
+        const float r = __uint_as_float(*((volatile unsigned int*)&c->res32[slot]));
+        const float vm = __uint_as_float(*((volatile unsigned int*)&c->vmax32[slot]));
+        c->res32[next] = 0u;
+        c->vmax32[next] = 0u;
+        int e = 0;
+        frexpf(vm, &e);
+        const double ulp = (vm > 0.0f) ? ldexp(1.0, e - 24) : 0.0;
+        const double tol_eff = fmax(c->tol, 4.0 * ulp);
+        if ((double)r < tol_eff) {
+            done = 1;
+        } else if (r < c->best_res) {
+            c->best_res = r;
+            c->since_best = 0;
+        } else if (++c->since_best >= kStallSweeps) {
+            done = 3;
+        }
+    } else {
+        const double r = __longlong_as_double((long long)*((volatile unsigned long long*)&c->res64[slot]));
+        c->res64[next] = 0ull;
+        if (r < c->tol) done = 1;
+    }
+    if (!done && k >= c->max_sweeps) done = 2;
+    if (*((volatile int*)&c->error) & kErrTimeout) done = 4;
+    c->done = done;
+    __threadfence();
+}
+
 // ---------------------------------------------------------------------------- handle
+// Tiling of the pipelined CSR sweep: tiles of `ts` consecutive states whose rows (and
+// entries, at most `cap`) are staged in shared memory by bulk asynchronous copies.
+struct CsrPlan {
+    bool tma = false;
+    int apad = 8;        // lanes per state (power of two >= A)
+    int ts = 0;          // states per tile
+    int64_t cap = 0;     // max entries of a tile (+ alignment slack)
+    int stages = 0;
+    int ctas_per_sm = 0;
+    int smem = 0;        // dynamic shared memory per CTA
+    int64_t ntiles = 0;
+};
+
 struct Mdp {
     int fmt;              // VC_IMPLICIT / VC_CSR_F32 / VC_CSR_BF16 (| VC_PADDED)
     bool has_model;
@@ -188,19 +309,23 @@ struct Mdp {
     Rates rates;
     Coef<float> c32;
     Coef<double> c64;
-    // explicit CSR (owned)
+    // explicit CSR (owned; col / val / R / scale carry 16-byte tail padding for bulk copies)
     int64_t nnz_stored = 0, nnz_logical = 0, feasible_rows = 0;
     int64_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     void* val = nullptr;        // float or uint16 (bf16)
     float* scale = nullptr;     // BF16 per-row scale
     float* R = nullptr;         // [S*A], -inf = infeasible
+    CsrPlan plan;
     // work buffers (owned)
     float* Vb = nullptr;        // FP32 ping-pong partner
     float* U32 = nullptr;       // FP32 post-decision values (implicit)
     double* U64 = nullptr;      // FP64 post-decision values
-    double* V64a = nullptr;     // FP64 ping-pong pair
+    double* V64a = nullptr;     // FP64 pair
     double* V64b = nullptr;
+    float* E0 = nullptr;        // FP32 correction ping-pong
+    float* E1 = nullptr;
+    float* Rres = nullptr;      // FP32 copy of the FP64 policy residual
     int32_t* pi = nullptr;      // policy under refinement
     int32_t* pi2 = nullptr;
     Ctl* ctl = nullptr;         // device control block
@@ -219,6 +344,10 @@ int build_csr_from_model(Mdp* m, cudaStream_t st);
 int count_model_rows(Mdp* m, cudaStream_t st);
 int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
                    const float* row_scale, const float* R, cudaStream_t st);
+int plan_csr(Mdp* m, cudaStream_t st);
+
+// Grid of the persistent state-parallel kernels.
+int state_grid(const Mdp* m);
 
 // One FP32 Bellman backup V_in -> V_out (implicit or CSR), optional policy / gap.
 int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc,
@@ -228,7 +357,22 @@ int launch_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, dou
                      cudaStream_t st);
 // One FP64 policy-evaluation sweep over the chosen rows.
 int launch_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st);
-// Elementwise helpers.
+// r = (R_pi + gamma P_pi V64) - V64 in FP64, stored as float (policy residual).
+int launch_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl sc, cudaStream_t st);
+// One FP32 correction sweep e_out = r + gamma P_pi e_in.
+int launch_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_in, float* e_out, SweepCtl sc,
+                     cudaStream_t st);
+// V64 += e (FP64 add of the FP32 correction).
+int launch_axpy64(double* V64, const float* e, int n, cudaStream_t st);
 int launch_f32_to_f64(const float* in, double* out, int n, cudaStream_t st);
+
+// CSR kernels (vc_csr.cu).
+int csr_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st);
+int csr_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double* qgap, SweepCtl sc,
+                  cudaStream_t st);
+int csr_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st);
+int csr_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl sc, cudaStream_t st);
+int csr_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_in, float* e_out, SweepCtl sc,
+                  cudaStream_t st);
 
 }  // namespace vc

@@ -28,6 +28,7 @@ VC_IMPLICIT = 0
 VC_CSR_F32 = 1
 VC_CSR_BF16 = 2
 VC_PADDED = 16
+VC_DIRECT = 32
 VC_VAL_F32 = 0
 VC_VAL_BF16 = 1
 VC_ITER_FP32_ONLY = 1
@@ -165,10 +166,11 @@ class MDP:
 
     # ------------------------------------------------------------------ construction
     @classmethod
-    def build(cls, params: dict, fmt: str = "implicit", padded: bool = False, stream=None) -> "MDP":
+    def build(cls, params: dict, fmt: str = "implicit", padded: bool = False, direct: bool = False,
+              stream=None) -> "MDP":
         L = load()
         _dev()
-        code = FORMATS[fmt] | (VC_PADDED if padded else 0)
+        code = FORMATS[fmt] | (VC_PADDED if padded else 0) | (VC_DIRECT if direct else 0)
         cp, keep = _params(params)
         h = ctypes.c_void_p()
         _check(L.vc_build_mdp(ctypes.byref(cp), code, _stream(stream), ctypes.byref(h)))
