@@ -48,10 +48,16 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOAD_DESC))
     ap.add_argument("--form", default="csr_f32", choices=["csr_f32", "csr_bf16", "implicit"])
-    ap.add_argument("--padded", action="store_true")
+    ap.add_argument("--layout", default="padded", choices=["padded", "canonical"],
+                    help="padded: every row holds 2H+3 entries (340,000,000 per sweep on the large MDP, the "
+                         "workload's stated CSR size); canonical: only non-zero successors (130,468,750)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and the variants")
-    return ap.parse_args()
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default CSR schedule (profiling runs: no tuning launches before the timed ones)")
+    args = ap.parse_args()
+    args.padded = args.layout == "padded" and args.form != "implicit"
+    return args
 
 
 def peaks():
@@ -137,6 +143,8 @@ def run_native(args):
     m = native.MDP.build(p, fmt=args.form, padded=args.padded)
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t0) * 1e3
+    tune_us = m.autotune(reps=5) if (args.form != "implicit" and not args.no_autotune) else None
+    tune_report = m.autotune_report() if tune_us is not None else None
     info = m.info()
     S = int(info["S"])
     nnz = int(info["nnz_logical"])
@@ -207,6 +215,8 @@ def run_native(args):
         "certified": all(s["certified"] == 1 for s in stats),
         "residual64": max(s["residual64"] for s in stats),
         "build_ms": build_ms,
+        "autotuned_sweep_us": tune_us,
+        "autotune": tune_report.strip().splitlines() if tune_report else None,
         "gpu_launches": int(launches),
         "region_wall_s": region_s,
         "clocks": ck,
@@ -251,7 +261,9 @@ def roofline(m, info, args, V, dev, stream):
     implicit = args.form == "implicit"
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_post+k_max" if implicit else "k_csr32",
-            "bytes_per_launch": int(info["sweep_bytes"]), "launch_us": avg_s * 1e6}
+            "bytes_per_launch": int(info["sweep_bytes"]), "launch_us": avg_s * 1e6,
+            "plan": {k: int(info[k]) for k in ("csr_pipelined", "csr_tile_states", "csr_stages", "csr_ctas_per_sm",
+                                                "csr_smem_bytes")}}
 
 
 def e2e(args, p, native, torch, nnz):
@@ -285,11 +297,13 @@ def e2e(args, p, native, torch, nnz):
 def variants(args, p, native, torch, dev, stream):
     """The other storage forms of the same workload, same step, device-timed."""
     out = {}
-    forms = [("implicit", False), ("csr_f32", True), ("csr_bf16", False)]
+    forms = [("implicit", False), ("csr_f32", False), ("csr_f32", True), ("csr_bf16", False), ("csr_bf16", True)]
     for form, padded in forms:
         if form == args.form and padded == args.padded:
             continue
         m = native.MDP.build(p, fmt=form, padded=padded)
+        if form != "implicit":
+            m.autotune(reps=5)
         info = m.info()
         V = torch.zeros(info["S"], dtype=torch.float32, device=dev)
         for _ in range(2):

@@ -91,7 +91,11 @@ typedef struct vc_info {
     int64_t device_bytes;   /* device memory owned by the handle */
     int64_t sweep_bytes;    /* algorithmic HBM bytes of one FP32 sweep */
     int32_t has_model;      /* 1 if built from vc_params (exact FP64 P available) */
-    int32_t reserved;
+    int32_t csr_pipelined;  /* 1 if CSR sweeps stage tiles through shared memory */
+    int32_t csr_tile_states;/* states per staged tile */
+    int32_t csr_stages;     /* tiles in flight per CTA */
+    int32_t csr_ctas_per_sm;/* resident CTAs per SM of the CSR sweep */
+    int32_t csr_smem_bytes; /* dynamic shared memory per CTA */
 } vc_info;
 
 /* Statistics of vc_value_iterate (host struct, filled on return). */
@@ -203,6 +207,23 @@ int vc_bellman64(vc_mdp* m, const double* V, double* V_out, int32_t* pi, double*
  */
 int vc_evaluate_policy(vc_mdp* m, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
                        int64_t* sweeps_out, void* stream);
+
+/*
+ * Autotuner of the CSR sweep schedule: times every feasible shared-memory tiling (states
+ * per tile, pipeline stages, CTAs per SM) and the direct-load kernel on this handle, reps
+ * sweeps each on `stream`, and keeps the fastest for later sweeps.  *best_us (host,
+ * nullable) receives its time per sweep.  No-op for VC_IMPLICIT handles.  The schedule
+ * never changes results: every candidate does the same arithmetic in the same order.
+ */
+int vc_autotune(vc_mdp* m, int reps, double* best_us, void* stream);
+
+/*
+ * Text table of the last vc_autotune on this handle (one line per candidate: kernel,
+ * states per tile, stages, CTAs per SM, shared memory bytes, microseconds per sweep)
+ * copied into the host buffer buf of len bytes, NUL-terminated and truncated to fit.
+ * Returns the length needed including the NUL (1 if the handle was never tuned).
+ */
+int64_t vc_autotune_report(const vc_mdp* m, char* buf, int64_t len);
 
 /* Release a handle and all device memory it owns (NULL is a no-op). */
 int vc_destroy(vc_mdp* m);

@@ -260,6 +260,11 @@ int vc_mdp_info(const vc_mdp* mh, vc_info* out) {
     out->feasible_rows = m->feasible_rows;
     out->device_bytes = m->device_bytes;
     out->has_model = m->has_model ? 1 : 0;
+    out->csr_pipelined = m->plan.tma ? 1 : 0;
+    out->csr_tile_states = m->plan.ts;
+    out->csr_stages = m->plan.stages;
+    out->csr_ctas_per_sm = m->plan.ctas_per_sm;
+    out->csr_smem_bytes = m->plan.smem;
     const int64_t rows = (int64_t)m->S * m->A;
     const int base = m->fmt & 0xF;
     if (base == VC_IMPLICIT)
@@ -287,6 +292,28 @@ int vc_mdp_export_csr(const vc_mdp* mh, int64_t* row_ptr, int32_t* col, void* va
     if (row_scale && m->scale) VC_CUDA(cudaMemcpyAsync(row_scale, m->scale, 4 * rows, cudaMemcpyDeviceToDevice, st));
     if (R) VC_CUDA(cudaMemcpyAsync(R, m->R, 4 * rows, cudaMemcpyDeviceToDevice, st));
     return VC_OK;
+}
+
+int vc_autotune(vc_mdp* mh, int reps, double* best_us, void* stream) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    Mdp* m = (Mdp*)mh;
+    if ((m->fmt & 0xF) == VC_IMPLICIT) {
+        if (best_us) *best_us = 0.0;
+        return VC_OK;
+    }
+    return autotune_csr(m, reps, (cudaStream_t)stream, best_us);
+}
+
+int64_t vc_autotune_report(const vc_mdp* mh, char* buf, int64_t len) {
+    if (!mh) return 0;
+    const std::string& r = ((const Mdp*)mh)->tune_report;
+    if (buf && len > 0) {
+        const int64_t n = std::min<int64_t>(len - 1, (int64_t)r.size());
+        memcpy(buf, r.data(), (size_t)n);
+        buf[n] = 0;
+    }
+    return (int64_t)r.size() + 1;
 }
 
 int vc_destroy(vc_mdp* mh) {

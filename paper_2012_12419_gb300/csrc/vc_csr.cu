@@ -16,6 +16,9 @@
 // Fallback, k_csr_direct: the same row mapping reading rows straight from global memory,
 // for tiles that do not fit in shared memory (very long rows) or A > 32.
 #include <math.h>
+#include <stdio.h>
+
+#include <vector>
 
 #include "vc_internal.cuh"
 
@@ -58,7 +61,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (long long it = 0; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (it >= 8) __nanosleep(128);
+        if (it >= 32) __nanosleep(64);
     }
     return false;
 }
@@ -134,10 +137,10 @@ __device__ __forceinline__ void top2_reduce(float& b1, int& ia, float& b2) {
     }
 }
 
-// Dot product of one stored row with V, in column order.  Entries go in batches of
-// kBatch: every gather of a batch is issued before the first multiply-add, so a row of up
-// to kBatch successors costs one L2 round trip instead of one per entry; the adds stay in
-// column order (identical results to the sequential loop).
+// Dot product of one stored row with V, fused multiply-adds in column order (the
+// arithmetic of every CSR sweep kernel, so their results agree bitwise).  Entries go in
+// batches of kBatch: every gather of a batch is issued before the first multiply-add, so
+// a row of up to kBatch successors costs one memory round trip.
 constexpr int kBatch = 16;
 
 template <typename VT>
@@ -226,8 +229,20 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
         // ---------------- producer: one lane issues the bulk copies of each tile
         if (lane == 0) {
             const uint64_t pol = l2_evict_first();
+            // entry bounds of a tile; the next tile's are loaded one iteration ahead so
+            // their latency overlaps the wait for a free stage
+            auto bounds = [&](int64_t t, int64_t& e0, int64_t& e1) {
+                const int64_t s0 = t * a.ts;
+                const int64_t s1 = (s0 + a.ts < a.S) ? s0 + a.ts : a.S;
+                e0 = a.row_ptr[s0 * a.A];
+                e1 = a.row_ptr[s1 * a.A];
+            };
+            int64_t ne0 = 0, ne1 = 0;
+            if (blockIdx.x < a.ntiles) bounds(blockIdx.x, ne0, ne1);
             int i = 0;
             for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
+                const int64_t e0 = ne0, e1 = ne1;
+                if (t + gridDim.x < a.ntiles) bounds(t + gridDim.x, ne0, ne1);
                 const int stg = i % a.stages;
                 if (i >= a.stages && !mbar_wait(&empty[stg], (uint32_t)(((i / a.stages) - 1) & 1))) {
                     atomicExch(&s_fail, 1);
@@ -237,7 +252,6 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
                 const int64_t s0 = t * a.ts;
                 const int64_t s1 = (s0 + a.ts < a.S) ? s0 + a.ts : a.S;
                 const int64_t r0 = s0 * a.A, r1 = s1 * a.A;
-                const int64_t e0 = a.row_ptr[r0], e1 = a.row_ptr[r1];
                 unsigned char* base = stage0 + (size_t)stg * a.L.bytes;
                 const uint32_t b_rp = (uint32_t)(((r1 - r0 + 1) + 1) & ~1LL) * 8u;
                 const uint32_t b_R = (uint32_t)(((r1 - r0) + 3) & ~3LL) * 4u;
@@ -257,7 +271,9 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
             }
         }
     } else {
-        // ---------------- consumers: lanes = rows, APAD lanes per state
+        // ---------------- consumers: lanes = rows, APAD lanes per state.  Four consecutive
+        // states x A actions per warp step keep the V gathers of one load instruction
+        // within a few cache lines (same successor offsets, adjacent states).
         const int grp = lane / APAD, act = lane % APAD;
         int i = 0;
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
@@ -543,35 +559,55 @@ static int pow2_at_least(int a) {
     return p;
 }
 
-// Sets the kernel's dynamic shared memory and returns how many CTAs of it fit on an SM.
+// Dynamic shared memory limit of a kernel instance, and how many CTAs fit on an SM.
+// `bytes` is the per-block opt-in limit; the kernel's static shared memory comes off it.
+// *dyn_limit receives the dynamic amount actually allowed.
 template <typename VT, int APAD>
-static cudaError_t set_tma_smem(int bytes, int* per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_csr_tma<VT, APAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+static cudaError_t set_tma_smem(int bytes, int* dyn_limit) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_csr_tma<VT, APAD>);
     if (e != cudaSuccess) return e;
+    *dyn_limit = bytes - (int)fa.sharedSizeBytes;
+    return cudaFuncSetAttribute(k_csr_tma<VT, APAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_limit);
+}
+
+template <typename VT, int APAD>
+static cudaError_t tma_occupancy(int bytes, int* per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_csr_tma<VT, APAD>, (kNW + 1) * 32, bytes);
 }
 
 template <typename VT>
-static cudaError_t set_tma_smem_any(int apad, int bytes, int* per_sm) {
+static cudaError_t set_tma_smem_any(int apad, int bytes, int* dyn_limit) {
     switch (apad) {
-        case 1: return set_tma_smem<VT, 1>(bytes, per_sm);
-        case 2: return set_tma_smem<VT, 2>(bytes, per_sm);
-        case 4: return set_tma_smem<VT, 4>(bytes, per_sm);
-        case 8: return set_tma_smem<VT, 8>(bytes, per_sm);
-        case 16: return set_tma_smem<VT, 16>(bytes, per_sm);
-        default: return set_tma_smem<VT, 32>(bytes, per_sm);
+        case 1: return set_tma_smem<VT, 1>(bytes, dyn_limit);
+        case 2: return set_tma_smem<VT, 2>(bytes, dyn_limit);
+        case 4: return set_tma_smem<VT, 4>(bytes, dyn_limit);
+        case 8: return set_tma_smem<VT, 8>(bytes, dyn_limit);
+        case 16: return set_tma_smem<VT, 16>(bytes, dyn_limit);
+        default: return set_tma_smem<VT, 32>(bytes, dyn_limit);
     }
 }
 
-// Chooses tile size / stages / CTAs per SM of the pipelined sweep: the largest tile that
-// lets two CTAs per SM keep at least two stages each (else one CTA with up to four),
-// measuring the largest tile on the device so any CSR fits.
-int plan_csr(Mdp* m, cudaStream_t st) {
-    CsrPlan& P = m->plan;
-    P = CsrPlan();
+template <typename VT>
+static cudaError_t tma_occupancy_any(int apad, int bytes, int* per_sm) {
+    switch (apad) {
+        case 1: return tma_occupancy<VT, 1>(bytes, per_sm);
+        case 2: return tma_occupancy<VT, 2>(bytes, per_sm);
+        case 4: return tma_occupancy<VT, 4>(bytes, per_sm);
+        case 8: return tma_occupancy<VT, 8>(bytes, per_sm);
+        case 16: return tma_occupancy<VT, 16>(bytes, per_sm);
+        default: return tma_occupancy<VT, 32>(bytes, per_sm);
+    }
+}
+
+// Candidate tilings of the pipelined sweep, in preference order: (CTAs per SM, stages)
+// pairs with the most consumer warps and copies in flight first, largest tile first; the
+// largest tile of each size is measured on the device so any CSR fits.
+static int enumerate_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
+    out.clear();
     if (m->A > 32 || (m->fmt & VC_DIRECT)) return VC_OK;
-    P.apad = pow2_at_least(m->A);
-    const int spw = 32 / P.apad;
+    const int apad = pow2_at_least(m->A);
+    const int spw = 32 / apad;
     const bool bf16 = (m->fmt & 0xF) == VC_CSR_BF16;
     const int vt = bf16 ? 2 : 4;
     int dev = 0, smem_sm = 0, smem_blk = 0;
@@ -584,10 +620,11 @@ int plan_csr(Mdp* m, cudaStream_t st) {
         int ts;
         long long cap;
     };
-    Cand cands[8];
-    int nc = 0;
-    for (int k = 8; k >= 1; k >>= 1) {
-        const int ts = k * kNW * spw;
+    std::vector<Cand> cands;
+    // tiles of 8, 4, 2, 1 and 1/2 state rows of the consumer warps (multiples of 4 states)
+    for (int k2 = 16; k2 >= 1; k2 >>= 1) {
+        const int ts = k2 * kNW * spw / 2;
+        if (ts < 4 || ts % 4) continue;
         const int64_t nt = ((int64_t)m->S + ts - 1) / ts;
         VC_CUDA(cudaMemsetAsync(dcap, 0, 8, st));
         count_launches(1);
@@ -596,40 +633,51 @@ int plan_csr(Mdp* m, cudaStream_t st) {
         unsigned long long cap = 0;
         VC_CUDA(cudaMemcpyAsync(&cap, dcap, 8, cudaMemcpyDeviceToHost, st));
         VC_CUDA(cudaStreamSynchronize(st));
-        cands[nc++] = {ts, (long long)cap + 16};
+        cands.push_back({ts, (long long)cap + 16});
     }
     VC_CUDA(cudaFreeAsync(dcap, st));
+    // one attribute per kernel instance: allow the largest request, launches ask for less
+    int dyn_limit = 0;
+    cudaError_t e = bf16 ? set_tma_smem_any<uint16_t>(apad, smem_blk, &dyn_limit)
+                         : set_tma_smem_any<float>(apad, smem_blk, &dyn_limit);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_csr_tma)");
+    smem_blk = dyn_limit;
     const int hdr = 128;  // barriers
-    // preference: (CTAs per SM, stages) pairs, most consumer warps and copies in flight first
-    const int prefs[][2] = {{3, 3}, {3, 2}, {2, 3}, {2, 2}, {1, 4}, {1, 3}, {1, 2}};
+    const int prefs[][2] = {{4, 3}, {4, 2}, {3, 3}, {3, 2}, {2, 3}, {2, 2}, {1, 4}, {1, 3}, {1, 2}};
     for (auto& pr : prefs) {
         const int ctas = pr[0], stages = pr[1];
         const int budget = (smem_sm - 1024 * ctas) / ctas;
-        for (int c = 0; c < nc; c++) {
-            const StageLayout L = stage_layout(cands[c].ts, m->A, cands[c].cap, vt, bf16);
+        for (const Cand& c : cands) {
+            const StageLayout L = stage_layout(c.ts, m->A, c.cap, vt, bf16);
             const long long need = hdr + (long long)stages * L.bytes;
-            if (need <= budget && need <= smem_blk) {
-                P.tma = true;
-                P.ts = cands[c].ts;
-                P.cap = cands[c].cap;
-                P.stages = stages;
-                P.ctas_per_sm = ctas;
-                P.smem = (int)need;
-                P.ntiles = ((int64_t)m->S + P.ts - 1) / P.ts;
-                int per_sm = 0;
-                cudaError_t e = bf16 ? set_tma_smem_any<uint16_t>(P.apad, P.smem, &per_sm)
-                                     : set_tma_smem_any<float>(P.apad, P.smem, &per_sm);
-                if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_csr_tma)");
-                if (per_sm < 1) {
-                    P.tma = false;
-                    return VC_OK;
-                }
-                P.ctas_per_sm = per_sm < ctas ? per_sm : ctas;
-                return VC_OK;
-            }
+            if (need > budget || need > smem_blk) continue;
+            int per_sm = 0;
+            e = bf16 ? tma_occupancy_any<uint16_t>(apad, (int)need, &per_sm)
+                     : tma_occupancy_any<float>(apad, (int)need, &per_sm);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+            if (per_sm < 1) continue;
+            CsrPlan P;
+            P.tma = true;
+            P.apad = apad;
+            P.ts = c.ts;
+            P.cap = c.cap;
+            P.stages = stages;
+            P.ctas_per_sm = per_sm < ctas ? per_sm : ctas;
+            P.smem = (int)need;
+            P.ntiles = ((int64_t)m->S + P.ts - 1) / P.ts;
+            out.push_back(P);
         }
     }
-    return VC_OK;  // nothing fits: the direct kernel is used
+    return VC_OK;
+}
+
+// Default plan: the first candidate (the direct kernel if none fits).
+int plan_csr(Mdp* m, cudaStream_t st) {
+    std::vector<CsrPlan> cands;
+    int rc = enumerate_plans(m, st, cands);
+    if (rc) return rc;
+    m->plan = cands.empty() ? CsrPlan() : cands.front();
+    return VC_OK;
 }
 
 // ------------------------------------------------------------------------ launchers
@@ -749,6 +797,52 @@ int csr_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_in, 
     else
         k_csr_correct32<float><<<state_grid(m), kThreads, 0, st>>>(a, pi, r, e_in, e_out, sc);
     VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+// Times every candidate tiling (and the direct kernel) on this handle and keeps the
+// fastest: reps FP32 sweeps each after two warm-up sweeps, CUDA events on `st`.
+int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
+    std::vector<CsrPlan> cands;
+    int rc = enumerate_plans(m, st, cands);
+    if (rc) return rc;
+    cands.push_back(CsrPlan());  // direct kernel
+    if (reps < 1) reps = 1;
+    float* A = m->Vb;
+    float* B = m->E0;
+    VC_CUDA(cudaMemsetAsync(A, 0, 4 * (size_t)m->S, st));
+    cudaEvent_t e0, e1;
+    VC_CUDA(cudaEventCreate(&e0));
+    VC_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    CsrPlan chosen = cands.front();
+    m->tune_report = "kernel tile_states stages ctas_per_sm smem_bytes us_per_sweep\n";
+    for (const CsrPlan& P : cands) {
+        m->plan = P;
+        SweepCtl none{m->ctl, kModeNone, 0, nullptr};
+        for (int w = 0; w < 2; w++)
+            if ((rc = csr_sweep32(m, A, B, nullptr, nullptr, none, st))) return rc;
+        VC_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < reps; r++)
+            if ((rc = csr_sweep32(m, (r & 1) ? B : A, (r & 1) ? A : B, nullptr, nullptr, none, st))) return rc;
+        VC_CUDA(cudaEventRecord(e1, st));
+        VC_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        VC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double us = 1e3 * ms / reps;
+        char line[160];
+        snprintf(line, sizeof(line), "%s %d %d %d %d %.2f\n", P.tma ? "pipelined" : "direct", P.ts, P.stages,
+                 P.ctas_per_sm, P.smem, us);
+        m->tune_report += line;
+        if (us < best) {
+            best = us;
+            chosen = P;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->plan = chosen;
+    if (best_us) *best_us = best;
     return VC_OK;
 }
 

@@ -317,6 +317,7 @@ struct Mdp {
     float* scale = nullptr;     // BF16 per-row scale
     float* R = nullptr;         // [S*A], -inf = infeasible
     CsrPlan plan;
+    std::string tune_report;    // candidates and times of the last autotune
     // work buffers (owned)
     float* Vb = nullptr;        // FP32 ping-pong partner
     float* U32 = nullptr;       // FP32 post-decision values (implicit)
@@ -345,6 +346,7 @@ int count_model_rows(Mdp* m, cudaStream_t st);
 int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
                    const float* row_scale, const float* R, cudaStream_t st);
 int plan_csr(Mdp* m, cudaStream_t st);
+int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us);
 
 // Grid of the persistent state-parallel kernels.
 int state_grid(const Mdp* m);

@@ -37,7 +37,7 @@ FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF
 
 EXPORTS = [
     "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
-    "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches",
+    "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report",
 ]
 
 
@@ -61,7 +61,8 @@ class Info(ctypes.Structure):
         ("S", ctypes.c_int64), ("A", ctypes.c_int32), ("fmt", ctypes.c_int32),
         ("nnz_logical", ctypes.c_int64), ("nnz_stored", ctypes.c_int64), ("feasible_rows", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64), ("sweep_bytes", ctypes.c_int64),
-        ("has_model", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("has_model", ctypes.c_int32), ("csr_pipelined", ctypes.c_int32), ("csr_tile_states", ctypes.c_int32),
+        ("csr_stages", ctypes.c_int32), ("csr_ctas_per_sm", ctypes.c_int32), ("csr_smem_bytes", ctypes.c_int32),
     ]
 
 
@@ -110,10 +111,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_mdp_export_csr.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.vc_bellman32.argtypes = [vp, vp, vp, vp, vp, vp]
         L.vc_kernel_launches.argtypes = []
+        L.vc_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dbl), vp]
+        L.vc_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
         for name in EXPORTS:
-            if name not in ("vc_last_error", "vc_kernel_launches"):
+            if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
         L.vc_kernel_launches.restype = ctypes.c_int64
+        L.vc_autotune_report.restype = ctypes.c_int64
         _lib = L
         return _lib
 
@@ -245,6 +249,21 @@ class MDP:
         gap = torch.empty(self.S, dtype=torch.float32, device=dev)
         _check(load().vc_extract_policy(self._h, _ptr(V), _ptr(pi), _ptr(gap), _stream(stream)))
         return pi, gap
+
+    def autotune(self, reps: int = 5, stream=None) -> float:
+        """Time the CSR sweep schedules on this instance and keep the fastest (us per sweep)."""
+        us = ctypes.c_double()
+        _check(load().vc_autotune(self._h, int(reps), ctypes.byref(us), _stream(stream)))
+        self._info = None
+        return us.value
+
+    def autotune_report(self) -> str:
+        """Candidates and times of the last autotune, one line each."""
+        L = load()
+        n = L.vc_autotune_report(self._h, None, 0)
+        buf = ctypes.create_string_buffer(int(n))
+        L.vc_autotune_report(self._h, buf, int(n))
+        return buf.value.decode()
 
     def bellman32(self, V, V_out=None, pi=None, qgap=None, stream=None):
         """One FP32 Bellman sweep (outputs optional, preallocated CUDA tensors)."""
