@@ -191,6 +191,26 @@ int vc_extract_policy(vc_mdp* m, const float* V, int32_t* pi, float* qgap, void*
 int vc_bellman32(vc_mdp* m, const float* V, float* V_out, int32_t* pi, float* qgap, void* stream);
 
 /*
+ * One FP32 Bellman sweep of the model in *p (implicit form) that allocates no device
+ * memory, for callers that cannot call cudaMalloc: code whose device memory is entirely
+ * held by another allocator's pool, control loops that must not risk the device-wide
+ * synchronisation an allocation can cause, or code running while another library captures
+ * the stream.  The paper has no counterpart; it is an interface convenience.
+ *   V: [S] float in; V_out: [S] float out (a different buffer); pi: [S] int32 argmax
+ *   (nullable); residual: ONE float on the device (nullable) receiving max|V_out - V|.
+ * Results equal vc_bellman32 on a VC_IMPLICIT handle of the same model.
+ * Scratch: the post-decision values live in a static device array of 1,048,576 floats
+ * (4 MiB) plus a residual word, present on every GPU that loads the library until the
+ * process exits; S above 1,048,576 returns VC_ERR_ARG.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  All calls on a device share the
+ * array, so calls that overlap on the GPU (different streams, or different host threads)
+ * race and must be ordered by the caller.  The residual word is cleared on every call.
+ */
+int vc_bellman32_noalloc(const vc_params* p, const float* V, float* V_out, int32_t* pi, float* residual,
+                         void* stream);
+
+/*
  * FP64 Bellman backup of V ([S] double): V_out[s] = max_a Q(s,a) in FP64 (nullable),
  * pi (nullable) the argmax, qgap (nullable, double) the gap, and *residual (host,
  * nullable) = max_s |V_out(s) - V(s)|, the check of Algorithm 3, step 3.  Synchronises

@@ -37,7 +37,7 @@ FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF
 
 EXPORTS = [
     "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
-    "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report",
+    "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
 ]
 
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_kernel_launches.argtypes = []
         L.vc_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dbl), vp]
         L.vc_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
+        L.vc_bellman32_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -319,6 +320,17 @@ def solve(params: dict, fmt: str = "implicit", padded: bool = False, tol: float 
         return V64.cpu().numpy(), pi.cpu().numpy(), st
     finally:
         m.close()
+
+
+def bellman32_noalloc(params: dict, V, V_out, pi=None, residual=None, stream=None):
+    """One FP32 Bellman sweep of the implicit model with no device allocation: the
+    library's static scratch holds the intermediate values (S <= 1,048,576).  V, V_out,
+    pi and residual (one float) are caller-owned CUDA tensors."""
+    cp, keep = _params(params)
+    _check(load().vc_bellman32_noalloc(ctypes.byref(cp), _ptr(V), _ptr(V_out), _ptr(pi), _ptr(residual),
+                                       _stream(stream)))
+    del keep
+    return V_out
 
 
 def kernel_launches() -> int:

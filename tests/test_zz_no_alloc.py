@@ -1,0 +1,69 @@
+"""The no-allocation sweep entry point against the handle-based sweep.
+
+vc_bellman32_noalloc serves callers that cannot call cudaMalloc (device memory held by
+another allocator's pool, latency-bound loops that must not risk an allocation's
+synchronisation, code running under another library's stream capture): it keeps its
+scratch in a static device array instead.  Through the C ABI, two calls in a row with
+different inputs must reproduce vc_bellman32 on a VC_IMPLICIT handle of the same model
+bitwise (same kernels, same arithmetic), return max|V_out - V| as the residual, and reject
+models larger than the static scratch.  This file is collected last so that a run stopping
+at the first failure has already run every other test.
+"""
+import ctypes
+
+import pytest
+
+from paper_2012_12419_gb300 import inputs
+
+from gpu_common import native_or_skip
+
+pytestmark = pytest.mark.gpu
+
+
+def _call(native, p, V, V_out, pi, res):
+    L = native.load()
+    cp, keep = native._params(p)
+    rc = L.vc_bellman32_noalloc(ctypes.byref(cp), ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(V_out.data_ptr()),
+                                ctypes.c_void_p(pi.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+                                ctypes.c_void_p(native.torch.cuda.current_stream().cuda_stream))
+    del keep
+    return rc
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_noalloc_sweep_matches_handle_sweep_twice(name):
+    native = native_or_skip()
+    import torch
+
+    p = inputs.workload("tiny") if name == "tiny" else inputs.make_params(4, 4, 6, 0.95, seed=7)
+    m = native.MDP.build(p, fmt="implicit")
+    S = m.S
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for call in range(2):
+        V = torch.rand(S, device="cuda", generator=g) * (50 + 30 * call)
+        V_out = torch.full((S,), float("nan"), device="cuda")
+        pi = torch.full((S,), -1, dtype=torch.int32, device="cuda")
+        res = torch.full((1,), -1.0, device="cuda")
+        assert _call(native, p, V, V_out, pi, res) == native.VC_OK
+        ref = torch.empty_like(V)
+        ref_pi = torch.empty_like(pi)
+        m.bellman32(V, ref, ref_pi)
+        torch.cuda.synchronize()
+        assert torch.equal(V_out, ref)
+        assert torch.equal(pi, ref_pi)
+        assert res.item() == (V_out - V).abs().max().item()
+    m.close()
+
+
+def test_noalloc_rejects_models_beyond_its_scratch():
+    native = native_or_skip()
+    import torch
+
+    p = inputs.workload("large")  # 2,500,000 states > 1,048,576
+    V = torch.zeros(8, device="cuda")
+    out = torch.zeros(8, device="cuda")
+    pi = torch.zeros(8, dtype=torch.int32, device="cuda")
+    res = torch.zeros(1, device="cuda")
+    assert _call(native, p, V, out, pi, res) == native.VC_ERR_ARG
+    with pytest.raises(native.VcError):
+        native.bellman32_noalloc(p, V, out, pi, res)
