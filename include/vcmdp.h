@@ -245,6 +245,36 @@ int vc_autotune(vc_mdp* m, int reps, double* best_us, void* stream);
  */
 int64_t vc_autotune_report(const vc_mdp* m, char* buf, int64_t len);
 
+/* Statistics of vc_value_grad (host struct). */
+typedef struct vc_grad_stats {
+    int64_t sweeps;          /* FP32 adjoint sweeps (first solve) */
+    int64_t correction_sweeps; /* FP32 correction sweeps of the FP64 refinement */
+    int32_t rounds;          /* refinement rounds */
+    int32_t reserved;
+    double residual64;       /* FP64 max|rho + gamma P_pi^T lam - lam| of the returned lam */
+    double J;                /* rho . V */
+    int64_t nnz_transpose;   /* entries of P_pi^T */
+} vc_grad_stats;
+
+/*
+ * Adjoint gradient of J = rho . V_pi for a handle built from model parameters:
+ *     dJ/dtheta_i = lam . (dR_pi/dtheta_i + gamma (dP_pi/dtheta_i) V),
+ *     (I - gamma P_pi)^T lam = rho,
+ * theta = (lambda, mu_1..mu_H, delta_1..delta_H, f, w_occ, w_loss, w_q), 2H+5 entries.
+ * V is the policy's value ([S] double, e.g. V64 from vc_value_iterate, which equals the
+ * optimum when pi is optimal: then this is the derivative of the optimal J wherever the
+ * optimal action is unique), pi its
+ * policy ([S] int32, feasible everywhere, else VC_ERR_ARG), rho [S] double weights.
+ * lam is solved with pull sweeps over an explicit transpose P_pi^T (FP32, then FP64
+ * residual + FP32 correction rounds until the FP64 residual is below tol).
+ * dJ_dtheta: [2H+5] double on the device; lambda_out: [S] double (nullable).  Temporary
+ * device memory for P_pi^T is stream-ordered (cudaMallocAsync) and released before
+ * return.  Synchronises `stream`.  VC_ERR_ARG for a handle built from an explicit CSR.
+ * Errors: VC_ERR_NOT_CONVERGED if the residual test is not met within max_sweeps.
+ */
+int vc_value_grad(vc_mdp* m, const double* V, const int32_t* pi, const double* rho, double* dJ_dtheta,
+                  double* lambda_out, double tol, int64_t max_sweeps, vc_grad_stats* stats, void* stream);
+
 /* Release a handle and all device memory it owns (NULL is a no-op). */
 int vc_destroy(vc_mdp* m);
 

@@ -466,3 +466,31 @@ def sweep_states(p: dict, V: np.ndarray, Vn: np.ndarray, s0: int, s1: int, step:
                                   ctypes.c_int64, ctypes.c_int64]
     L.or_sweep_states.restype = ctypes.c_int64
     return int(L.or_sweep_states(ctypes.byref(_params(p)), _ptr(V), _ptr(Vn), int(s0), int(s1), int(step)))
+
+
+def grad_contract(p: dict, V, pi, lam) -> np.ndarray:
+    """sum_s lam[s] (dR/dtheta + gamma dP/dtheta V) over the policy's rows, in C (any size)."""
+    L = lib()
+    L.or_grad_contract.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+    L.or_grad_contract.restype = ctypes.c_int
+    V = np.ascontiguousarray(V, np.float64)
+    pi = np.ascontiguousarray(pi, np.int32)
+    lam = np.ascontiguousarray(lam, np.float64)
+    g = np.zeros(2 * MAXH + 5, np.float64)
+    if L.or_grad_contract(ctypes.byref(_params(p)), _ptr(V), _ptr(pi), _ptr(lam), _ptr(g)) != 0:
+        raise ValueError("policy infeasible")
+    return g[: 2 * int(p["H"]) + 5].copy()
+
+
+def adjoint_apply(p: dict, pi, lam) -> np.ndarray:
+    """P_pi^T lam (push form), any size."""
+    L = lib()
+    L.or_adjoint_apply.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_adjoint_apply.restype = ctypes.c_int
+    pi = np.ascontiguousarray(pi, np.int32)
+    lam = np.ascontiguousarray(lam, np.float64)
+    out = np.zeros(len(lam), np.float64)
+    if L.or_adjoint_apply(ctypes.byref(_params(p)), _ptr(pi), _ptr(lam), _ptr(out)) != 0:
+        raise ValueError("policy infeasible")
+    return out

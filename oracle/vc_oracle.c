@@ -675,3 +675,41 @@ int64_t or_sweep_states(const or_params* p, const double* V, double* Vn, int64_t
     }
     return updates;
 }
+
+/*
+ * Gradient contraction for a fixed policy: g_i = sum_s lam[s] * (dR(s,pi)/dtheta_i +
+ * gamma * sum_j dP(j|s,pi)/dtheta_i * V[j]), theta as in or_transition_grads (2H+5
+ * entries).  Returns 0, or 2 if pi is infeasible somewhere.
+ */
+int or_grad_contract(const or_params* p, const double* V, const int32_t* pi, const double* lam, double* g) {
+    const int64_t S = or_num_states(p);
+    const int nt = 2 * p->H + 5;
+    int64_t cols[OR_MAXSUCC];
+    double dprobs[OR_MAXSUCC * OR_NTHETA], dR[OR_NTHETA];
+    for (int i = 0; i < nt; i++) g[i] = 0.0;
+    for (int64_t s = 0; s < S; s++) {
+        int n = or_transition_grads(p, s, pi[s], cols, dprobs, dR);
+        if (n < 0) return 2;
+        for (int i = 0; i < nt; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < n; j++) acc += dprobs[j * nt + i] * V[cols[j]];
+            g[i] += lam[s] * (dR[i] + p->gamma * acc);
+        }
+    }
+    return 0;
+}
+
+/* out[y] = sum_s lam[s] * P(y | s, pi[s]): P_pi transposed applied to lam, by pushing
+ * each row.  Returns 0, or 2 if pi is infeasible somewhere. */
+int or_adjoint_apply(const or_params* p, const int32_t* pi, const double* lam, double* out) {
+    const int64_t S = or_num_states(p);
+    int64_t cols[OR_MAXSUCC];
+    double probs[OR_MAXSUCC], Rv;
+    for (int64_t y = 0; y < S; y++) out[y] = 0.0;
+    for (int64_t s = 0; s < S; s++) {
+        int n = or_transitions(p, s, pi[s], cols, probs, &Rv);
+        if (n < 0) return 2;
+        for (int j = 0; j < n; j++) out[cols[j]] += lam[s] * probs[j];
+    }
+    return 0;
+}

@@ -294,6 +294,132 @@ int vc_mdp_export_csr(const vc_mdp* mh, int64_t* row_ptr, int32_t* col, void* va
     return VC_OK;
 }
 
+int vc_value_grad(vc_mdp* mh, const double* V, const int32_t* pi, const double* rho, double* dJ_dtheta,
+                  double* lambda_out, double tol, int64_t max_sweeps, vc_grad_stats* stats, void* stream) {
+    g_err.clear();
+    if (!mh || !V || !pi || !rho || !dJ_dtheta) return fail(VC_ERR_ARG, "NULL argument");
+    if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
+    Mdp* m = (Mdp*)mh;
+    if (!m->has_model) return fail(VC_ERR_ARG, "the gradient needs a handle built from model parameters");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = m->S;
+    const int nt = 2 * m->md.H + 5;
+    vc_grad_stats gs;
+    memset(&gs, 0, sizeof(gs));
+
+    // temporaries, stream-ordered; freed on every exit path
+    int32_t* cnt = nullptr;
+    int32_t* fillpos = nullptr;
+    int64_t* rowT = nullptr;
+    int32_t* colT = nullptr;
+    float* valT = nullptr;
+    double* valT64 = nullptr;
+    float* rhoF = nullptr;
+    double* partial = nullptr;
+    double* out = nullptr;
+    int* err = nullptr;
+    auto release = [&]() {
+        void* ps[] = {cnt, fillpos, rowT, colT, valT, valT64, rhoF, partial, out, err};
+        for (void* p : ps)
+            if (p) cudaFreeAsync(p, st);
+    };
+    auto bail = [&](int rc) {
+        release();
+        cudaStreamSynchronize(st);
+        return rc;
+    };
+#define VC_TRY(call)                                                \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return bail(cuda_fail(e_, #call)); \
+    } while (0)
+
+    // ---- P_pi^T: in-degree count, exclusive scan, fill, per-row sort by source
+    VC_TRY(cudaMallocAsync((void**)&cnt, 4 * (size_t)S, st));
+    VC_TRY(cudaMallocAsync((void**)&fillpos, 4 * (size_t)S, st));
+    VC_TRY(cudaMallocAsync((void**)&rowT, 8 * ((size_t)S + 3), st));
+    VC_TRY(cudaMallocAsync((void**)&err, 16, st));
+    VC_TRY(cudaMemsetAsync(cnt, 0, 4 * (size_t)S, st));
+    VC_TRY(cudaMemsetAsync(fillpos, 0, 4 * (size_t)S, st));
+    VC_TRY(cudaMemsetAsync(err, 0, 16, st));
+    int rc = launch_adj_count(m, pi, cnt, err, st);
+    if (rc) return bail(rc);
+    if ((rc = exclusive_scan(m, cnt, S, rowT, st))) return bail(rc);
+    int herr = 0;
+    int64_t nnzT = 0;
+    VC_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VC_TRY(cudaMemcpyAsync(&nnzT, rowT + S, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    VC_TRY(cudaStreamSynchronize(st));
+    if (herr) return bail(fail(VC_ERR_ARG, "the policy picks an infeasible action"));
+    gs.nnz_transpose = nnzT;
+    VC_TRY(cudaMallocAsync((void**)&colT, 4 * ((size_t)nnzT + 16), st));
+    VC_TRY(cudaMallocAsync((void**)&valT, 4 * ((size_t)nnzT + 16), st));
+    VC_TRY(cudaMallocAsync((void**)&valT64, 8 * ((size_t)nnzT + 16), st));
+    if ((rc = launch_adj_fill(m, pi, rowT, fillpos, colT, valT, valT64, st))) return bail(rc);
+
+    // ---- lam: the transposed system as a one-action stored MDP (reward rho, matrix P^T)
+    VC_TRY(cudaMallocAsync((void**)&rhoF, 4 * ((size_t)S + 8), st));
+    if ((rc = launch_f64_to_f32(rho, rhoF, S, st))) return bail(rc);
+    Mdp T;
+    T.fmt = VC_CSR_F32 | VC_DIRECT;
+    T.has_model = false;
+    T.S = S;
+    T.A = 1;
+    T.gamma = m->gamma;
+    T.row_ptr = rowT;
+    T.col = colT;
+    T.val = valT;
+    T.R = rhoF;
+    T.ctl = m->ctl;
+    T.ctl_host = m->ctl_host;
+    T.num_sms = m->num_sms;
+    auto sweep_T = [&](const float* in, float* o, SweepCtl sc) { return csr_sweep32(&T, in, o, nullptr, nullptr, sc, st); };
+    VC_TRY(cudaMemsetAsync(m->E0, 0, 4 * (size_t)S, st));
+    int fin = 0;
+    if ((rc = loop32(m, m->E0, m->E1, tol, max_sweeps, st, &fin, sweep_T))) return bail(rc);
+    gs.sweeps = m->ctl_host->sweeps;
+    double* lam = m->V64b;
+    if ((rc = launch_f32_to_f64(fin == 1 ? m->E1 : m->E0, lam, S, st))) return bail(rc);
+
+    // ---- FP64 residual + FP32 correction rounds
+    bool ok = false;
+    for (int round = 0; round < 20; round++) {
+        VC_TRY(cudaMemsetAsync(&m->ctl->changes, 0, 2 * sizeof(unsigned long long), st));
+        SweepCtl sc{m->ctl, kModeCert64, 0, nullptr};
+        if ((rc = launch_adj_resid64(m, rowT, colT, valT64, rho, lam, m->Rres, sc, st))) return bail(rc);
+        VC_TRY(cudaMemcpyAsync(m->ctl_host, m->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        VC_TRY(cudaStreamSynchronize(st));
+        double r64;
+        memcpy(&r64, &m->ctl_host->cert64, 8);
+        gs.residual64 = r64;
+        if (r64 < tol) {
+            ok = true;
+            break;
+        }
+        gs.rounds++;
+        T.R = m->Rres;  // correction e = r + gamma P^T e
+        VC_TRY(cudaMemsetAsync(m->E0, 0, 4 * (size_t)S, st));
+        if ((rc = loop32(m, m->E0, m->E1, 0.5 * tol, max_sweeps, st, &fin, sweep_T))) return bail(rc);
+        gs.correction_sweeps += m->ctl_host->sweeps;
+        if ((rc = launch_axpy64(lam, fin == 1 ? m->E1 : m->E0, S, st))) return bail(rc);
+    }
+
+    // ---- contraction over states, reduced in a fixed order
+    const int g = state_grid(m);
+    VC_TRY(cudaMallocAsync((void**)&partial, 8 * (size_t)g * grad_partial_stride(m), st));
+    VC_TRY(cudaMallocAsync((void**)&out, 8 * ((size_t)nt + 1), st));
+    if ((rc = launch_grad_contract(m, pi, V, lam, rho, partial, out, st))) return bail(rc);
+    VC_TRY(cudaMemcpyAsync(dJ_dtheta, out, 8 * (size_t)nt, cudaMemcpyDeviceToDevice, st));
+    VC_TRY(cudaMemcpyAsync(&gs.J, out + nt, 8, cudaMemcpyDeviceToHost, st));
+    if (lambda_out) VC_TRY(cudaMemcpyAsync(lambda_out, lam, 8 * (size_t)S, cudaMemcpyDeviceToDevice, st));
+    release();
+    VC_TRY(cudaStreamSynchronize(st));
+#undef VC_TRY
+    if (stats) *stats = gs;
+    if (!ok) return fail(VC_ERR_NOT_CONVERGED, "adjoint residual above tol");
+    return VC_OK;
+}
+
 int vc_autotune(vc_mdp* mh, int reps, double* best_us, void* stream) {
     g_err.clear();
     if (!mh) return fail(VC_ERR_ARG, "NULL handle");

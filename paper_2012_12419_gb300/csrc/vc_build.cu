@@ -109,83 +109,6 @@ int build_model(const vc_params* p, Mdp* m) {
     return VC_OK;
 }
 
-// --------------------------------------------------------- device: one model row (FP64)
-constexpr int kMaxRow = 2 * kMaxH + 3;
-
-// Successors of (s, a), merged and sorted by column, zero probabilities dropped.
-// Returns the count, or -1 if a is infeasible in s.  R receives the expected reward.
-__device__ int model_row(const Model& md, const Rates& rt, int s, int a, int* cols, double* probs, double* R) {
-    Digits d;
-    decode(md, s, d);
-    int x = s;
-    if (a < md.H) {
-        const bool ok = d.q >= 1 && d.occ[a] < md.C && (a == md.H - 1 || d.ph == 1);
-        if (!ok) return -1;
-        d.occ[a] += 1;
-        d.q -= 1;
-        x = s + md.stride[a] - 2;
-    }
-    const double Lam = rt.Lam;
-    int n = 0;
-    double total = 0.0, self_extra = 0.0, occ_sum = 0.0, lost = 0.0;
-    for (int k = 0; k < md.H; k++) {
-        const int o = d.occ[k];
-        const double pcomp = rt.mu[k] * o / Lam;
-        const double pdep = rt.delta[k] / Lam;
-        total += pcomp + pdep;
-        occ_sum += o;
-        lost += rt.delta[k] * o / Lam;
-        if (o == 0) {
-            self_extra += pdep;  // departure of an empty host changes nothing
-        } else if (o == 1) {
-            cols[n] = x - md.stride[k];  // completion and departure both empty the host
-            probs[n++] = pcomp + pdep;
-        } else {
-            cols[n] = x - md.stride[k];
-            probs[n++] = pcomp;
-            cols[n] = x - o * md.stride[k];
-            probs[n++] = pdep;
-        }
-    }
-    const double parr = rt.lambda / Lam;
-    total += parr;
-    if (d.q < md.Q) {
-        cols[n] = x + 2;
-        probs[n++] = parr;
-    } else {
-        self_extra += parr;  // blocked arrival
-        lost += parr;
-    }
-    const double pflip = (d.ph ? 1.0 - rt.f : rt.f) / Lam;
-    total += pflip;
-    cols[n] = d.ph ? x - 1 : x + 1;
-    probs[n++] = pflip;
-    cols[n] = x;
-    probs[n++] = (1.0 - total) + self_extra;
-    // insertion sort by column (at most 2H+3 entries, all columns distinct)
-    for (int i = 1; i < n; i++) {
-        const int c = cols[i];
-        const double v = probs[i];
-        int j = i - 1;
-        while (j >= 0 && cols[j] > c) {
-            cols[j + 1] = cols[j];
-            probs[j + 1] = probs[j];
-            j--;
-        }
-        cols[j + 1] = c;
-        probs[j + 1] = v;
-    }
-    int m = 0;
-    for (int i = 0; i < n; i++) {
-        if (probs[i] != 0.0) {
-            cols[m] = cols[i];
-            probs[m++] = probs[i];
-        }
-    }
-    *R = rt.w_occ * occ_sum + rt.w_q * d.q + rt.w_loss * lost;
-    return m;
-}
-
 // Round a positive finite double to bfloat16, nearest-even: first to float with
 // round-to-odd (truncate, then set the last bit if anything was lost), then float to
 // bf16 with nearest-even.  Rounding to odd at 24 bits before rounding to 8 bits gives
@@ -354,7 +277,7 @@ __global__ void k_scan_apply(const int32_t* __restrict__ cnt, int64_t n, const l
 }
 
 // out[0..n] = exclusive prefix sums of cnt[0..n-1], out[n] = total.  Scratch: tile sums.
-static int exclusive_scan(Mdp* m, const int32_t* cnt, int64_t n, int64_t* out, cudaStream_t st) {
+int exclusive_scan(Mdp* m, const int32_t* cnt, int64_t n, int64_t* out, cudaStream_t st) {
     const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
     long long* scratch = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(long long) * (ntiles + 1), st);

@@ -139,6 +139,83 @@ __device__ __forceinline__ bool apply_action(const Model& md, int s, int a, Digi
     return true;
 }
 
+// --------------------------------------------------------- device: one model row (FP64)
+constexpr int kMaxRow = 2 * kMaxH + 3;
+
+// Successors of (s, a), merged and sorted by column, zero probabilities dropped.
+// Returns the count, or -1 if a is infeasible in s.  R receives the expected reward.
+__device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s, int a, int* cols, double* probs, double* R) {
+    Digits d;
+    decode(md, s, d);
+    int x = s;
+    if (a < md.H) {
+        const bool ok = d.q >= 1 && d.occ[a] < md.C && (a == md.H - 1 || d.ph == 1);
+        if (!ok) return -1;
+        d.occ[a] += 1;
+        d.q -= 1;
+        x = s + md.stride[a] - 2;
+    }
+    const double Lam = rt.Lam;
+    int n = 0;
+    double total = 0.0, self_extra = 0.0, occ_sum = 0.0, lost = 0.0;
+    for (int k = 0; k < md.H; k++) {
+        const int o = d.occ[k];
+        const double pcomp = rt.mu[k] * o / Lam;
+        const double pdep = rt.delta[k] / Lam;
+        total += pcomp + pdep;
+        occ_sum += o;
+        lost += rt.delta[k] * o / Lam;
+        if (o == 0) {
+            self_extra += pdep;  // departure of an empty host changes nothing
+        } else if (o == 1) {
+            cols[n] = x - md.stride[k];  // completion and departure both empty the host
+            probs[n++] = pcomp + pdep;
+        } else {
+            cols[n] = x - md.stride[k];
+            probs[n++] = pcomp;
+            cols[n] = x - o * md.stride[k];
+            probs[n++] = pdep;
+        }
+    }
+    const double parr = rt.lambda / Lam;
+    total += parr;
+    if (d.q < md.Q) {
+        cols[n] = x + 2;
+        probs[n++] = parr;
+    } else {
+        self_extra += parr;  // blocked arrival
+        lost += parr;
+    }
+    const double pflip = (d.ph ? 1.0 - rt.f : rt.f) / Lam;
+    total += pflip;
+    cols[n] = d.ph ? x - 1 : x + 1;
+    probs[n++] = pflip;
+    cols[n] = x;
+    probs[n++] = (1.0 - total) + self_extra;
+    // insertion sort by column (at most 2H+3 entries, all columns distinct)
+    for (int i = 1; i < n; i++) {
+        const int c = cols[i];
+        const double v = probs[i];
+        int j = i - 1;
+        while (j >= 0 && cols[j] > c) {
+            cols[j + 1] = cols[j];
+            probs[j + 1] = probs[j];
+            j--;
+        }
+        cols[j + 1] = c;
+        probs[j + 1] = v;
+    }
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        if (probs[i] != 0.0) {
+            cols[m] = cols[i];
+            probs[m++] = probs[i];
+        }
+    }
+    *R = rt.w_occ * occ_sum + rt.w_q * d.q + rt.w_loss * lost;
+    return m;
+}
+
 // --------------------------------------------------------------------------- control
 // Device-side loop control shared by the sweep kernels of one handle.
 struct Ctl {
@@ -367,6 +444,20 @@ int launch_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_i
 // V64 += e (FP64 add of the FP32 correction).
 int launch_axpy64(double* V64, const float* e, int n, cudaStream_t st);
 int launch_f32_to_f64(const float* in, double* out, int n, cudaStream_t st);
+
+// out[0..n] = exclusive prefix sums of cnt (int32 -> int64), out[n] = total.
+int exclusive_scan(Mdp* m, const int32_t* cnt, int64_t n, int64_t* out, cudaStream_t st);
+
+// Adjoint gradient kernels (vc_grad.cu).
+int launch_adj_count(Mdp* m, const int32_t* pi, int32_t* cnt, int* err, cudaStream_t st);
+int launch_adj_fill(Mdp* m, const int32_t* pi, const int64_t* rowT, int32_t* fillpos, int32_t* colT, float* valT,
+                    double* valT64, cudaStream_t st);
+int launch_adj_resid64(Mdp* m, const int64_t* rowT, const int32_t* colT, const double* valT64, const double* rho,
+                       const double* lam, float* r, SweepCtl sc, cudaStream_t st);
+int launch_f64_to_f32(const double* in, float* out, int n, cudaStream_t st);
+int grad_partial_stride(const Mdp* m);
+int launch_grad_contract(Mdp* m, const int32_t* pi, const double* V, const double* lam, const double* rho,
+                         double* partial, double* out, cudaStream_t st);
 
 // CSR kernels (vc_csr.cu).
 int csr_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st);

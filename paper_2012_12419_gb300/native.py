@@ -38,6 +38,7 @@ FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF
 EXPORTS = [
     "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
+    "vc_value_grad",
 ]
 
 
@@ -77,6 +78,17 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class GradStats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int64), ("correction_sweeps", ctypes.c_int64), ("rounds", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("residual64", ctypes.c_double), ("J", ctypes.c_double),
+        ("nnz_transpose", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -114,6 +126,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dbl), vp]
         L.vc_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
         L.vc_bellman32_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp]
+        L.vc_value_grad.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i64, ctypes.POINTER(GradStats), vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -297,6 +310,20 @@ class MDP:
                                         _stream(stream)))
         torch.cuda.synchronize()
         return row_ptr, col[:nnz], val[:nnz], scale, R
+
+    def value_grad(self, V64, pi, rho, tol: float = 1e-11, max_sweeps: int = 1_000_000, want_lambda=False,
+                   stream=None):
+        """dJ/dtheta of J = rho . V_pi (theta = lambda, mu.., delta.., f, w_occ, w_loss, w_q).
+
+        Returns (dJ [2H+5] float64 CUDA tensor, lam [S] float64 or None, stats dict)."""
+        dev = _dev()
+        H = (int(self.info()["A"]) - 1)
+        dJ = torch.empty(2 * H + 5, dtype=torch.float64, device=dev)
+        lam = torch.empty(self.S, dtype=torch.float64, device=dev) if want_lambda else None
+        gs = GradStats()
+        _check(load().vc_value_grad(self._h, _ptr(V64), _ptr(pi), _ptr(rho), _ptr(dJ), _ptr(lam), float(tol),
+                                    int(max_sweeps), ctypes.byref(gs), _stream(stream)))
+        return dJ, lam, gs.as_dict()
 
     def evaluate_policy(self, pi, V0=None, tol: float = 1e-10, max_sweeps: int = 1_000_000, stream=None):
         dev = _dev()

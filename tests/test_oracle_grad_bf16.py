@@ -84,6 +84,19 @@ def test_dense_adjoint_matches_finite_differences_and_euler():
     assert J == pytest.approx(float(w @ g[2 * H + 2:2 * H + 5]), rel=1e-9)
 
 
+def test_contraction_and_adjoint_apply_match_dense_forms():
+    """The any-size C loops used at full scale agree with the dense forms pinned above."""
+    p = inputs.workload("tiny")
+    rho = _rho_empty_hosts(p)
+    V, pi, _, _ = oracle.solve(p, tol=1e-12)
+    P, R = oracle.policy_matrices(p, pi)
+    lam = np.linalg.solve((np.eye(len(R)) - p["gamma"] * P).T, rho)
+    assert np.max(np.abs(oracle.adjoint_apply(p, pi, lam) - P.T @ lam)) < 1e-13
+    g = oracle.grad_contract(p, V, pi, lam)
+    g_dense = oracle.grad_dense(p, V, pi, rho)
+    assert np.max(np.abs(g - g_dense)) < 1e-10 * np.max(np.abs(g_dense))
+
+
 def test_bf16_round_to_nearest_even_cases():
     one = 0x3F80
     assert oracle.bf16_rne(1.0) == one
