@@ -67,6 +67,9 @@ extern "C" {
 
 /* flags for vc_value_iterate */
 #define VC_ITER_FP32_ONLY 1  /* stop after the FP32 sweeps: no FP64 refinement / certificate */
+#define VC_ITER_ACCURATE 2   /* certify the error, not the residual: refine until the FP64
+                                residual is below tol (1-gamma)/(2 gamma), so that
+                                max|V64 - V*| <= gamma/(1-gamma) * residual <= tol/2 */
 
 /* Model parameters (host struct; mu and delta are HOST arrays of length H). */
 typedef struct vc_params {
@@ -274,6 +277,73 @@ typedef struct vc_grad_stats {
  */
 int vc_value_grad(vc_mdp* m, const double* V, const int32_t* pi, const double* rho, double* dJ_dtheta,
                   double* lambda_out, double tol, int64_t max_sweeps, vc_grad_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ batched solves */
+
+/* Sizes and schedule of a batch (host struct). */
+typedef struct vc_batch_info_t {
+    int32_t n;              /* instances */
+    int32_t tiles;          /* tiles of the schedule */
+    int64_t total_states;   /* sum of the instances' S (length of the concatenated arrays) */
+    int32_t tile_states;    /* states per tile */
+    int32_t blocks_per_sm;  /* persistent grid = SMs x blocks_per_sm (capped by the tile count) */
+    int32_t grid;
+    int32_t reserved;
+    int64_t device_bytes;
+} vc_batch_info_t;
+
+/* Per-instance result of vc_value_iterate_batch (host struct array of length n). */
+typedef struct vc_batch_stats {
+    int64_t sweeps;            /* FP32 sweeps of this instance */
+    int64_t correction_sweeps; /* FP32 correction sweeps of its refinement */
+    double residual64;         /* FP64 max|T V - V| of its certified values */
+    int32_t certified;         /* residual64 < tol */
+    int32_t termination;       /* FP32 loop: 1 tolerance, 2 max_sweeps, 3 FP32 floor stall */
+} vc_batch_stats;
+
+/*
+ * Build a batch of n independent instances (p: HOST array of n vc_params, each validated
+ * as in vc_build_mdp; implicit form).  Instance i occupies states [off_i, off_i + S_i) of
+ * the concatenated arrays, off from vc_batch_offsets.  The schedule (tile size, persistent
+ * grid) starts at 256 states per tile and 4 blocks per SM; vc_batch_autotune picks one by
+ * timing.  Two CUDA graphs are captured once per schedule: the FP32 value-iteration loop
+ * and the refinement's correction loop, each a device-side WHILE loop.  Algorithm 3 for
+ * every instance, applied to many cells of a vehicular cloud at once (the paper's BSDI
+ * partitions one state space into independent blocks; here the blocks are whole MDPs).
+ */
+int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out);
+
+int vc_batch_info(const vc_batch* b, vc_batch_info_t* out);
+
+/* Host array of n+1 int64: first state of each instance, then the total. */
+int vc_batch_offsets(const vc_batch* b, int64_t* offsets);
+
+/*
+ * Value iteration of every instance (Algorithm 3), each with its own gamma, tolerance test
+ * (max(tol, 4 ulp(max|V_i|)) or FP32 stall) and sweep count, in one graph launch; then,
+ * unless VC_ITER_FP32_ONLY, every instance's argmax policy is evaluated by FP64 residual +
+ * FP32 correction (one graph launch) + FP64 update and certified by one FP64 Bellman backup
+ * (repeated while an instance fails).  V: [total] float in (warm start) / out (FP32
+ * iterate); V64_out [total] double and pi_out [total] int32 nullable (pi is local to the
+ * instance: 0..H_i); per_inst: HOST array of n stats (nullable).  Synchronises `stream`.
+ * VC_ERR_NOT_CONVERGED if an instance is not certified (or, FP32 only, hit max_sweeps).
+ */
+int vc_value_iterate_batch(vc_batch* b, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
+                           int flags, vc_batch_stats* per_inst, void* stream);
+
+/*
+ * Autotuner of the batched schedule: times the FP32 loop graph for `sweeps` sweeps of every
+ * (tile size in {256, 512, 1024, 2048}, blocks per SM in {2, 4, 8}) and keeps the fastest,
+ * recapturing the graphs.  *best_ms (host, nullable) receives its time.  Results do not
+ * depend on the schedule.
+ */
+int vc_batch_autotune(vc_batch* b, int sweeps, double* best_ms, void* stream);
+
+/* Text table of the last vc_batch_autotune (same contract as vc_autotune_report). */
+int64_t vc_batch_autotune_report(const vc_batch* b, char* buf, int64_t len);
+
+/* Release a batch and all device memory it owns (NULL is a no-op). */
+int vc_batch_destroy(vc_batch* b);
 
 /* Release a handle and all device memory it owns (NULL is a no-op). */
 int vc_destroy(vc_mdp* m);

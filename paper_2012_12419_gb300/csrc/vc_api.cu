@@ -561,6 +561,9 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
         double* cur = m->V64a;
         double* other = m->V64b;
         const long long eval_max = std::max<long long>(100000, max_sweeps);
+        // certificate target: Algorithm 3's residual test, or (VC_ITER_ACCURATE) the
+        // residual that bounds max|V64 - V*| by tol/2 through gamma/(1-gamma)
+        const double r_target = (flags & VC_ITER_ACCURATE) ? tol * (1.0 - m->gamma) / (2.0 * m->gamma) : tol;
         bool certified = false;
         double r64 = INFINITY;
         for (int round = 0; round < 50; round++) {
@@ -571,7 +574,7 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
             }
             VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * S, st));
             int efin = 0;
-            rc = loop32(m, m->E0, m->E1, 0.5 * tol, eval_max, st, &efin,
+            rc = loop32(m, m->E0, m->E1, 0.5 * r_target, eval_max, st, &efin,
                         [&](const float* in, float* o, SweepCtl sc) {
                             return launch_correct32(m, pcur, m->Rres, in, o, sc, st);
                         });
@@ -584,7 +587,7 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
             sx.residual64 = r64;
             std::swap(cur, other);  // cur = T(previous), Algorithm 3's V^{k+1}
             std::swap(pcur, pnew);  // pcur = argmax of that backup
-            if (r64 < tol) {
+            if (r64 < r_target) {
                 certified = true;
                 break;
             }

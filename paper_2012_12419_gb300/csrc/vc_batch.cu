@@ -1,0 +1,873 @@
+// vc_batch.cu -- batched value iteration: hundreds of independent uneven-sized instances
+// of the placement MDP solved together (each by Algorithm 3 with its own gamma, its own
+// convergence test and its own sweep count).
+//
+// Layout: the instances' state ranges are concatenated; a tile table cuts every range into
+// tiles of at most `ts` states that never straddle two instances.  Every sweep kernel is
+// persistent (a few CTAs per SM, grid-stride over the tile table); a tile of an instance
+// that has terminated returns at once.  Per sweep and instance, each tile folds its
+// residual max|V' - V| into the instance's slot (one atomicMax per tile) and takes a ticket;
+// the instance's last tile closes its sweep (count, tolerance max(tol, 4 ulp(max|V|)),
+// FP32 stall, max_sweeps) and retires the instance from the active count.  All active
+// instances advance one sweep per launch, so a launch's parity names the ring slot.
+//
+// The FP32 loop is one CUDA graph: a conditional WHILE node whose body is two sweeps (the
+// ping-pong pair) and a one-thread kernel that keeps the loop running while any instance is
+// active and the sweep budget lasts.  There are no inter-CTA waits anywhere: instances only
+// couple through their per-sweep tickets.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "vc_internal.cuh"
+
+namespace vc {
+
+struct InstDesc {
+    Model md;
+    Coef<float> c32;
+    Coef<double> c64;
+    long long off;  // first state in the concatenated arrays
+    int S;
+    int pad_;
+};
+
+struct BatchTile {
+    int inst;
+    int start;  // first state, relative to the instance
+    int count;
+    int pad_;
+};
+
+// Device-side control of the batched loops (SoA over instances).
+struct BatchCtl {
+    int* done;                 // 0 running, 1 converged, 2 max sweeps, 3 FP32 stall
+    int* sweeps;
+    int* ticket;
+    const int* tiles_of;       // tiles per instance (constant)
+    int* final_buf;            // buffer of the last iterate (0: A, 1: B)
+    int* since_best;
+    float* best_res;
+    unsigned int* res32;       // [2n] ring of two slots
+    unsigned int* vmax32;      // [2n]
+    unsigned long long* res64; // [n] FP64 residual of a certificate / residual pass
+    int* active;               // instances still running
+    long long* iters;          // sweeps launched by the graph loop
+    const long long* max_sweeps; // loop parameters in device memory, so one captured graph
+    const double* tol;           // serves every call
+    const float* tol_scale;      // per-instance factor on tol (nullptr: 1)
+};
+
+// Instance descriptor of a tile, staged in shared memory once per tile.
+__device__ __forceinline__ void load_desc(const InstDesc* __restrict__ descs, int inst, InstDesc& sd) {
+    const int n = (int)(sizeof(InstDesc) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(descs + inst);
+    int* dst = reinterpret_cast<int*>(&sd);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+// Closes an instance's sweep once its last tile arrives (thread 0 of that tile).
+__device__ void close_instance(const BatchCtl& c, int i, float res, float vmax, int parity, int out_buf) {
+    const double tol = *c.tol * (c.tol_scale ? (double)c.tol_scale[i] : 1.0);
+    const int slot = 2 * i + parity, next = 2 * i + (parity ^ 1);
+    atomicMax(&c.res32[slot], __float_as_uint(res));
+    atomicMax(&c.vmax32[slot], __float_as_uint(vmax));
+    __threadfence();
+    const int t = atomicAdd(&c.ticket[i], 1);
+    if (t != c.tiles_of[i] - 1) return;
+    __threadfence();
+    const float r = __uint_as_float(*((volatile unsigned int*)&c.res32[slot]));
+    const float vm = __uint_as_float(*((volatile unsigned int*)&c.vmax32[slot]));
+    c.ticket[i] = 0;
+    c.res32[next] = 0u;
+    c.vmax32[next] = 0u;
+    const int k = c.sweeps[i] + 1;
+    c.sweeps[i] = k;
+    c.final_buf[i] = out_buf;
+    int e = 0;
+    frexpf(vm, &e);
+    const double ulp = (vm > 0.0f) ? ldexp(1.0, e - 24) : 0.0;
+    const double tol_eff = fmax(tol, 4.0 * ulp);
+    int done = 0;
+    if ((double)r < tol_eff) {
+        done = 1;
+    } else if (r < c.best_res[i]) {
+        c.best_res[i] = r;
+        c.since_best[i] = 0;
+    } else if (++c.since_best[i] >= kStallSweeps) {
+        done = 3;
+    }
+    if (!done && k >= *c.max_sweeps) done = 2;
+    if (done) {
+        c.done[i] = done;
+        atomicSub(c.active, 1);
+    }
+    __threadfence();
+}
+
+// Model arithmetic per instance (same formulas as the single-instance implicit kernels).
+template <int MH, typename T>
+__device__ __forceinline__ T b_expect(const Model& md, const Coef<T>& c, const T* __restrict__ V, int x,
+                                      const Digits& d) {
+    const T vx = V[x];
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o > 0) {
+                const T v1 = V[x - md.stride[k]];
+                if (o == 1) {
+                    acc += (c.pc[k] + c.pd[k]) * (v1 - vx);
+                } else {
+                    const T v0 = V[x - o * md.stride[k]];
+                    acc += c.pc[k] * T(o) * (v1 - vx) + c.pd[k] * (v0 - vx);
+                }
+            }
+        }
+    }
+    if (d.q < md.Q) acc += c.pa * (V[x + 2] - vx);
+    const T vf = V[d.ph ? x - 1 : x + 1];
+    acc += (d.ph ? c.pf1 : c.pf0) * (vf - vx);
+    return vx + acc;
+}
+
+template <int MH, typename T>
+__device__ __forceinline__ T b_reward(const Model& md, const Coef<T>& c, const Digits& d) {
+    T loss = T(0);
+    int occ_sum = 0;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            occ_sum += d.occ[k];
+            loss += c.lossd[k] * T(d.occ[k]);
+        }
+    }
+    if (d.q >= md.Q) loss += c.lossa;
+    return c.w_occ * T(occ_sum) + c.w_q * T(d.q) + loss;
+}
+
+template <typename T>
+__device__ __forceinline__ const Coef<T>& coef_of(const InstDesc& d);
+template <>
+__device__ __forceinline__ const Coef<float>& coef_of<float>(const InstDesc& d) {
+    return d.c32;
+}
+template <>
+__device__ __forceinline__ const Coef<double>& coef_of<double>(const InstDesc& d) {
+    return d.c64;
+}
+
+// Pass 1 over all active tiles: U(x) = R(x) + gamma E[V(next) | x] (per instance).
+// done = nullptr processes every instance (extraction / certificate passes).
+template <int MH, typename T>
+__global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                        const int* __restrict__ done, const T* __restrict__ V, T* __restrict__ U) {
+    __shared__ InstDesc sd;
+    __shared__ int skip;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x == 0) skip = done ? (*((volatile int*)&done[tl.inst]) != 0) : 0;
+        __syncthreads();
+        if (!skip) {
+            load_desc(descs, tl.inst, sd);
+            __syncthreads();
+            const T* Vi = V + sd.off;
+            T* Ui = U + sd.off;
+            for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
+                const int x = tl.start + j;
+                Digits d;
+                decode<MH>(sd.md, x, d);
+                Ui[x] = b_reward<MH>(sd.md, coef_of<T>(sd), d) + coef_of<T>(sd).gamma * b_expect<MH>(sd.md, coef_of<T>(sd), Vi, x, d);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 2: V'(s) = max_a U(x_a(s)); per-instance residual and close (loop mode, ctl given),
+// or plain extraction with policy / FP64 certificate residual into res64 (ctl null).
+template <int MH, typename T>
+__global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                       BatchCtl c, int loop, int parity, const T* __restrict__ U, const T* __restrict__ V_in,
+                       T* __restrict__ V_out, int32_t* __restrict__ pi, unsigned long long* __restrict__ res64) {
+    __shared__ InstDesc sd;
+    __shared__ int skip;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x == 0) skip = loop ? (*((volatile int*)&c.done[tl.inst]) != 0) : 0;
+        __syncthreads();
+        if (skip) {
+            __syncthreads();
+            continue;
+        }
+        load_desc(descs, tl.inst, sd);
+        __syncthreads();
+        const T* Ui = U + sd.off;
+        const T* Vi = V_in + sd.off;
+        T res = T(0), vabs = T(0);
+        for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
+            const int s = tl.start + j;
+            Digits d;
+            decode<MH>(sd.md, s, d);
+            T best = -INFINITY;
+            int arg = sd.md.H;
+            if (d.q >= 1) {
+#pragma unroll
+                for (int k = 0; k < MH; k++) {
+                    if (k < sd.md.H && d.occ[k] < sd.md.C && (k == sd.md.H - 1 || d.ph == 1)) {
+                        const T u = Ui[s + sd.md.stride[k] - 2];
+                        if (u > best) {
+                            best = u;
+                            arg = k;
+                        }
+                    }
+                }
+            }
+            const T u = Ui[s];
+            if (u > best) {
+                best = u;
+                arg = sd.md.H;
+            }
+            if (V_out) V_out[sd.off + s] = best;
+            if (pi) pi[sd.off + s] = arg;
+            res = fmax(res, fabs(best - Vi[s]));
+            vabs = fmax(vabs, fabs(best));
+        }
+        if (loop || res64) {
+            res = block_max<T, kThreads>(res);
+            vabs = block_max<T, kThreads>(vabs);
+            if (threadIdx.x == 0) {
+                if (loop)
+                    close_instance(c, tl.inst, (float)res, (float)vabs, parity, parity ^ 1);
+                else
+                    atomicMax(&res64[tl.inst], dbits((double)res));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Keeps the graph's while loop running while instances are active and budget remains.
+__global__ void k_bcond(cudaGraphConditionalHandle h, BatchCtl c, int sweeps_per_body) {
+    const long long it = *c.iters + sweeps_per_body;
+    *c.iters = it;
+    const int go = (*((volatile int*)c.active) > 0) && (it < *c.max_sweeps);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Policy residual in FP64: r = R(x_pi) + gamma E[V64(next) | x_pi] - V64 (as float).
+template <int MH>
+__global__ void k_bresid64(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                           const int32_t* __restrict__ pi, const double* __restrict__ V, float* __restrict__ r,
+                           int* err) {
+    __shared__ InstDesc sd;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        load_desc(descs, tl.inst, sd);
+        __syncthreads();
+        const double* Vi = V + sd.off;
+        for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
+            const int s = tl.start + j;
+            Digits d;
+            decode<MH>(sd.md, s, d);
+            int x = s;
+            if (!apply_action<MH>(sd.md, s, pi[sd.off + s], d, x)) {
+                atomicOr(err, kErrInfeasiblePolicy);
+                r[sd.off + s] = 0.0f;
+                continue;
+            }
+            r[sd.off + s] = (float)(b_reward<MH>(sd.md, sd.c64, d) + sd.c64.gamma * b_expect<MH>(sd.md, sd.c64, Vi, x, d) - Vi[s]);
+        }
+        __syncthreads();
+    }
+}
+
+// FP32 correction sweep e_out = r + gamma E[e_in(next) | x_pi] with per-instance close.
+template <int MH>
+__global__ void k_bcorr(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                        BatchCtl c, int parity, const int32_t* __restrict__ pi, const float* __restrict__ r,
+                        const float* __restrict__ e_in, float* __restrict__ e_out) {
+    __shared__ InstDesc sd;
+    __shared__ int skip;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x == 0) skip = (*((volatile int*)&c.done[tl.inst]) != 0);
+        __syncthreads();
+        if (skip) {
+            __syncthreads();
+            continue;
+        }
+        load_desc(descs, tl.inst, sd);
+        __syncthreads();
+        const float* Ei = e_in + sd.off;
+        float res = 0.0f, vabs = 0.0f;
+        for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
+            const int s = tl.start + j;
+            Digits d;
+            decode<MH>(sd.md, s, d);
+            int x = s;
+            apply_action<MH>(sd.md, s, pi[sd.off + s], d, x);  // feasibility checked by k_bresid64
+            const float v = r[sd.off + s] + sd.c32.gamma * b_expect<MH>(sd.md, sd.c32, Ei, x, d);
+            e_out[sd.off + s] = v;
+            res = fmaxf(res, fabsf(v - Ei[s]));
+            vabs = fmaxf(vabs, fabsf(v));
+        }
+        res = block_max<float, kThreads>(res);
+        vabs = block_max<float, kThreads>(vabs);
+        if (threadIdx.x == 0) close_instance(c, tl.inst, res, vabs, parity, parity ^ 1);
+        __syncthreads();
+    }
+}
+
+// Per-instance selection of the final ping-pong buffer into out (float or double).
+template <typename TI, typename TO>
+__global__ void k_bselect(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                          const int* __restrict__ final_buf, const TI* __restrict__ A, const TI* __restrict__ B,
+                          TO* __restrict__ out) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        const long long off = descs[tl.inst].off;
+        const TI* src = final_buf[tl.inst] ? B : A;
+        for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
+            const long long g = off + tl.start + j;
+            out[g] = (TO)src[g];
+        }
+    }
+}
+
+__global__ void k_baxpy(const float* __restrict__ A, const float* __restrict__ B, const InstDesc* __restrict__ descs,
+                        const BatchTile* __restrict__ tiles, int ntiles, const int* __restrict__ final_buf,
+                        double* __restrict__ V64) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        const long long off = descs[tl.inst].off;
+        const float* src = final_buf[tl.inst] ? B : A;
+        for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
+            const long long g = off + tl.start + j;
+            V64[g] += (double)src[g];
+        }
+    }
+}
+
+__global__ void k_binit(BatchCtl c, int n, int active) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        c.done[i] = 0;
+        c.sweeps[i] = 0;
+        c.ticket[i] = 0;
+        c.final_buf[i] = 0;
+        c.since_best[i] = 0;
+        c.best_res[i] = INFINITY;
+        c.res32[2 * i] = c.res32[2 * i + 1] = 0u;
+        c.vmax32[2 * i] = c.vmax32[2 * i + 1] = 0u;
+        c.res64[i] = 0ull;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *c.active = active;
+        *c.iters = 0;
+    }
+}
+
+__global__ void k_f32_to_f64_n(const float* __restrict__ in, double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+// ------------------------------------------------------------------------ batch handle
+struct Batch {
+    int n = 0;
+    long long total = 0;
+    int mh = 8;
+    int ts = 256;     // states per tile
+    int bps = 4;      // blocks per SM of the persistent grid
+    int grid = 0;
+    int ntiles = 0;
+    int num_sms = 0;
+    std::vector<InstDesc> h_desc;
+    std::vector<int> h_tiles_of;
+    InstDesc* d_desc = nullptr;
+    BatchTile* d_tiles = nullptr;
+    float *Va = nullptr, *Vb = nullptr, *U = nullptr, *E0 = nullptr, *E1 = nullptr, *Rr = nullptr;
+    double *V64 = nullptr, *V64b = nullptr, *U64 = nullptr;
+    int32_t *pi = nullptr, *pi2 = nullptr;
+    int *done = nullptr, *sweeps = nullptr, *ticket = nullptr, *tiles_of = nullptr, *final_buf = nullptr,
+        *since_best = nullptr, *active = nullptr, *err = nullptr;
+    float* best_res = nullptr;
+    unsigned int *res32 = nullptr, *vmax32 = nullptr;
+    unsigned long long* res64 = nullptr;
+    long long* iters = nullptr;
+    long long* max_d = nullptr;
+    double* tol_d = nullptr;
+    float* tol_scale = nullptr;  // per-instance factor of the correction loop's tolerance
+    cudaGraph_t g_vi = nullptr, g_corr = nullptr;
+    cudaGraphExec_t x_vi = nullptr, x_corr = nullptr;
+    std::vector<void*> owned;
+    int64_t device_bytes = 0;
+    std::string tune_report;
+};
+
+static int balloc(Batch* b, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    b->owned.push_back(*p);
+    b->device_bytes += (int64_t)bytes;
+    return VC_OK;
+}
+
+static BatchCtl ctl_of(Batch* b, bool scaled = false) {
+    BatchCtl c;
+    c.tol_scale = scaled ? b->tol_scale : nullptr;
+    c.done = b->done;
+    c.sweeps = b->sweeps;
+    c.ticket = b->ticket;
+    c.tiles_of = b->tiles_of;
+    c.final_buf = b->final_buf;
+    c.since_best = b->since_best;
+    c.best_res = b->best_res;
+    c.res32 = b->res32;
+    c.vmax32 = b->vmax32;
+    c.res64 = b->res64;
+    c.active = b->active;
+    c.iters = b->iters;
+    c.max_sweeps = b->max_d;
+    c.tol = b->tol_d;
+    return c;
+}
+
+// Tile table for tile size ts; tiles of an instance are contiguous in the table.
+static int build_tiles(Batch* b, cudaStream_t st) {
+    std::vector<BatchTile> tiles;
+    b->h_tiles_of.assign(b->n, 0);
+    for (int i = 0; i < b->n; i++) {
+        const int S = b->h_desc[i].S;
+        for (int s0 = 0; s0 < S; s0 += b->ts) {
+            BatchTile t;
+            t.inst = i;
+            t.start = s0;
+            t.count = std::min(b->ts, S - s0);
+            t.pad_ = 0;
+            tiles.push_back(t);
+            b->h_tiles_of[i]++;
+        }
+    }
+    b->ntiles = (int)tiles.size();
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    VC_CUDA(cudaMalloc((void**)&b->d_tiles, sizeof(BatchTile) * tiles.size()));
+    VC_CUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(b->tiles_of, b->h_tiles_of.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    b->grid = std::max(1, std::min(b->ntiles, b->num_sms * b->bps));
+    return VC_OK;
+}
+
+template <int MH>
+static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
+    const BatchCtl c = ctl_of(b);
+    k_bpost<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U);
+    k_bmax<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 0, b->U, b->Va, b->Vb,
+                                                     nullptr, nullptr);
+    k_bpost<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U);
+    k_bmax<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 1, b->U, b->Vb, b->Va,
+                                                     nullptr, nullptr);
+    k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
+}
+
+template <int MH>
+static void enqueue_corr_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
+    const BatchCtl c = ctl_of(b, true);
+    k_bcorr<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 0, b->pi, b->Rr, b->E0, b->E1);
+    k_bcorr<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, b->pi, b->Rr, b->E1, b->E0);
+    k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
+}
+
+// One graph: a WHILE node (default condition 1 at every launch) whose body is built by
+// capturing `body` on a private stream.
+template <typename Body>
+static int make_loop_graph(cudaGraph_t* g, cudaGraphExec_t* x, Body&& body) {
+    if (*x) cudaGraphExecDestroy(*x);
+    if (*g) cudaGraphDestroy(*g);
+    *x = nullptr;
+    *g = nullptr;
+    VC_CUDA(cudaGraphCreate(g, 0));
+    cudaGraphConditionalHandle h;
+    VC_CUDA(cudaGraphConditionalHandleCreate(&h, *g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    VC_CUDA(cudaGraphAddNode(&node, *g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    VC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    VC_CUDA(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    body(cs, h);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &captured);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (batched loop body)");
+    VC_CUDA(cudaGraphInstantiate(x, *g, 0));
+    return VC_OK;
+}
+
+static int build_graphs(Batch* b) {
+    int rc;
+    auto vi = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        if (b->mh == 4)
+            enqueue_vi_body<4>(b, cs, h);
+        else if (b->mh == 8)
+            enqueue_vi_body<8>(b, cs, h);
+        else
+            enqueue_vi_body<16>(b, cs, h);
+    };
+    auto corr = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        if (b->mh == 4)
+            enqueue_corr_body<4>(b, cs, h);
+        else if (b->mh == 8)
+            enqueue_corr_body<8>(b, cs, h);
+        else
+            enqueue_corr_body<16>(b, cs, h);
+    };
+    if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, vi))) return rc;
+    if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, corr))) return rc;
+    return VC_OK;
+}
+
+static void free_batch(Batch* b) {
+    if (!b) return;
+    if (b->x_vi) cudaGraphExecDestroy(b->x_vi);
+    if (b->g_vi) cudaGraphDestroy(b->g_vi);
+    if (b->x_corr) cudaGraphExecDestroy(b->x_corr);
+    if (b->g_corr) cudaGraphDestroy(b->g_corr);
+    for (void* p : b->owned) cudaFree(p);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    delete b;
+}
+
+static int reset_loop(Batch* b, double tol, long long max_sweeps, cudaStream_t st) {
+    VC_CUDA(cudaMemcpyAsync(b->tol_d, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(b->max_d, &max_sweeps, sizeof(long long), cudaMemcpyHostToDevice, st));
+    count_launches(1);
+    k_binit<<<(b->n + 255) / 256, 256, 0, st>>>(ctl_of(b), b->n, b->n);
+    VC_CUDA(cudaGetLastError());
+    // the parameters live in pageable host memory: make the copies complete before return
+    VC_CUDA(cudaStreamSynchronize(st));
+    return VC_OK;
+}
+
+template <int MH>
+static void enqueue_extract(Batch* b, const float* V, int32_t* pi, cudaStream_t st) {
+    k_bpost<MH, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U);
+    k_bmax<MH, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U, V,
+                                                     nullptr, pi, nullptr);
+}
+
+template <int MH>
+static void enqueue_cert(Batch* b, cudaStream_t st) {
+    k_bpost<MH, double><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64, b->U64);
+    k_bmax<MH, double><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U64,
+                                                      b->V64, b->V64b, b->pi2, b->res64);
+}
+
+template <int MH>
+static void enqueue_resid(Batch* b, cudaStream_t st) {
+    k_bresid64<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, b->V64, b->Rr, b->err);
+}
+
+template <typename F>
+static void by_mh(int mh, F&& f) {
+    if (mh == 4)
+        f(std::integral_constant<int, 4>());
+    else if (mh == 8)
+        f(std::integral_constant<int, 8>());
+    else
+        f(std::integral_constant<int, 16>());
+}
+
+}  // namespace vc
+
+using namespace vc;
+
+extern "C" {
+
+int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) {
+    set_error("");
+    if (!out || !p) return fail(VC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (n < 1) return fail(VC_ERR_ARG, "n must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch* b = new Batch();
+    b->n = n;
+    int rc = VC_OK;
+    int maxH = 1;
+    for (int i = 0; i < n && !rc; i++) {
+        Mdp tmp;
+        tmp.fmt = VC_IMPLICIT;
+        rc = build_model(&p[i], &tmp);
+        if (rc) {
+            set_error("instance " + std::to_string(i) + ": " + vc_last_error());
+            break;
+        }
+        InstDesc d;
+        memset(&d, 0, sizeof(d));
+        d.md = tmp.md;
+        d.c32 = tmp.c32;
+        d.c64 = tmp.c64;
+        d.off = b->total;
+        d.S = tmp.S;
+        b->h_desc.push_back(d);
+        b->total += tmp.S;
+        maxH = std::max(maxH, tmp.md.H);
+    }
+    if (!rc && b->total >= (1LL << 31)) rc = fail(VC_ERR_ARG, "total states must be < 2^31");
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    b->mh = maxH <= 4 ? 4 : (maxH <= 8 ? 8 : 16);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t T = (size_t)b->total, N = (size_t)n;
+    void** f4[] = {(void**)&b->Va, (void**)&b->Vb, (void**)&b->U, (void**)&b->E0, (void**)&b->E1, (void**)&b->Rr,
+                   (void**)&b->pi, (void**)&b->pi2};
+    for (void** pp : f4)
+        if (!rc) rc = balloc(b, pp, 4 * T);
+    void** f8[] = {(void**)&b->V64, (void**)&b->V64b, (void**)&b->U64};
+    for (void** pp : f8)
+        if (!rc) rc = balloc(b, pp, 8 * T);
+    void** fi[] = {(void**)&b->done, (void**)&b->sweeps, (void**)&b->ticket, (void**)&b->tiles_of,
+                   (void**)&b->final_buf, (void**)&b->since_best, (void**)&b->best_res};
+    for (void** pp : fi)
+        if (!rc) rc = balloc(b, pp, 4 * N);
+    if (!rc) rc = balloc(b, (void**)&b->res32, 8 * N);
+    if (!rc) rc = balloc(b, (void**)&b->vmax32, 8 * N);
+    if (!rc) rc = balloc(b, (void**)&b->res64, 8 * N);
+    if (!rc) rc = balloc(b, (void**)&b->active, 16);
+    if (!rc) rc = balloc(b, (void**)&b->err, 16);
+    if (!rc) rc = balloc(b, (void**)&b->iters, 16);
+    if (!rc) rc = balloc(b, (void**)&b->max_d, 16);
+    if (!rc) rc = balloc(b, (void**)&b->tol_d, 16);
+    if (!rc) rc = balloc(b, (void**)&b->tol_scale, 4 * N);
+    if (!rc) rc = balloc(b, (void**)&b->d_desc, sizeof(InstDesc) * N);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc.data(), sizeof(InstDesc) * N, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(descriptors)");
+    }
+    if (!rc) rc = build_tiles(b, st);
+    if (!rc) rc = build_graphs(b);
+    if (rc) {
+        free_batch(b);
+        return rc;
+    }
+    *out = (vc_batch*)b;
+    return VC_OK;
+}
+
+int vc_batch_info(const vc_batch* bh, vc_batch_info_t* out) {
+    set_error("");
+    if (!bh || !out) return fail(VC_ERR_ARG, "NULL argument");
+    const Batch* b = (const Batch*)bh;
+    out->n = b->n;
+    out->total_states = b->total;
+    out->tiles = b->ntiles;
+    out->tile_states = b->ts;
+    out->blocks_per_sm = b->bps;
+    out->grid = b->grid;
+    out->device_bytes = b->device_bytes;
+    return VC_OK;
+}
+
+int vc_batch_offsets(const vc_batch* bh, int64_t* offsets) {
+    set_error("");
+    if (!bh || !offsets) return fail(VC_ERR_ARG, "NULL argument");
+    const Batch* b = (const Batch*)bh;
+    for (int i = 0; i < b->n; i++) offsets[i] = b->h_desc[i].off;
+    offsets[b->n] = b->total;
+    return VC_OK;
+}
+
+int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
+                           int flags, vc_batch_stats* per_inst, void* stream) {
+    set_error("");
+    if (!bh || !V) return fail(VC_ERR_ARG, "NULL argument");
+    if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
+    Batch* b = (Batch*)bh;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t T = (size_t)b->total, N = (size_t)b->n;
+    int rc;
+    // ---- FP32 value iteration of every instance: one graph launch
+    VC_CUDA(cudaMemcpyAsync(b->Va, V, 4 * T, cudaMemcpyDeviceToDevice, st));
+    if ((rc = reset_loop(b, tol, max_sweeps, st))) return rc;
+    count_launches(1);
+    VC_CUDA(cudaGraphLaunch(b->x_vi, st));
+    count_launches(1);
+    k_bselect<float, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->final_buf, b->Va,
+                                                          b->Vb, V);
+    VC_CUDA(cudaGetLastError());
+    std::vector<int> done(N), sweeps(N), csweeps(N, 0), cert(N, 0);
+    std::vector<double> r64(N, INFINITY);
+    VC_CUDA(cudaMemcpyAsync(done.data(), b->done, 4 * N, cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaMemcpyAsync(sweeps.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    bool all_cert = false;
+    if (!(flags & VC_ITER_FP32_ONLY)) {
+        // ---- refinement of every instance: argmax policy, FP64 residual, FP32 correction
+        // (one graph launch), FP64 update, FP64 Bellman certificate; repeat on failures.
+        by_mh(b->mh, [&](auto m) { enqueue_extract<decltype(m)::value>(b, V, b->pi, st); });
+        count_launches(3);
+        k_f32_to_f64_n<<<b->grid, kThreads, 0, st>>>(V, b->V64, (long long)T);
+        const long long eval_max = std::max<long long>(100000, max_sweeps);
+        // Per-instance target of the FP64 residual: tol, or, in accuracy mode,
+        // tol (1 - gamma_i) / (2 gamma_i), which bounds max|V64 - V*| by tol / 2.
+        std::vector<float> scale(N, 1.0f);
+        if (flags & VC_ITER_ACCURATE)
+            for (size_t i = 0; i < N; i++) {
+                const double g = b->h_desc[i].c64.gamma;
+                scale[i] = (float)((1.0 - g) / (2.0 * g));
+            }
+        VC_CUDA(cudaMemcpyAsync(b->tol_scale, scale.data(), 4 * N, cudaMemcpyHostToDevice, st));
+        for (int round = 0; round < 20; round++) {
+            VC_CUDA(cudaMemsetAsync(b->err, 0, 4, st));
+            count_launches(1);
+            by_mh(b->mh, [&](auto m) { enqueue_resid<decltype(m)::value>(b, st); });
+            VC_CUDA(cudaMemsetAsync(b->E0, 0, 4 * T, st));
+            if ((rc = reset_loop(b, 0.5 * tol, eval_max, st))) return rc;
+            int herr = 0;
+            VC_CUDA(cudaMemcpyAsync(&herr, b->err, 4, cudaMemcpyDeviceToHost, st));
+            count_launches(1);
+            VC_CUDA(cudaGraphLaunch(b->x_corr, st));
+            count_launches(1);
+            k_baxpy<<<b->grid, kThreads, 0, st>>>(b->E0, b->E1, b->d_desc, b->d_tiles, b->ntiles, b->final_buf,
+                                                  b->V64);
+            std::vector<int> cs(N);
+            VC_CUDA(cudaMemcpyAsync(cs.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
+            VC_CUDA(cudaMemsetAsync(b->res64, 0, 8 * N, st));
+            count_launches(2);
+            by_mh(b->mh, [&](auto m) { enqueue_cert<decltype(m)::value>(b, st); });
+            std::vector<unsigned long long> rb(N);
+            VC_CUDA(cudaMemcpyAsync(rb.data(), b->res64, 8 * N, cudaMemcpyDeviceToHost, st));
+            VC_CUDA(cudaMemcpyAsync(b->V64, b->V64b, 8 * T, cudaMemcpyDeviceToDevice, st));
+            VC_CUDA(cudaMemcpyAsync(b->pi, b->pi2, 4 * T, cudaMemcpyDeviceToDevice, st));
+            VC_CUDA(cudaStreamSynchronize(st));
+            if (herr) return fail(VC_ERR_CUDA, "internal: batched refinement policy infeasible");
+            all_cert = true;
+            for (size_t i = 0; i < N; i++) {
+                csweeps[i] += cs[i];
+                double r;
+                memcpy(&r, &rb[i], 8);
+                r64[i] = r;
+                cert[i] = r < tol * (double)scale[i];
+                all_cert = all_cert && cert[i];
+            }
+            if (all_cert) break;
+        }
+        if (V64_out) VC_CUDA(cudaMemcpyAsync(V64_out, b->V64, 8 * T, cudaMemcpyDeviceToDevice, st));
+        if (pi_out) VC_CUDA(cudaMemcpyAsync(pi_out, b->pi, 4 * T, cudaMemcpyDeviceToDevice, st));
+    } else {
+        if (pi_out) by_mh(b->mh, [&](auto m) { enqueue_extract<decltype(m)::value>(b, V, pi_out, st); });
+        if (V64_out) {
+            count_launches(1);
+            k_f32_to_f64_n<<<b->grid, kThreads, 0, st>>>(V, V64_out, (long long)T);
+        }
+    }
+    VC_CUDA(cudaStreamSynchronize(st));
+    bool any_max = false;
+    for (size_t i = 0; i < N; i++) {
+        if (done[i] == 0 || done[i] == 2) any_max = true;
+        if (per_inst) {
+            per_inst[i].sweeps = sweeps[i];
+            per_inst[i].correction_sweeps = csweeps[i];
+            per_inst[i].residual64 = r64[i];
+            per_inst[i].certified = cert[i];
+            per_inst[i].termination = done[i];
+        }
+    }
+    if (flags & VC_ITER_FP32_ONLY) {
+        if (any_max) return fail(VC_ERR_NOT_CONVERGED, "an instance reached max_sweeps");
+        return VC_OK;
+    }
+    if (!all_cert) return fail(VC_ERR_NOT_CONVERGED, "an instance was not certified");
+    return VC_OK;
+}
+
+// Times the FP32 loop graph for every (tile size, blocks per SM) schedule on this batch
+// (a fixed number of sweeps from V = 0) and keeps the fastest.
+int vc_batch_autotune(vc_batch* bh, int sweeps, double* best_ms, void* stream) {
+    set_error("");
+    if (!bh) return fail(VC_ERR_ARG, "NULL handle");
+    Batch* b = (Batch*)bh;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (sweeps < 2) sweeps = 2;
+    const int tss[] = {256, 512, 1024, 2048};
+    const int bpss[] = {2, 4, 8};
+    cudaEvent_t e0, e1;
+    VC_CUDA(cudaEventCreate(&e0));
+    VC_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_ts = b->ts, best_bps = b->bps;
+    int rc;
+    b->tune_report = "tile_states blocks_per_sm grid tiles ms\n";
+    for (int ts : tss) {
+        for (int bps : bpss) {
+            b->ts = ts;
+            b->bps = bps;
+            if ((rc = build_tiles(b, st))) return rc;
+            if ((rc = build_graphs(b))) return rc;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 2; rep++) {
+                VC_CUDA(cudaMemsetAsync(b->Va, 0, 4 * (size_t)b->total, st));
+                if ((rc = reset_loop(b, 1e-30, sweeps, st))) return rc;
+                VC_CUDA(cudaEventRecord(e0, st));
+                count_launches(1);
+                VC_CUDA(cudaGraphLaunch(b->x_vi, st));
+                VC_CUDA(cudaEventRecord(e1, st));
+                VC_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                VC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                ms_best = std::min(ms_best, ms);
+            }
+            char line[128];
+            snprintf(line, sizeof(line), "%d %d %d %d %.3f\n", ts, bps, b->grid, b->ntiles, ms_best);
+            b->tune_report += line;
+            if (ms_best < best) {
+                best = ms_best;
+                best_ts = ts;
+                best_bps = bps;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->ts = best_ts;
+    b->bps = best_bps;
+    if ((rc = build_tiles(b, st))) return rc;
+    if ((rc = build_graphs(b))) return rc;
+    if (best_ms) *best_ms = best;
+    return VC_OK;
+}
+
+int64_t vc_batch_autotune_report(const vc_batch* bh, char* buf, int64_t len) {
+    if (!bh) return 0;
+    const std::string& r = ((const Batch*)bh)->tune_report;
+    if (buf && len > 0) {
+        const int64_t n = std::min<int64_t>(len - 1, (int64_t)r.size());
+        memcpy(buf, r.data(), (size_t)n);
+        buf[n] = 0;
+    }
+    return (int64_t)r.size() + 1;
+}
+
+int vc_batch_destroy(vc_batch* bh) {
+    set_error("");
+    free_batch((Batch*)bh);
+    return VC_OK;
+}
+
+}  // extern "C"

@@ -32,13 +32,15 @@ VC_DIRECT = 32
 VC_VAL_F32 = 0
 VC_VAL_BF16 = 1
 VC_ITER_FP32_ONLY = 1
+VC_ITER_ACCURATE = 2
 
 FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF16}
 
 EXPORTS = [
     "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
-    "vc_value_grad",
+    "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
+    "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy",
 ]
 
 
@@ -89,6 +91,21 @@ class GradStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("tiles", ctypes.c_int32), ("total_states", ctypes.c_int64),
+        ("tile_states", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("grid", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int64), ("correction_sweeps", ctypes.c_int64), ("residual64", ctypes.c_double),
+        ("certified", ctypes.c_int32), ("termination", ctypes.c_int32),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -127,11 +144,19 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
         L.vc_bellman32_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp]
         L.vc_value_grad.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i64, ctypes.POINTER(GradStats), vp]
+        L.vc_build_batch.argtypes = [ctypes.POINTER(Params), i32, vp, ctypes.POINTER(vp)]
+        L.vc_batch_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+        L.vc_batch_offsets.argtypes = [vp, vp]
+        L.vc_value_iterate_batch.argtypes = [vp, vp, vp, vp, dbl, i64, ctypes.c_int, ctypes.POINTER(BatchStats), vp]
+        L.vc_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dbl), vp]
+        L.vc_batch_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
+        L.vc_batch_destroy.argtypes = [vp]
         for name in EXPORTS:
-            if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report"):
+            if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
         L.vc_kernel_launches.restype = ctypes.c_int64
         L.vc_autotune_report.restype = ctypes.c_int64
+        L.vc_batch_autotune_report.restype = ctypes.c_int64
         _lib = L
         return _lib
 
@@ -241,8 +266,11 @@ class MDP:
 
     # ------------------------------------------------------------------------- solve
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
-                      want_v64: bool = True, want_pi: bool = True, stream=None, raise_on_nonconvergence=True):
-        """Algorithm 3 on the device.  Returns (V fp32, V64 fp64 or None, pi int32 or None, stats dict)."""
+                      want_v64: bool = True, want_pi: bool = True, stream=None, raise_on_nonconvergence=True,
+                      accurate: bool = False):
+        """Algorithm 3 on the device.  Returns (V fp32, V64 fp64 or None, pi int32 or None, stats dict).
+
+        accurate=True certifies the error rather than the residual: max|V64 - V*| <= tol / 2."""
         dev = _dev()
         S = self.S
         if V is None:
@@ -250,8 +278,9 @@ class MDP:
         V64 = torch.empty(S, dtype=torch.float64, device=dev) if want_v64 else None
         pi = torch.empty(S, dtype=torch.int32, device=dev) if want_pi else None
         st = Stats()
+        flags = (VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
         rc = load().vc_value_iterate(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
-                                     VC_ITER_FP32_ONLY if fp32_only else 0, ctypes.byref(st), _stream(stream))
+                                     flags, ctypes.byref(st), _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
         d = st.as_dict()
         d["status"] = rc
@@ -347,6 +376,78 @@ def solve(params: dict, fmt: str = "implicit", padded: bool = False, tol: float 
         return V64.cpu().numpy(), pi.cpu().numpy(), st
     finally:
         m.close()
+
+
+class Batch:
+    """Many independent instances solved together (a ``vc_batch`` handle)."""
+
+    def __init__(self, params_list, stream=None):
+        L = load()
+        _dev()
+        n = len(params_list)
+        arr = (Params * n)()
+        self._keep = []
+        for i, p in enumerate(params_list):
+            cp, keep = _params(p)
+            arr[i] = cp
+            self._keep.append(keep)
+        h = ctypes.c_void_p()
+        _check(L.vc_build_batch(arr, n, _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        off = np.zeros(n + 1, np.int64)
+        _check(L.vc_batch_offsets(self._h, off.ctypes.data_as(ctypes.c_void_p)))
+        self.offsets = off
+
+    def info(self) -> dict:
+        inf = BatchInfo()
+        _check(load().vc_batch_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in BatchInfo._fields_ if k != "reserved"}
+
+    @property
+    def total(self) -> int:
+        return int(self.offsets[-1])
+
+    def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
+                      stream=None, raise_on_nonconvergence=True, accurate: bool = False):
+        """Returns (V fp32 [total], V64 [total] or None, pi [total] or None, list of per-instance dicts, status).
+
+        accurate=True certifies every instance's error: max|V64_i - V*_i| <= tol / 2."""
+        dev = _dev()
+        if V is None:
+            V = torch.zeros(self.total, dtype=torch.float32, device=dev)
+        V64 = torch.empty(self.total, dtype=torch.float64, device=dev)
+        pi = torch.empty(self.total, dtype=torch.int32, device=dev)
+        st = (BatchStats * self.n)()
+        flags = (VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
+        rc = load().vc_value_iterate_batch(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
+                                           flags, st, _stream(stream))
+        _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
+        stats = [{k: getattr(s, k) for k, _ in BatchStats._fields_} for s in st]
+        return V, V64, pi, stats, rc
+
+    def autotune(self, sweeps: int = 20, stream=None) -> float:
+        ms = ctypes.c_double()
+        _check(load().vc_batch_autotune(self._h, int(sweeps), ctypes.byref(ms), _stream(stream)))
+        return ms.value
+
+    def autotune_report(self) -> str:
+        L = load()
+        n = L.vc_batch_autotune_report(self._h, None, 0)
+        buf = ctypes.create_string_buffer(int(n))
+        L.vc_batch_autotune_report(self._h, buf, int(n))
+        return buf.value.decode()
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().vc_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bellman32_noalloc(params: dict, V, V_out, pi=None, residual=None, stream=None):
