@@ -37,6 +37,8 @@ WORKLOAD_DESC = {
     "tiny": "tiny MDP: H=3 C=3 Q=4, S=640, A=4, gamma=0.95",
     "precision": "precision MDP: H=8 C=4 Q=15, S=12,500,000, A=9, gamma=0.95",
     "grad": "differentiation MDP: H=6 C=4 Q=10, S=343,750, A=7, gamma=0.95",
+    "batched": "512 uneven instances: H in 2..5, C in 2..6, Q in 3..12, gamma in {0.9, 0.95, 0.99}, "
+               "S in [72, 436,982]",
 }
 
 
@@ -51,12 +53,16 @@ def parse():
     ap.add_argument("--layout", default="padded", choices=["padded", "canonical"],
                     help="padded: every row holds 2H+3 entries (340,000,000 per sweep on the large MDP, the "
                          "workload's stated CSR size); canonical: only non-zero successors (130,468,750)")
+    ap.add_argument("--no-sliced", dest="sliced", action="store_false",
+                    help="CSR kernels only: build no sliced (SELL-C-sigma) copy of the stored matrix for the "
+                         "autotuner to choose")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and the variants")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default CSR schedule (profiling runs: no tuning launches before the timed ones)")
     args = ap.parse_args()
     args.padded = args.layout == "padded" and args.form != "implicit"
+    args.sliced = args.sliced and args.form != "implicit"
     return args
 
 
@@ -140,7 +146,7 @@ def run_native(args):
 
     p = inputs.workload(args.workload)
     t0 = time.perf_counter()
-    m = native.MDP.build(p, fmt=args.form, padded=args.padded)
+    m = native.MDP.build(p, fmt=args.form, padded=args.padded, sliced=args.sliced)
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t0) * 1e3
     tune_us = m.autotune(reps=5) if (args.form != "implicit" and not args.no_autotune) else None
@@ -201,7 +207,8 @@ def run_native(args):
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
-            "workload": WORKLOAD_DESC[args.workload], "form": args.form + ("+padded" if args.padded else ""),
+            "workload": WORKLOAD_DESC[args.workload],
+            "form": args.form + ("+padded" if args.padded else "") + ("+sliced" if args.sliced else ""),
             "tol": args.tol, "nnz_logical_per_sweep": nnz, "nnz_stored_per_sweep": int(info["nnz_stored"]),
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "256 MiB buffer written between steps, outside the step events",
@@ -228,11 +235,288 @@ def run_native(args):
             if world == 1:
                 out["cpu_baseline"] = cpu_baseline(p, args)
             out["variants"] = variants(args, p, native, torch, dev, stream)
+            if world == 1 and args.workload == "large":
+                out["comparisons"] = comparisons(args, native, torch, dev, stream)
         print(json.dumps(out))
     m.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- batched arm
+def _implicit_nnz(native, p):
+    """Logical successor count per sweep of one instance (canonical, feasible rows)."""
+    m = native.MDP.build(p, fmt="implicit")
+    n = int(m.info()["nnz_logical"])
+    m.close()
+    return n
+
+
+def run_batched(args):
+    """512 uneven instances in one graph-captured persistent solve (per-instance gamma and
+    termination).  Under torchrun the instances are split across ranks by the LPT rule and
+    each rank solves its share; value = all ranks' updates / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2012_12419_gb300 import inputs, native, shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    native.load(build_if_missing=(rank == 0))
+    if world > 1:
+        dist.barrier()
+        native.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    ps_all = inputs.batch_params(512, seed=2)
+    idx, ps = shard.shard_of(ps_all, rank, world, args.tol)
+    nnz = [_implicit_nnz(native, p) for p in ps]
+    t0 = time.perf_counter()
+    b = native.Batch(ps)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    tune_ms = b.autotune(sweeps=20) if not args.no_autotune else None
+    tune_sweep_ms = tune_ms / 20 if tune_ms else None
+    binfo = b.info()
+    V = torch.zeros(b.total, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        V.zero_()
+        _, _, _, st, _ = b.value_iterate(V, tol=args.tol)
+        return st
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = native.kernel_launches()
+    times, stats = [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        stats.append(st)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    launches = native.kernel_launches() - launches0
+    ck = clocks.stop()
+    ms = [a.elapsed_time(c) for a, c in times]
+    total_ms = sum(ms)
+    units = float(sum(n * s["sweeps"] for st in stats for n, s in zip(nnz, st)))
+    if world > 1:
+        t = torch.tensor([total_ms, units], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms_all, units_all = float(tmax[0]), float(t[1])
+        gathered = shard.gather_by_index({i: (s["sweeps"], s["certified"]) for i, s in zip(idx, stats[-1])},
+                                         len(ps_all))
+    else:
+        total_ms_all, units_all = total_ms, units
+        gathered = [(s["sweeps"], s["certified"]) for s in stats[-1]]
+    last = stats[-1]
+    out = {
+        "metric": METRIC, "value": units_all / (total_ms_all / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms_all / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD_DESC["batched"], "form": "implicit, batched graph",
+            "tol": args.tol, "instances": len(ps_all), "instances_this_rank": len(ps),
+            "states_this_rank": int(binfo["total_states"]),
+            "parallelism": f"LPT split over {world} ranks" if world > 1 else "single",
+            "l2": "256 MiB buffer written between steps, outside the step events",
+            "step": "V=0 -> one graph launch of FP32 sweeps with per-instance termination -> argmax -> "
+                    "FP64 policy evaluation -> FP64 Bellman certificate per instance",
+        },
+        "time_to_residual_ms": statistics.median(ms),
+        "certified": all(c == 1 for _, c in gathered),
+        "sweeps_max": max(s for s, _ in gathered), "sweeps_median": statistics.median([s for s, _ in gathered]),
+        "residual64": max(s["residual64"] for s in last),
+        "build_ms": build_ms,
+        "schedule": {k: int(binfo[k]) for k in ("tile_states", "blocks_per_sm", "grid", "tiles")},
+        "autotune": b.autotune_report().strip().splitlines() if tune_ms else None,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+    }
+    if rank == 0 and tune_sweep_ms:
+        hbm, src = peaks()
+        nbytes = 8 * int(binfo["total_states"])
+        ach = nbytes / (tune_sweep_ms / 1e3) / 1e9
+        out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "traffic": None, "peak_source": f"{src} hbm_gbs",
+                           "kernel": "k_bpost+k_bmax (one graph pass = one sweep of every instance)",
+                           "bytes_per_launch": nbytes, "launch_us": tune_sweep_ms * 1e3}
+    if rank == 0 and not args.no_extras:
+        out["e2e"] = batched_e2e(args, ps, nnz, native, torch)
+        if world == 1:
+            out["cpu_baseline"] = cpu_baseline_batched(ps_all)
+            out["vs_per_instance"] = batched_vs_per_instance(args, ps, b, native, torch, dev, stream)
+    if rank == 0:
+        print(json.dumps(out))
+    b.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def batched_e2e(args, ps, nnz, native, torch):
+    """Public API from host parameters to host results, every step: batch build (H2D of the
+    parameter structs and rate arrays), solve, D2H of V64 and pi into pinned buffers."""
+    import ctypes
+
+    ms, units = [], []
+    for _ in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = native.Batch(ps)
+        _, V64, pi, st, _ = b.value_iterate(tol=args.tol)
+        hv = torch.empty(V64.numel(), dtype=torch.float64, pin_memory=True)
+        hp = torch.empty(pi.numel(), dtype=torch.int32, pin_memory=True)
+        hv.copy_(V64, non_blocking=True)
+        hp.copy_(pi, non_blocking=True)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+        units.append(sum(n * x["sweeps"] for n, x in zip(nnz, st)))
+        b.close()
+    ms, units = ms[1:], units[1:]  # the first call warms the allocator
+    h2d = sum(ctypes.sizeof(native.Params) + 16 * int(p["H"]) for p in ps)
+    return {"value": sum(units) / (sum(ms) / 1e3), "unit": UNIT, "ms_per_step": statistics.median(ms),
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(hv.numel()) * 12}
+
+
+def _timed(torch, stream, fn, reps):
+    """Median device time (events on the launching stream) of fn() over reps calls."""
+    ms, last = [], None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        last = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms), last
+
+
+def batched_vs_per_instance(args, ps, b, native, torch, dev, stream):
+    """The batched graph solve against the plain FP32 form: every instance solved on its
+    own (implicit FP32 sweeps, same certification), one after another on the same GPU."""
+    ms_b, (_, V64b, _, stb, _) = _timed(torch, stream, lambda: b.value_iterate(tol=args.tol), 3)
+    ms_ba, (_, V64a, _, sta, _) = _timed(torch, stream, lambda: b.value_iterate(tol=args.tol, accurate=True), 3)
+    ms_ff, _ = _timed(torch, stream, lambda: b.value_iterate(tol=args.tol, fp32_only=True), 3)
+    ms_ = [native.MDP.build(p, fmt="implicit") for p in ps]
+    for m in ms_:
+        m.value_iterate(tol=args.tol)
+
+    def solo():
+        return [m.value_iterate(tol=args.tol) for m in ms_]
+
+    ms_s, res = _timed(torch, stream, solo, 2)
+    off = b.offsets
+    dv = 0.0
+    for i, (_, V64s, _, st) in enumerate(res):
+        dv = max(dv, float((V64b[off[i]:off[i + 1]] - V64s).abs().max()))
+    for m in ms_:
+        m.close()
+    return {
+        "per_instance_fp32_ms": ms_s, "batched_ms": ms_b, "speedup": ms_s / ms_b,
+        "batched_fp32_loop_only_ms": ms_ff, "batched_accurate_ms": ms_ba,
+        "per_instance_sweeps_total": int(sum(r[3]["sweeps"] for r in res)),
+        "batched_sweeps_total": int(sum(s["sweeps"] for s in stb)),
+        "max_abs_V64_batched_minus_per_instance": dv,
+        "all_certified": all(s["certified"] == 1 for s in stb) and all(r[3]["certified"] == 1 for r in res),
+        "accurate_all_certified": all(s["certified"] == 1 for s in sta),
+        "note": "per-instance = vc_value_iterate on each of the instances in turn (implicit FP32 form)",
+    }
+
+
+def cpu_baseline_batched(ps_all, min_seconds: float = 10.0):
+    """The FP64 oracle's Bellman sweeps over the batch's instances in order, single thread."""
+    import numpy as np
+
+    import oracle
+
+    updates, done = 0, 0
+    t0 = time.perf_counter()
+    for p in ps_all:
+        S = oracle.num_states(p)
+        V, Vn = np.zeros(S), np.zeros(S)
+        updates += oracle.sweep_states(p, V, Vn, 0, S, 1)
+        done += 1
+        if time.perf_counter() - t0 > min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one Jacobi sweep from V=0 of each of the first {done} instances ({updates} updates, "
+                      f"{dt:.1f} s)"}
+
+
+def comparisons(args, native, torch, dev, stream):
+    """BF16 storage and the adjoint gradient, each timed against the plain FP32 form on the
+    same GPU at the same certified residual."""
+    from paper_2012_12419_gb300 import inputs
+
+    out = {}
+    p = inputs.workload("precision")
+    res = {}
+    for layout in ("padded", "canonical", "padded+sliced", "canonical+sliced"):
+        for form in ("csr_f32", "csr_bf16"):
+            m = native.MDP.build(p, fmt=form, padded=layout.startswith("padded"), sliced=layout.endswith("sliced"))
+            m.autotune(reps=3)
+            info = m.info()
+            V = torch.zeros(info["S"], dtype=torch.float32, device=dev)
+
+            def solve():
+                V.zero_()
+                return m.value_iterate(V, tol=args.tol)
+
+            solve()
+            t, (_, V64, _, st) = _timed(torch, stream, solve, 2)
+            res[(layout, form)] = V64
+            out[f"precision_{form}_{layout}"] = {
+                "time_to_residual_ms": t, "sweeps": int(st["sweeps"]), "ms_fp32_sweeps": st["ms_fp32"],
+                "ms_fp64_refine": st["ms_fp64"], "certified": st["certified"] == 1,
+                "updates_per_s": info["nnz_logical"] * st["sweeps"] / (t / 1e3),
+                "sweep_bytes": int(info["sweep_bytes"]), "nnz_stored": int(info["nnz_stored"])}
+            m.close()
+        f32, bf = res[(layout, "csr_f32")], res[(layout, "csr_bf16")]
+        out[f"precision_{layout}_bf16_speedup"] = (out[f"precision_csr_f32_{layout}"]["time_to_residual_ms"]
+                                                   / out[f"precision_csr_bf16_{layout}"]["time_to_residual_ms"])
+        out[f"precision_{layout}_bf16_minus_f32_max_rel"] = float(((bf - f32).abs() / f32.abs().clamp_min(1.0)).max())
+    res.clear()
+
+    g = inputs.workload("grad")
+    m = native.MDP.build(g, fmt="implicit")
+    S = m.S
+    rho = torch.zeros(S, dtype=torch.float64, device=dev)
+    rho[: 2 * (g["Q"] + 1)] = 1.0 / (2 * (g["Q"] + 1))  # uniform over the states with every host empty
+    t_fwd, (_, V64, pi, st) = _timed(torch, stream, lambda: m.value_iterate(tol=args.tol), 3)
+    t_adj, (dJ, _, gs) = _timed(torch, stream, lambda: m.value_grad(V64, pi, rho, tol=args.tol), 3)
+    t_adj11, (dJ11, _, gs11) = _timed(torch, stream, lambda: m.value_grad(V64, pi, rho, tol=1e-11), 3)
+    out["grad_forward_fp32_ms"] = t_fwd
+    out["grad_adjoint_ms"] = t_adj
+    out["grad_adjoint_over_forward"] = t_adj / t_fwd
+    out["grad_adjoint_tol1e-11_ms"] = t_adj11
+    out["grad_adjoint_sweeps"] = int(gs["sweeps"])
+    out["grad_forward_sweeps"] = int(st["sweeps"])
+    out["grad_nnz_transpose"] = int(gs["nnz_transpose"])
+    out["grad_max_abs_dJ_tol1e-6_minus_tol1e-11"] = float((dJ - dJ11).abs().max())
+    m.close()
+    return out
 
 
 # DRAM bytes (read + write) of one sweep-kernel launch from an ncu capture of this exact
@@ -246,7 +530,7 @@ def measured_traffic(args):
     import hashlib
 
     key = (args.workload, args.form, args.padded)
-    if key not in TRAFFIC_BYTES:
+    if args.sliced or key not in TRAFFIC_BYTES:
         return None
     h = hashlib.sha256()
     for name in ("vc_csr.cu", "vc_internal.cuh"):
@@ -280,7 +564,9 @@ def roofline(m, info, args, V, dev, stream):
     achieved = info["sweep_bytes"] / avg_s / 1e9
     implicit = args.form == "implicit"
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_post+k_max" if implicit else ("k_csr_tma" if info["csr_pipelined"] else "k_csr_direct"),
+            "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_post+k_max" if implicit else (
+                ("k_sell_ring" if info["csr_pipelined"] else "k_sell") if info["csr_sliced"]
+                else ("k_csr_tma" if info["csr_pipelined"] else "k_csr_direct")),
             "bytes_per_launch": int(info["sweep_bytes"]), "launch_us": avg_s * 1e6,
             "plan": {k: int(info[k]) for k in ("csr_pipelined", "csr_tile_states", "csr_stages", "csr_ctas_per_sm",
                                                 "csr_smem_bytes")}}
@@ -314,14 +600,21 @@ def e2e(args, p, native, torch, nnz):
             "d2h_bytes_per_step": d2h, "ms_per_step": statistics.median(ms)}
 
 
+def _best_plan(m):
+    """The autotuner's chosen line (kernel, tile, stages, CTAs/SM, smem, us per sweep)."""
+    rows = m.autotune_report().strip().splitlines()[1:]
+    return min(rows, key=lambda r: float(r.split()[-1])) if rows else None
+
+
 def variants(args, p, native, torch, dev, stream):
     """The other storage forms of the same workload, same step, device-timed."""
     out = {}
-    forms = [("implicit", False), ("csr_f32", False), ("csr_f32", True), ("csr_bf16", False), ("csr_bf16", True)]
-    for form, padded in forms:
-        if form == args.form and padded == args.padded:
+    forms = [("implicit", False, False)] + [(f, pd, sl) for sl in (False, True) for f in ("csr_f32", "csr_bf16")
+                                             for pd in (False, True)]
+    for form, padded, sliced in forms:
+        if form == args.form and padded == args.padded and sliced == args.sliced:
             continue
-        m = native.MDP.build(p, fmt=form, padded=padded)
+        m = native.MDP.build(p, fmt=form, padded=padded, sliced=sliced)
         if form != "implicit":
             m.autotune(reps=5)
         info = m.info()
@@ -342,11 +635,16 @@ def variants(args, p, native, torch, dev, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / reps
-        out[form + ("+padded" if padded else "")] = {
+        best = _best_plan(m) if form != "implicit" else None
+        sweep_us = float(best.split()[-1]) if best else None
+        out[form + ("+padded" if padded else "") + ("+sliced" if sliced else "")] = {
             "time_to_residual_ms": t, "updates_per_s": info["nnz_logical"] * sweeps / reps / (t / 1e3),
+            "sweep_us": sweep_us,
+            "sweep_hbm_frac": (info["sweep_bytes"] / (sweep_us * 1e-6) / 1e9 / peaks()[0]) if sweep_us else None,
             "ms_fp32_sweeps": st["ms_fp32"], "ms_fp64_refine": st["ms_fp64"],
             "sweeps": sweeps // reps, "nnz_stored": int(info["nnz_stored"]),
-            "sweep_bytes": int(info["sweep_bytes"])}
+            "nnz_sliced": int(info["nnz_sliced"]), "sweep_bytes": int(info["sweep_bytes"]),
+            "tuned": best}
         m.close()
     return out
 
@@ -382,28 +680,50 @@ def run_reference(args):
     import oracle
     from paper_2012_12419_gb300 import inputs
 
-    p = inputs.workload(args.workload)
-    S = oracle.num_states(p)
-    V = np.zeros(S)
-    Vn = np.zeros(S)
     stride = 16  # one step: backups of every 16th state (about 1/16 of a sweep)
-    for _ in range(max(3, args.warmup)):
-        oracle.sweep_states(p, V, Vn, 0, S, stride * 4)
+    if args.workload == "batched":
+        # one step: backups of every 16th state of every instance (1/16 of a batch sweep)
+        ps = inputs.batch_params(512, seed=2)
+        Ss = [oracle.num_states(p) for p in ps]
+        target = sum(Ss)
+        bufs = {}
+
+        def one(k):
+            n, i, done = 0, (k * 37) % len(ps), 0
+            while done < target:
+                p, S = ps[i], Ss[i]
+                if i not in bufs:
+                    bufs[i] = (np.zeros(S), np.zeros(S))
+                n += oracle.sweep_states(p, bufs[i][0], bufs[i][1], k % stride, S, stride)
+                done += S
+                i = (i + 1) % len(ps)
+            return n
+    else:
+        p = inputs.workload(args.workload)
+        S = oracle.num_states(p)
+        V = np.zeros(S)
+        Vn = np.zeros(S)
+
+        def one(k):
+            return oracle.sweep_states(p, V, Vn, k % stride, S, stride)
+    for k in range(max(3, args.warmup)):
+        one(k)
     ups, secs = 0, 0.0
     for k in range(args.steps):
         t0 = time.perf_counter()
-        ups += oracle.sweep_states(p, V, Vn, k % stride, S, stride)
+        ups += one(k)
         secs += time.perf_counter() - t0
     value = ups / secs
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": secs / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "impl": "reference",
+        "higher_is_better": True, "scaling": "strong" if args.workload == "batched" else "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD_DESC[args.workload], "form": "oracle enumeration (FP64, single thread)",
                    "tol": args.tol},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: Jacobi backups of every {stride}th state of the instance"},
+                         "sample": f"each step: Jacobi backups of every {stride}th state of the "
+                                   + ("512 instances" if args.workload == "batched" else "instance")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -413,6 +733,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_native(args)
 

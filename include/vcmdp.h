@@ -60,6 +60,8 @@ extern "C" {
 #define VC_PADDED 16   /* CSR rows padded to exactly 2H+3 entries, infeasible rows included */
 #define VC_DIRECT 32   /* CSR sweeps read rows straight from global memory (no shared-memory
                           pipeline); same arithmetic and results, for comparison */
+#define VC_SLICED 64   /* also build the sliced copy of the matrix (vc_mdp_slice) and sweep it;
+                          with VC_DIRECT the sliced sweep reads global memory directly */
 
 /* value types for vc_build_mdp_csr */
 #define VC_VAL_F32 0
@@ -99,6 +101,9 @@ typedef struct vc_info {
     int32_t csr_stages;     /* tiles in flight per CTA */
     int32_t csr_ctas_per_sm;/* resident CTAs per SM of the CSR sweep */
     int32_t csr_smem_bytes; /* dynamic shared memory per CTA */
+    int32_t csr_sliced;     /* 1 if FP32 sweeps run on the sliced copy (vc_mdp_slice) */
+    int32_t reserved;
+    int64_t nnz_sliced;     /* entries of the sliced copy incl. padding (0 if none) */
 } vc_info;
 
 /* Statistics of vc_value_iterate (host struct, filled on return). */
@@ -131,6 +136,7 @@ int64_t vc_kernel_launches(void);
  * entries are bf16(p) rounded to nearest even from the FP64 probability; each row
  * carries scale = 1/sum_j bf16(p_j) (FP64 sum, rounded to FP32).  Every handle built
  * here also keeps the FP64 model for refinement, certification and gradients.
+ * fmt | VC_SLICED also builds the sliced copy (vc_mdp_slice) before returning.
  * Errors: VC_ERR_ARG for H outside 1..16, C < 1, Q < 0, S >= 2^31, rates <= 0 (mu,
  * lambda; delta >= 0), f outside (0,1), gamma outside (0,1); VC_ERR_OOM.
  */
@@ -162,6 +168,23 @@ int vc_mdp_info(const vc_mdp* m, vc_info* out);
  */
 int vc_mdp_export_csr(const vc_mdp* m, int64_t* row_ptr, int32_t* col, void* val, float* row_scale, float* R,
                       void* stream);
+
+/*
+ * Add a sliced copy of the stored matrix to a CSR handle and make the FP32 sweeps use
+ * it.  This is a storage layout for the Eq. 18 backup of the same rows, not an operation
+ * of the paper: SELL-C-sigma (Kreutzer et al., SIAM J. Sci. Comput. 36(5), 2014) with 32
+ * states per slice, states sorted inside windows of 4096 by feasible-action mask and row
+ * length; each (slice, action) block stores its rows lane-fastest, padded to the block's
+ * longest feasible row with zero-valued entries.  Infeasible rows store nothing.  The
+ * sweep keeps the CSR kernels' arithmetic (FMA in column order, lowest-index argmax), so
+ * V, pi and the residual are bitwise those of the CSR sweep.  The CSR stays (FP64
+ * refinement of user matrices, export, autotuner candidates); the copy adds
+ * nnz_sliced x (4 + value bytes) + 4 S A (+ 4 S A for BF16) bytes.  Runs on `stream`
+ * and synchronises it.  The sweep stages tiles of slices through shared memory (the
+ * direct-load sliced kernel on VC_DIRECT handles or when no tile fits).  Errors:
+ * VC_ERR_ARG for a VC_IMPLICIT handle or A > 31; VC_ERR_OOM.  Idempotent.
+ */
+int vc_mdp_slice(vc_mdp* m, void* stream);
 
 /*
  * Value iteration (Algorithm 3).  V: [S] float, in: V^0 (zeros = the paper's step 1,
@@ -233,8 +256,9 @@ int vc_evaluate_policy(vc_mdp* m, const int32_t* pi, double* V_pi, double tol, i
 
 /*
  * Autotuner of the CSR sweep schedule: times every feasible shared-memory tiling (states
- * per tile, pipeline stages, CTAs per SM) and the direct-load kernel on this handle, reps
- * sweeps each on `stream`, and keeps the fastest for later sweeps.  *best_us (host,
+ * per tile, pipeline stages, CTAs per SM), the direct-load kernel and, when the handle
+ * has a sliced copy, the sliced sweep at several CTAs per SM, reps sweeps each on
+ * `stream`, and keeps the fastest for later sweeps.  *best_us (host,
  * nullable) receives its time per sweep.  No-op for VC_IMPLICIT handles.  The schedule
  * never changes results: every candidate does the same arithmetic in the same order.
  */

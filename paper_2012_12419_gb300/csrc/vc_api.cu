@@ -34,7 +34,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 static void free_mdp(Mdp* m) {
     if (!m) return;
     void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64, m->V64a,
-                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->ctl};
+                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->ctl, m->sell_off,
+                    m->sell_col, m->sell_val, m->sell_R, m->sell_scale, m->sell_perm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->ctl_host) cudaFreeHost(m->ctl_host);
@@ -192,6 +193,24 @@ const char* vc_last_error(void) { return g_err.c_str(); }
 
 int64_t vc_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+// Builds the sliced copy and switches the FP32 sweep to it: the first pipelined tiling that
+// fits, else (or for VC_DIRECT handles) the direct sliced kernel at 4 CTAs per SM.
+static int use_sliced(Mdp* m, cudaStream_t st) {
+    int rc = build_sliced(m, st);
+    if (rc) return rc;
+    std::vector<CsrPlan> cands;
+    if (!(m->fmt & VC_DIRECT) && (rc = sell_plans(m, st, cands))) return rc;
+    if (cands.empty()) {
+        CsrPlan P;
+        P.sliced = true;
+        P.ctas_per_sm = 4;
+        m->plan = P;
+    } else {
+        m->plan = cands.front();
+    }
+    return VC_OK;
+}
+
 int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
     g_err.clear();
     if (!out) return fail(VC_ERR_ARG, "out is NULL");
@@ -199,9 +218,9 @@ int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
     const int base = fmt & 0xF;
     if (base != VC_IMPLICIT && base != VC_CSR_F32 && base != VC_CSR_BF16)
         return fail(VC_ERR_ARG, "unknown format");
-    if ((fmt & ~(0xF | VC_PADDED | VC_DIRECT)) != 0) return fail(VC_ERR_ARG, "unknown format flag");
-    if (base == VC_IMPLICIT && (fmt & (VC_PADDED | VC_DIRECT)))
-        return fail(VC_ERR_ARG, "VC_PADDED / VC_DIRECT need a CSR format");
+    if ((fmt & ~(0xF | VC_PADDED | VC_DIRECT | VC_SLICED)) != 0) return fail(VC_ERR_ARG, "unknown format flag");
+    if (base == VC_IMPLICIT && (fmt & (VC_PADDED | VC_DIRECT | VC_SLICED)))
+        return fail(VC_ERR_ARG, "VC_PADDED / VC_DIRECT / VC_SLICED need a CSR format");
     Mdp* m = new Mdp();
     m->fmt = fmt;
     m->num_sms = device_sms();
@@ -210,6 +229,7 @@ int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
     if (!rc && base != VC_IMPLICIT) rc = build_csr_from_model(m, st);
     if (!rc && base == VC_IMPLICIT) rc = count_model_rows(m, st);  // logical nnz, nothing stored
     if (!rc) rc = alloc_work(m);
+    if (!rc && (fmt & VC_SLICED)) rc = use_sliced(m, st);
     if (rc) {
         free_mdp(m);
         return rc;
@@ -265,13 +285,28 @@ int vc_mdp_info(const vc_mdp* mh, vc_info* out) {
     out->csr_stages = m->plan.stages;
     out->csr_ctas_per_sm = m->plan.ctas_per_sm;
     out->csr_smem_bytes = m->plan.smem;
+    out->csr_sliced = m->plan.sliced ? 1 : 0;
+    out->nnz_sliced = m->nnz_sliced;
     const int64_t rows = (int64_t)m->S * m->A;
     const int base = m->fmt & 0xF;
     if (base == VC_IMPLICIT)
         out->sweep_bytes = 8 * (int64_t)m->S;
+    else if (m->plan.sliced)
+        out->sweep_bytes = sell_sweep_bytes(m);
     else
         out->sweep_bytes = m->nnz_stored * ((base == VC_CSR_BF16 ? 2 : 4) + 4) + rows * (8 + 4) +
                            (base == VC_CSR_BF16 ? rows * 4 : 0) + 8 * (int64_t)m->S;
+    return VC_OK;
+}
+
+int vc_mdp_slice(vc_mdp* mh, void* stream) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    Mdp* m = (Mdp*)mh;
+    if ((m->fmt & 0xF) == VC_IMPLICIT) return fail(VC_ERR_ARG, "an implicit handle stores no matrix to slice");
+    int rc = use_sliced(m, (cudaStream_t)stream);
+    if (rc) return rc;
+    m->fmt |= VC_SLICED;
     return VC_OK;
 }
 

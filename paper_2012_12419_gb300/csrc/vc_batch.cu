@@ -465,6 +465,11 @@ static int build_tiles(Batch* b, cudaStream_t st) {
     return VC_OK;
 }
 
+// Kernels in one pass of each loop body (two sweeps per pass); the launch counter adds
+// passes x this after every graph launch, since the graph runs them without a host call.
+constexpr int kViBodyKernels = 5;
+constexpr int kCorrBodyKernels = 3;
+
 template <int MH>
 static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
     const BatchCtl c = ctl_of(b);
@@ -705,8 +710,9 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     // ---- FP32 value iteration of every instance: one graph launch
     VC_CUDA(cudaMemcpyAsync(b->Va, V, 4 * T, cudaMemcpyDeviceToDevice, st));
     if ((rc = reset_loop(b, tol, max_sweeps, st))) return rc;
-    count_launches(1);
     VC_CUDA(cudaGraphLaunch(b->x_vi, st));
+    long long vi_iters = 0, corr_iters = 0;
+    VC_CUDA(cudaMemcpyAsync(&vi_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
     count_launches(1);
     k_bselect<float, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->final_buf, b->Va,
                                                           b->Vb, V);
@@ -716,6 +722,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     VC_CUDA(cudaMemcpyAsync(done.data(), b->done, 4 * N, cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaMemcpyAsync(sweeps.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaStreamSynchronize(st));
+    count_launches((int)(vi_iters / 2 * kViBodyKernels));
     bool all_cert = false;
     if (!(flags & VC_ITER_FP32_ONLY)) {
         // ---- refinement of every instance: argmax policy, FP64 residual, FP32 correction
@@ -741,8 +748,8 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             if ((rc = reset_loop(b, 0.5 * tol, eval_max, st))) return rc;
             int herr = 0;
             VC_CUDA(cudaMemcpyAsync(&herr, b->err, 4, cudaMemcpyDeviceToHost, st));
-            count_launches(1);
             VC_CUDA(cudaGraphLaunch(b->x_corr, st));
+            VC_CUDA(cudaMemcpyAsync(&corr_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
             count_launches(1);
             k_baxpy<<<b->grid, kThreads, 0, st>>>(b->E0, b->E1, b->d_desc, b->d_tiles, b->ntiles, b->final_buf,
                                                   b->V64);
@@ -756,6 +763,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             VC_CUDA(cudaMemcpyAsync(b->V64, b->V64b, 8 * T, cudaMemcpyDeviceToDevice, st));
             VC_CUDA(cudaMemcpyAsync(b->pi, b->pi2, 4 * T, cudaMemcpyDeviceToDevice, st));
             VC_CUDA(cudaStreamSynchronize(st));
+            count_launches((int)(corr_iters / 2 * kCorrBodyKernels));
             if (herr) return fail(VC_ERR_CUDA, "internal: batched refinement policy infeasible");
             all_cert = true;
             for (size_t i = 0; i < N; i++) {
@@ -825,7 +833,7 @@ int vc_batch_autotune(vc_batch* bh, int sweeps, double* best_ms, void* stream) {
                 VC_CUDA(cudaMemsetAsync(b->Va, 0, 4 * (size_t)b->total, st));
                 if ((rc = reset_loop(b, 1e-30, sweeps, st))) return rc;
                 VC_CUDA(cudaEventRecord(e0, st));
-                count_launches(1);
+                count_launches((sweeps + 1) / 2 * kViBodyKernels);
                 VC_CUDA(cudaGraphLaunch(b->x_vi, st));
                 VC_CUDA(cudaEventRecord(e1, st));
                 VC_CUDA(cudaEventSynchronize(e1));

@@ -21,66 +21,11 @@
 #include <vector>
 
 #include "vc_internal.cuh"
+#include "vc_ptx.cuh"
 
 namespace vc {
 
 constexpr int kNW = 8;                      // consumer warps of the pipelined kernel
-constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier polling (~0.5-2 s worst case)
-
-// --------------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Polls the barrier phase with a hard iteration limit; false if it never completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (it >= 32) __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ uint64_t l2_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-// Global -> shared bulk copy; both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
 // ----------------------------------------------------------------------- tile layout
 struct StageLayout {
     int off_rp, off_R, off_scale, off_col, off_val, bytes;
@@ -736,6 +681,7 @@ static void launch_direct(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStrea
 }
 
 int csr_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st) {
+    if (m->plan.sliced) return sell_sweep32(m, V_in, V_out, pi, qgap, sc, st);
     const CsrArgs a = args_of(m, V_in, V_out, pi, qgap);
     const bool bf16 = (m->fmt & 0xF) == VC_CSR_BF16;
     count_launches(1);
@@ -807,6 +753,17 @@ int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
     int rc = enumerate_plans(m, st, cands);
     if (rc) return rc;
     cands.push_back(CsrPlan());  // direct kernel
+    if (m->sell_perm) {
+        std::vector<CsrPlan> sp;
+        if ((rc = sell_plans(m, st, sp))) return rc;
+        cands.insert(cands.end(), sp.begin(), sp.end());
+        for (int bps : {2, 4, 8}) {
+            CsrPlan P;
+            P.sliced = true;
+            P.ctas_per_sm = bps;
+            cands.push_back(P);
+        }
+    }
     if (reps < 1) reps = 1;
     float* A = m->Vb;
     float* B = m->E0;
@@ -831,8 +788,13 @@ int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
         VC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         const double us = 1e3 * ms / reps;
         char line[160];
-        snprintf(line, sizeof(line), "%s %d %d %d %d %.2f\n", P.tma ? "pipelined" : "direct", P.ts, P.stages,
-                 P.ctas_per_sm, P.smem, us);
+        char kname[40];
+        if (P.sliced && P.tma)
+            snprintf(kname, sizeof(kname), "sliced-pipelined-w%d", P.warps);
+        else
+            snprintf(kname, sizeof(kname), "%s", P.sliced ? "sliced-direct" : (P.tma ? "pipelined" : "direct"));
+        snprintf(line, sizeof(line), "%s %d %d %d %d %.2f\n", kname, P.sliced ? 32 * (P.tma ? P.ts : 1) : P.ts,
+                 P.stages, P.ctas_per_sm, P.smem, us);
         m->tune_report += line;
         if (us < best) {
             best = us;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/vcmdp.h"
 
@@ -291,6 +292,24 @@ __device__ __forceinline__ T block_max(T v) {
     return r;
 }
 
+// Block-wide max of a non-negative float for any block size up to 1024 threads (a whole
+// number of warps); result valid in thread 0.  Every thread of the block must call it.
+__device__ __forceinline__ float block_max_dyn(float v) {
+    __shared__ float part[32];
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int nw = (int)(blockDim.x >> 5);
+    if (l == 0) part[w] = v;
+    __syncthreads();
+    float r = 0.0f;
+    if (threadIdx.x < 32) {
+        r = (l < nw) ? part[l] : 0.0f;
+        r = warp_max(r);
+    }
+    __syncthreads();
+    return r;
+}
+
 __device__ __forceinline__ unsigned int fbits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
@@ -368,6 +387,7 @@ __device__ void finish_block(const SweepCtl& sc, T res, T vmax, long long sweep)
 // entries, at most `cap`) are staged in shared memory by bulk asynchronous copies.
 struct CsrPlan {
     bool tma = false;
+    bool sliced = false; // sweep the sliced layout (k_sell) instead of the CSR
     int apad = 8;        // lanes per state (power of two >= A)
     int ts = 0;          // states per tile
     int64_t cap = 0;     // max entries of a tile (+ alignment slack)
@@ -375,6 +395,7 @@ struct CsrPlan {
     int ctas_per_sm = 0;
     int smem = 0;        // dynamic shared memory per CTA
     int64_t ntiles = 0;
+    int warps = 0;       // consumer warps per CTA (sliced ring sweep)
 };
 
 struct Mdp {
@@ -395,6 +416,16 @@ struct Mdp {
     float* R = nullptr;         // [S*A], -inf = infeasible
     CsrPlan plan;
     std::string tune_report;    // candidates and times of the last autotune
+    // sliced copy of the stored matrix (SELL-C-sigma, C = 32 states per slice): block
+    // (g, a) holds width(g, a) x 32 entries, entry j of lane l at (off[g*A+a] + j)*32 + l
+    int64_t sell_slices = 0, nnz_sliced = 0;
+    int64_t* sell_off = nullptr;   // [G*A + 1] block offsets in units of 32 entries
+    int32_t* sell_col = nullptr;
+    void* sell_val = nullptr;
+    float* sell_R = nullptr;       // [G*A*32], -inf = infeasible or padding lane
+    float* sell_scale = nullptr;   // [G*A*32] (BF16 only)
+    int32_t* sell_perm = nullptr;  // [G*32] state of (slice, lane), -1 = padding lane
+    std::vector<int64_t> sell_slice_rows;  // host: rows of 32 entries per slice (planning)
     // work buffers (owned)
     float* Vb = nullptr;        // FP32 ping-pong partner
     float* U32 = nullptr;       // FP32 post-decision values (implicit)
@@ -423,6 +454,11 @@ int count_model_rows(Mdp* m, cudaStream_t st);
 int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
                    const float* row_scale, const float* R, cudaStream_t st);
 int plan_csr(Mdp* m, cudaStream_t st);
+// Sliced layout (vc_sell.cu): build from the stored CSR, sweep, sweep bytes.
+int build_sliced(Mdp* m, cudaStream_t st);
+int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out);
+int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st);
+int64_t sell_sweep_bytes(const Mdp* m);
 int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us);
 
 // Grid of the persistent state-parallel kernels.

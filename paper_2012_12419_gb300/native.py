@@ -29,6 +29,7 @@ VC_CSR_F32 = 1
 VC_CSR_BF16 = 2
 VC_PADDED = 16
 VC_DIRECT = 32
+VC_SLICED = 64
 VC_VAL_F32 = 0
 VC_VAL_BF16 = 1
 VC_ITER_FP32_ONLY = 1
@@ -40,7 +41,7 @@ EXPORTS = [
     "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
-    "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy",
+    "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice",
 ]
 
 
@@ -66,6 +67,7 @@ class Info(ctypes.Structure):
         ("device_bytes", ctypes.c_int64), ("sweep_bytes", ctypes.c_int64),
         ("has_model", ctypes.c_int32), ("csr_pipelined", ctypes.c_int32), ("csr_tile_states", ctypes.c_int32),
         ("csr_stages", ctypes.c_int32), ("csr_ctas_per_sm", ctypes.c_int32), ("csr_smem_bytes", ctypes.c_int32),
+        ("csr_sliced", ctypes.c_int32), ("reserved", ctypes.c_int32), ("nnz_sliced", ctypes.c_int64),
     ]
 
 
@@ -151,6 +153,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(dbl), vp]
         L.vc_batch_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
         L.vc_batch_destroy.argtypes = [vp]
+        L.vc_mdp_slice.argtypes = [vp, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -210,10 +213,11 @@ class MDP:
     # ------------------------------------------------------------------ construction
     @classmethod
     def build(cls, params: dict, fmt: str = "implicit", padded: bool = False, direct: bool = False,
-              stream=None) -> "MDP":
+              sliced: bool = False, stream=None) -> "MDP":
         L = load()
         _dev()
-        code = FORMATS[fmt] | (VC_PADDED if padded else 0) | (VC_DIRECT if direct else 0)
+        code = (FORMATS[fmt] | (VC_PADDED if padded else 0) | (VC_DIRECT if direct else 0)
+                | (VC_SLICED if sliced else 0))
         cp, keep = _params(params)
         h = ctypes.c_void_p()
         _check(L.vc_build_mdp(ctypes.byref(cp), code, _stream(stream), ctypes.byref(h)))
@@ -236,6 +240,12 @@ class MDP:
         _check(L.vc_build_mdp_csr(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), vdt, _ptr(row_scale),
                                   _ptr(R), float(gamma), _stream(stream), ctypes.byref(h)))
         return cls(h)
+
+    def slice(self, stream=None) -> "MDP":
+        """Add the sliced copy of the stored matrix and sweep it from now on."""
+        _check(load().vc_mdp_slice(self._h, _stream(stream)))
+        self._info = None
+        return self
 
     def close(self):
         if self._h is not None and self._h.value:
@@ -474,7 +484,7 @@ def exported_symbols(path: str | None = None):
 
 def fmt_name(code: int) -> str:
     inv = {v: k for k, v in FORMATS.items()}
-    return inv[code & 0xF] + ("+padded" if code & VC_PADDED else "")
+    return inv[code & 0xF] + ("+padded" if code & VC_PADDED else "") + ("+sliced" if code & VC_SLICED else "")
 
 
 __all__ = ["MDP", "solve", "VcError", "load", "exported_symbols", "np"]

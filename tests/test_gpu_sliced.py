@@ -1,0 +1,182 @@
+"""The sliced (SELL-C-sigma) copy of the stored matrix and its FP32 sweep.
+
+* one sweep on the sliced copy equals the CSR sweep bitwise (values, policy, Q-gap) for
+  the generated model in every stored form and for arbitrary CSR matrices (ragged rows,
+  infeasible actions, A from 1 to 31, S from 1 to several windows of 4096 with a ragged
+  last slice);
+* the copy's size (entries incl. padding) equals a host-side recomputation of the layout
+  from the oracle's CSR (sort key, slice widths) exactly;
+* a full solve on the sliced copy is certified and matches the oracle within 1e-6;
+* the autotuner's sliced candidates keep the results; invalid requests are errors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2012_12419_gb300 import inputs
+
+from gpu_common import native_or_skip, policy_mismatches, rel_err
+
+pytestmark = pytest.mark.gpu
+
+MID = inputs.make_params(4, 4, 6, 0.95, seed=7)      # S = 8750: three windows, ragged slice
+TINY = inputs.workload("tiny")                         # S = 640: one partial window
+CSR_FORMS = [("csr_f32", False), ("csr_f32", True), ("csr_bf16", False), ("csr_bf16", True)]
+
+
+def _sweep(m, V):
+    import torch
+
+    Vo = torch.empty_like(V)
+    pi = torch.empty(V.numel(), dtype=torch.int32, device=V.device)
+    gap = torch.empty_like(V)
+    m.bellman32(V, Vo, pi, gap)
+    torch.cuda.synchronize()
+    return Vo, pi, gap
+
+
+def _host_sliced_entries(row_ptr, R, S, A, C=32, sigma=4096):
+    """Entries of the sliced layout, recomputed on the host from the layout's definition:
+    states sorted in windows by (feasible mask, -total length, index); per slice and
+    action the longest feasible row, times 32."""
+    L = np.diff(row_ptr).reshape(S, A)
+    feas = np.asarray(R).reshape(S, A) != -np.inf
+    L = np.where(feas, L, 0)
+    mask = (feas[:, : min(A, 30)] * (1 << np.arange(min(A, 30)))).sum(axis=1)
+    if A > 30:
+        mask = mask | (feas[:, 30:].any(axis=1) << 30)
+    tot = np.minimum(L.sum(axis=1), 0xFFFFF)
+    order = []
+    for w0 in range(0, S, sigma):
+        idx = np.arange(w0, min(S, w0 + sigma))
+        order.append(idx[np.lexsort((idx, -tot[idx], mask[idx]))])
+    order = np.concatenate(order)
+    Lo = L[order]
+    pad = (-S) % C
+    Lo = np.vstack([Lo, np.zeros((pad, A), dtype=Lo.dtype)])
+    return int(Lo.reshape(-1, C, A).max(axis=1).sum()) * C
+
+
+@pytest.mark.parametrize("fmt,padded", CSR_FORMS)
+@pytest.mark.parametrize("which", ["tiny", "mid"])
+def test_sliced_sweep_equals_csr_sweep(which, fmt, padded):
+    native = native_or_skip()
+    import torch
+
+    p = TINY if which == "tiny" else MID
+    mc = native.MDP.build(p, fmt=fmt, padded=padded, direct=True)
+    ms = native.MDP.build(p, fmt=fmt, padded=padded, sliced=True)
+    md = native.MDP.build(p, fmt=fmt, padded=padded, sliced=True, direct=True)
+    info = ms.info()
+    assert info["csr_sliced"] == 1 and info["nnz_sliced"] > 0
+    assert info["csr_pipelined"] == 1 and md.info()["csr_pipelined"] == 0
+    S, A = info["S"], info["A"]
+    rp, col, val, R = oracle.build_csr(p, padded=padded)[:4]
+    assert info["nnz_sliced"] == _host_sliced_entries(rp, R, S, A)
+    G = (S + 31) // 32
+    vbytes = 2 if fmt == "csr_bf16" else 4
+    assert info["sweep_bytes"] == (info["nnz_sliced"] * (vbytes + 4) + G * A * 32 * (8 if vbytes == 2 else 4)
+                                   + (G * A + 1) * 8 + G * 32 * 4 + 8 * S)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for scale in (100.0, 1e-3):
+        V = torch.rand(S, device="cuda", generator=g) * scale - scale / 3
+        a, b, c = _sweep(mc, V), _sweep(ms, V), _sweep(md, V)
+        for x, y, z in zip(a, b, c):
+            assert torch.equal(x, y) and torch.equal(x, z)
+    mc.close()
+    ms.close()
+    md.close()
+
+
+@pytest.mark.parametrize("S,A,seed", [(1, 1, 0), (7, 3, 1), (300, 5, 2), (5000, 9, 3), (9000, 31, 4),
+                                      (33, 2, 5)])
+def test_sliced_arbitrary_csr(S, A, seed):
+    native = native_or_skip()
+    import torch
+
+    mdp = inputs.random_csr_mdp(S, A, max_succ=min(S, 12), seed=seed, gamma=0.9)
+    val32 = mdp["val"].astype(np.float32)
+    R32 = mdp["R"].astype(np.float32)
+    dev = "cuda"
+    args = (S, A, torch.tensor(mdp["row_ptr"], device=dev), torch.tensor(mdp["col"], device=dev),
+            torch.tensor(val32, device=dev), torch.tensor(R32, device=dev), 0.9)
+    mc = native.MDP.from_csr(*args)
+    ms = native.MDP.from_csr(*args).slice()
+    assert ms.info()["nnz_sliced"] == _host_sliced_entries(mdp["row_ptr"], R32, S, A)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    V = torch.rand(S, device=dev, generator=g) * 10
+    ref = _sweep(mc, V)
+    for x, y in zip(ref, _sweep(ms, V)):
+        assert torch.equal(x, y)
+    # every schedule the autotuner may pick (pipelined / direct, CSR / sliced)
+    ms.autotune(reps=2)
+    for x, y in zip(ref, _sweep(ms, V)):
+        assert torch.equal(x, y)
+    # full certified solve on the sliced copy against the oracle on the same FP32 matrix
+    Vo, _ = oracle.vi_csr(S, A, mdp["row_ptr"], mdp["col"], val32.astype(np.float64), R32.astype(np.float64), 0.9,
+                          tol=1e-12)
+    pio, gapo = oracle.policy_csr(S, A, mdp["row_ptr"], mdp["col"], val32.astype(np.float64),
+                                  R32.astype(np.float64), 0.9, Vo)
+    _, V64, pi, st = ms.value_iterate(tol=1e-8)
+    assert st["certified"] == 1
+    assert np.max(np.abs(V64.cpu().numpy() - Vo)) <= 1e-6 * max(1.0, np.max(np.abs(Vo)))
+    assert policy_mismatches(pi.cpu().numpy(), pio, gapo)[0] == 0
+    mc.close()
+    ms.close()
+
+
+@pytest.mark.parametrize("fmt,padded", [("csr_f32", False), ("csr_bf16", True)])
+def test_sliced_solve_matches_oracle(fmt, padded):
+    native = native_or_skip()
+    p = MID
+    m = native.MDP.build(p, fmt=fmt, padded=padded, sliced=True)
+    _, V64, pi, st = m.value_iterate(tol=1e-6)
+    assert st["certified"] == 1
+    Vs, pis, gaps, _ = oracle.solve(p, tol=1e-12)
+    assert rel_err(V64.cpu().numpy(), Vs) <= 1e-6
+    assert policy_mismatches(pi.cpu().numpy(), pis, gaps)[0] == 0
+    # same iterate and sweep count as the CSR handle (bitwise-equal sweeps)
+    mc = native.MDP.build(p, fmt=fmt, padded=padded)
+    V1, _, _, s1 = mc.value_iterate(tol=1e-6, fp32_only=True)
+    V2, _, _, s2 = m.value_iterate(tol=1e-6, fp32_only=True)
+    import torch
+
+    assert s1["sweeps"] == s2["sweeps"] and torch.equal(V1, V2)
+    m.close()
+    mc.close()
+
+
+def test_autotune_with_sliced_candidates_keeps_results():
+    native = native_or_skip()
+    import torch
+
+    m = native.MDP.build(MID, fmt="csr_f32", padded=True, sliced=True)
+    V = torch.rand(m.S, device="cuda") * 50
+    ref = _sweep(m, V)
+    us = m.autotune(reps=3)
+    rep = m.autotune_report().strip().splitlines()
+    assert us > 0 and sum(1 for r in rep if r.startswith("sliced-direct")) == 3
+    assert any(r.startswith("sliced-pipelined") for r in rep)
+    for x, y in zip(ref, _sweep(m, V)):
+        assert torch.equal(x, y)
+    m.close()
+
+
+def test_sliced_errors():
+    native = native_or_skip()
+    import torch
+
+    with pytest.raises(native.VcError):
+        native.MDP.build(TINY, fmt="implicit", sliced=True)
+    mi = native.MDP.build(TINY, fmt="implicit")
+    with pytest.raises(native.VcError):
+        mi.slice()
+    mi.close()
+    S, A = 40, 32
+    mdp = inputs.random_csr_mdp(S, A, max_succ=8, seed=9, gamma=0.9)
+    m = native.MDP.from_csr(S, A, torch.tensor(mdp["row_ptr"], device="cuda"), torch.tensor(mdp["col"], device="cuda"),
+                            torch.tensor(mdp["val"].astype(np.float32), device="cuda"),
+                            torch.tensor(mdp["R"].astype(np.float32), device="cuda"), 0.9)
+    with pytest.raises(native.VcError, match="A <= 31"):
+        m.slice()
+    m.close()
