@@ -34,8 +34,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 static void free_mdp(Mdp* m) {
     if (!m) return;
     void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64, m->V64a,
-                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->ctl, m->sell_off,
-                    m->sell_col, m->sell_val, m->sell_R, m->sell_scale, m->sell_perm};
+                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->ctl, m->sell_rec, m->sell_slab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->ctl_host) cudaFreeHost(m->ctl_host);

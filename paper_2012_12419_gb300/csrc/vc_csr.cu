@@ -753,7 +753,7 @@ int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
     int rc = enumerate_plans(m, st, cands);
     if (rc) return rc;
     cands.push_back(CsrPlan());  // direct kernel
-    if (m->sell_perm) {
+    if (m->sell_slab) {
         std::vector<CsrPlan> sp;
         if ((rc = sell_plans(m, st, sp))) return rc;
         cands.insert(cands.end(), sp.begin(), sp.end());

@@ -416,15 +416,12 @@ struct Mdp {
     float* R = nullptr;         // [S*A], -inf = infeasible
     CsrPlan plan;
     std::string tune_report;    // candidates and times of the last autotune
-    // sliced copy of the stored matrix (SELL-C-sigma, C = 32 states per slice): block
-    // (g, a) holds width(g, a) x 32 entries, entry j of lane l at (off[g*A+a] + j)*32 + l
-    int64_t sell_slices = 0, nnz_sliced = 0;
-    int64_t* sell_off = nullptr;   // [G*A + 1] block offsets in units of 32 entries
-    int32_t* sell_col = nullptr;
-    void* sell_val = nullptr;
-    float* sell_R = nullptr;       // [G*A*32], -inf = infeasible or padding lane
-    float* sell_scale = nullptr;   // [G*A*32] (BF16 only)
-    int32_t* sell_perm = nullptr;  // [G*32] state of (slice, lane), -1 = padding lane
+    // sliced copy of the stored matrix (SELL-C-sigma, C = 32 states per slice): one
+    // 128-byte-aligned record per slice in a byte slab (header, state map, R / scale,
+    // col / val rows lane-fastest)
+    int64_t sell_slices = 0, nnz_sliced = 0, sell_bytes = 0;
+    int64_t* sell_rec = nullptr;          // [G + 1] record offsets in units of 128 bytes
+    unsigned char* sell_slab = nullptr;   // the records
     std::vector<int64_t> sell_slice_rows;  // host: rows of 32 entries per slice (planning)
     // work buffers (owned)
     float* Vb = nullptr;        // FP32 ping-pong partner

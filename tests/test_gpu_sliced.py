@@ -35,10 +35,10 @@ def _sweep(m, V):
     return Vo, pi, gap
 
 
-def _host_sliced_entries(row_ptr, R, S, A, C=32, sigma=4096):
-    """Entries of the sliced layout, recomputed on the host from the layout's definition:
-    states sorted in windows by (feasible mask, -total length, index); per slice and
-    action the longest feasible row, times 32."""
+def _host_slice_rows(row_ptr, R, S, A, C=32, sigma=4096):
+    """Rows (of 32 entries) of every slice of the sliced layout, recomputed on the host from
+    the layout's definition: states sorted in windows by (feasible mask, -total length,
+    index); per slice and action the longest feasible row."""
     L = np.diff(row_ptr).reshape(S, A)
     feas = np.asarray(R).reshape(S, A) != -np.inf
     L = np.where(feas, L, 0)
@@ -54,7 +54,21 @@ def _host_sliced_entries(row_ptr, R, S, A, C=32, sigma=4096):
     Lo = L[order]
     pad = (-S) % C
     Lo = np.vstack([Lo, np.zeros((pad, A), dtype=Lo.dtype)])
-    return int(Lo.reshape(-1, C, A).max(axis=1).sum()) * C
+    return Lo.reshape(-1, C, A).max(axis=1).sum(axis=1)
+
+
+def _host_sliced_entries(row_ptr, R, S, A):
+    return int(_host_slice_rows(row_ptr, R, S, A).sum()) * 32
+
+
+def _host_sweep_bytes(row_ptr, R, S, A, vbytes):
+    """Slab bytes (one record per slice: header, state map, R [and scale], col, val rows,
+    each region rounded to 128 bytes) + record offsets + V in and out."""
+    rows = _host_slice_rows(row_ptr, R, S, A)
+    r128 = lambda x: (x + 127) // 128 * 128
+    rec = 256 + 128 * A * (2 if vbytes == 2 else 1) + 128 * rows + r128(32 * vbytes * rows)
+    G = len(rows)
+    return int(rec.sum()) + 8 * (G + 1) + 8 * S
 
 
 @pytest.mark.parametrize("fmt,padded", CSR_FORMS)
@@ -73,10 +87,8 @@ def test_sliced_sweep_equals_csr_sweep(which, fmt, padded):
     S, A = info["S"], info["A"]
     rp, col, val, R = oracle.build_csr(p, padded=padded)[:4]
     assert info["nnz_sliced"] == _host_sliced_entries(rp, R, S, A)
-    G = (S + 31) // 32
     vbytes = 2 if fmt == "csr_bf16" else 4
-    assert info["sweep_bytes"] == (info["nnz_sliced"] * (vbytes + 4) + G * A * 32 * (8 if vbytes == 2 else 4)
-                                   + (G * A + 1) * 8 + G * 32 * 4 + 8 * S)
+    assert info["sweep_bytes"] == _host_sweep_bytes(rp, R, S, A, vbytes)
     g = torch.Generator(device="cuda").manual_seed(5)
     for scale in (100.0, 1e-3):
         V = torch.rand(S, device="cuda", generator=g) * scale - scale / 3
@@ -156,6 +168,7 @@ def test_autotune_with_sliced_candidates_keeps_results():
     us = m.autotune(reps=3)
     rep = m.autotune_report().strip().splitlines()
     assert us > 0 and sum(1 for r in rep if r.startswith("sliced-direct")) == 3
+    assert sum(1 for r in rep if r.startswith("sliced-pipelined")) >= 3
     assert any(r.startswith("sliced-pipelined") for r in rep)
     for x, y in zip(ref, _sweep(m, V)):
         assert torch.equal(x, y)
