@@ -334,8 +334,41 @@ __device__ __forceinline__ float ld_val<uint16_t>(const uint16_t* p) {
     return __uint_as_float((uint32_t)*p << 16);
 }
 
+// W consecutive entries of a lane's row: all loads and gathers first, then the fused
+// multiply-adds in column order onto acc.
+template <typename VT, int W>
+__device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, const float* __restrict__ V, float acc) {
+    float wv[W], gv[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+        wv[u] = ld_val<VT>(vp + u * kSellC);
+        gv[u] = __ldg(V + cp[u * kSellC]);
+    }
+#pragma unroll
+    for (int u = 0; u < W; ++u) acc = fmaf(wv[u], gv[u], acc);
+    return acc;
+}
+
+// Row sum of w entries in column order: batches of 16, then one exactly sized batch for
+// the rest (no predicated slots).
+template <typename VT>
+__device__ __forceinline__ float row_dot(const int32_t* cp, const VT* vp, int w, const float* __restrict__ V) {
+    float acc = 0.0f;
+    for (; w > kSellBatch; w -= kSellBatch, cp += kSellBatch * kSellC, vp += kSellBatch * kSellC)
+        acc = dot_fixed<VT, kSellBatch>(cp, vp, V, acc);
+    switch (w) {
+#define VC_DOT_CASE(n) \
+    case n: return dot_fixed<VT, n>(cp, vp, V, acc);
+        VC_DOT_CASE(1) VC_DOT_CASE(2) VC_DOT_CASE(3) VC_DOT_CASE(4) VC_DOT_CASE(5) VC_DOT_CASE(6) VC_DOT_CASE(7)
+        VC_DOT_CASE(8) VC_DOT_CASE(9) VC_DOT_CASE(10) VC_DOT_CASE(11) VC_DOT_CASE(12) VC_DOT_CASE(13)
+        VC_DOT_CASE(14) VC_DOT_CASE(15) VC_DOT_CASE(16)
+#undef VC_DOT_CASE
+        default: return acc;
+    }
+}
+
 // Q value of lane `lane` in block `a` of a slice record (shared or global memory):
-// R + gamma (scale) sum_j val_j V[col_j], the sum in column order in batches of 16.
+// R + gamma (scale) sum_j val_j V[col_j], the sum in column order.
 template <typename VT>
 __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a, int lane, float gamma, bool has_scale,
                                          const float* __restrict__ V) {
@@ -347,20 +380,7 @@ __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a,
     const int r0 = hdr[a], w = hdr[a + 1] - r0;
     const int32_t* cp = reinterpret_cast<const int32_t*>(rec + L.col) + r0 * kSellC + lane;
     const VT* vp = reinterpret_cast<const VT*>(rec + L.val) + r0 * kSellC + lane;
-    float acc = 0.0f;
-    for (int j0 = 0; j0 < w; j0 += kSellBatch) {
-        float wv[kSellBatch], gv[kSellBatch];
-#pragma unroll
-        for (int u = 0; u < kSellBatch; ++u) {
-            if (j0 + u < w) {
-                wv[u] = ld_val<VT>(vp + (j0 + u) * kSellC);
-                gv[u] = __ldg(V + cp[(j0 + u) * kSellC]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kSellBatch; ++u)
-            if (j0 + u < w) acc = fmaf(wv[u], gv[u], acc);
-    }
+    const float acc = row_dot<VT>(cp, vp, w, V);
     const float sc = has_scale ? reinterpret_cast<const float*>(rec + L.scale)[a * kSellC + lane] : 1.0f;
     return rr + gamma * (has_scale ? sc * acc : acc);
 }
@@ -415,6 +435,8 @@ constexpr int kHead = 512;      // barriers and per-slot words at the start of s
 static_assert(kSlots * (8 + 8 + 4 + 4) <= 384 && 384 + 8 * kSlots <= kHead, "slot words exceed the header");
 
 struct SellRingArgs {
+    FastDiv div_nb;   // division by TS * A (blocks per full tile)
+    FastDiv div_A;    // division by A
     int TS;           // slices per tile (the last tile may hold fewer)
     int64_t ntiles;
     int ring;         // bytes of the tile ring
@@ -521,7 +543,7 @@ __global__ void __launch_bounds__((kMaxRW + 1) * 32, 1) k_sell_ring(SellArgs a, 
             int gb = 0;
             if (lane == 0) gb = atomicAdd(&s_next, 1);
             gb = __shfl_sync(0xffffffffu, gb, 0);
-            i = gb / nb_full;
+            i = (int)fdiv((uint32_t)gb, t.div_nb);
             const int b = gb - i * nb_full;
             if (i >= nt_cta) break;
             const int64_t tile = blockIdx.x + (int64_t)i * gridDim.x;
@@ -536,7 +558,7 @@ __global__ void __launch_bounds__((kMaxRW + 1) * 32, 1) k_sell_ring(SellArgs a, 
             }
             const unsigned char* base = ring + *((volatile uint32_t*)&slot_pos[s]);
             float* qb = qbuf + s * t.qfloats;
-            const int sl = b / A, act = b - sl * A;
+            const int sl = (int)fdiv((uint32_t)b, t.div_A), act = b - sl * A;
             long long roff = 0;
             for (int k = 0; k < sl; ++k)
                 roff += rec_layout(A, reinterpret_cast<const int32_t*>(base + roff)[A], (int)sizeof(VT), a.has_scale)
@@ -656,6 +678,8 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
     const bool bf16 = a.has_scale;
     if (m->plan.tma) {
         SellRingArgs t;
+        t.div_nb = make_fastdiv((uint32_t)(m->plan.ts * m->A));
+        t.div_A = make_fastdiv((uint32_t)m->A);
         t.TS = m->plan.ts;
         t.ntiles = m->plan.ntiles;
         t.ring = (int)m->plan.cap;
