@@ -520,20 +520,22 @@ def comparisons(args, native, torch, dev, stream):
 
 
 # DRAM bytes (read + write) of one sweep-kernel launch from an ncu capture of this exact
-# kernel source (profiles/k_csr_tma_large_padded.md); reported only while the sources
-# hash the same, since a changed kernel voids the counters.
-TRAFFIC_SOURCE_SHA = "7757ddf9d879dd67d9e2720416a684946b17a50d8eb137b23e33f87a1a0707f6"
-TRAFFIC_BYTES = {("large", "csr_f32", True): 2_977_282_880}
+# kernel source (profiles/k_sell_ring_large_padded.md, k_sell_ring_large_canonical.md);
+# reported only while the sources hash the same, since a changed kernel voids the counters.
+TRAFFIC_SOURCES = ("vc_sell.cu", "vc_internal.cuh", "vc_ptx.cuh")
+TRAFFIC_SOURCE_SHA = "458fb1a184f264b28bc1fd4bfed42d877b4c5662f18bdde24dbfca6d13a820c1"
+TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_495_657_976,
+                 ("large", "csr_f32", False, True): 1_195_567_736}
 
 
-def measured_traffic(args):
+def measured_traffic(args, info):
     import hashlib
 
-    key = (args.workload, args.form, args.padded)
-    if args.sliced or key not in TRAFFIC_BYTES:
+    key = (args.workload, args.form, args.padded, bool(info["csr_sliced"]))
+    if key not in TRAFFIC_BYTES or not info["csr_pipelined"]:
         return None
     h = hashlib.sha256()
-    for name in ("vc_csr.cu", "vc_internal.cuh"):
+    for name in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_2012_12419_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return TRAFFIC_BYTES[key] if h.hexdigest() == TRAFFIC_SOURCE_SHA else None
@@ -560,7 +562,7 @@ def roofline(m, info, args, V, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     avg_s = e0.elapsed_time(e1) / 1e3 / n
-    traffic = measured_traffic(args)
+    traffic = measured_traffic(args, info)
     achieved = info["sweep_bytes"] / avg_s / 1e9
     implicit = args.form == "implicit"
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
