@@ -444,25 +444,46 @@ def batched_vs_per_instance(args, ps, b, native, torch, dev, stream):
     }
 
 
-def cpu_baseline_batched(ps_all, min_seconds: float = 10.0):
-    """The FP64 oracle's Bellman sweeps over the batch's instances in order, single thread."""
+def cpu_baseline_batched(ps_all, min_seconds: float = 6.0):
+    """The FP64 oracle's Bellman sweeps over the batch's instances (one sweep of each, in
+    order), single thread and with the instances spread over every host core."""
+    import threading
+
     import numpy as np
 
     import oracle
 
-    updates, done = 0, 0
+    cores = os.cpu_count() or 1
+
+    def one(p):
+        S = oracle.num_states(p)
+        return oracle.sweep_states(p, np.zeros(S), np.zeros(S), 0, S, 1)
+
+    u1, n1 = 0, 0
     t0 = time.perf_counter()
     for p in ps_all:
-        S = oracle.num_states(p)
-        V, Vn = np.zeros(S), np.zeros(S)
-        updates += oracle.sweep_states(p, V, Vn, 0, S, 1)
-        done += 1
+        u1 += one(p)
+        n1 += 1
         if time.perf_counter() - t0 > min_seconds:
             break
-    dt = time.perf_counter() - t0
-    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one Jacobi sweep from V=0 of each of the first {done} instances ({updates} updates, "
-                      f"{dt:.1f} s)"}
+    t1 = time.perf_counter() - t0
+    counts = [0] * cores
+
+    def work(k):
+        counts[k] = sum(one(p) for p in ps_all[k::cores])
+
+    t0 = time.perf_counter()
+    ts = [threading.Thread(target=work, args=(k,)) for k in range(cores)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    tn = time.perf_counter() - t0
+    un = sum(counts)
+    return {"value": un / tn, "unit": UNIT, "cores": cores, "kind": "oracle", "single_thread_value": u1 / t1,
+            "sample": f"one Jacobi sweep from V=0 of each of the {len(ps_all)} instances on {cores} threads "
+                      f"({un} updates, {tn:.1f} s); single thread: the first {n1} instances ({u1} updates, "
+                      f"{t1:.1f} s)"}
 
 
 def comparisons(args, native, torch, dev, stream):
@@ -651,25 +672,48 @@ def variants(args, p, native, torch, dev, stream):
     return out
 
 
-def cpu_baseline(p, args, min_seconds: float = 10.0):
-    """The FP64 oracle's Bellman sweeps over the same instance, single thread."""
+def _oracle_sweeps_threaded(p, nthreads: int, min_seconds: float):
+    """Full Jacobi sweeps of the oracle (as it stands) with the state space split into
+    nthreads contiguous ranges, one host thread each (the oracle's C routine runs outside
+    the Python lock, so the threads run in parallel).  Returns (updates, seconds, sweeps)."""
+    import threading
+
     import numpy as np
 
     import oracle
 
     S = oracle.num_states(p)
-    V = np.zeros(S)
-    Vn = np.zeros(S)
+    V, Vn = np.zeros(S), np.zeros(S)
+    bounds = [S * k // nthreads for k in range(nthreads + 1)]
     updates, sweeps = 0, 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < min_seconds and sweeps < 3:
-        updates += oracle.sweep_states(p, V, Vn, 0, S, 1)
+    while time.perf_counter() - t0 < min_seconds and sweeps < 50:
+        counts = [0] * nthreads
+
+        def work(k):
+            counts[k] = oracle.sweep_states(p, V, Vn, bounds[k], bounds[k + 1], 1)
+
+        ts = [threading.Thread(target=work, args=(k,)) for k in range(nthreads)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        updates += sum(counts)
         V, Vn = Vn, V
         sweeps += 1
-    dt = time.perf_counter() - t0
-    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sweeps} full Jacobi sweep(s) of the {args.workload} instance from V=0 "
-                      f"({updates} updates, {dt:.1f} s)"}
+    return updates, time.perf_counter() - t0, sweeps
+
+
+def cpu_baseline(p, args, min_seconds: float = 6.0):
+    """The FP64 oracle's Bellman sweeps over the same instance: on every host core (the
+    value) and on one thread (reported beside it)."""
+    cores = os.cpu_count() or 1
+    u1, t1, n1 = _oracle_sweeps_threaded(p, 1, min_seconds)
+    un, tn, nn = _oracle_sweeps_threaded(p, cores, min_seconds)
+    return {"value": un / tn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": u1 / t1,
+            "sample": f"full Jacobi sweeps of the {args.workload} instance from V=0: {nn} sweep(s) on {cores} "
+                      f"threads ({un} updates, {tn:.1f} s) and {n1} on one thread ({u1} updates, {t1:.1f} s)"}
 
 
 # ------------------------------------------------------------------------ reference arm
@@ -682,32 +726,44 @@ def run_reference(args):
     import oracle
     from paper_2012_12419_gb300 import inputs
 
-    stride = 16  # one step: backups of every 16th state (about 1/16 of a sweep)
-    if args.workload == "batched":
-        # one step: backups of every 16th state of every instance (1/16 of a batch sweep)
-        ps = inputs.batch_params(512, seed=2)
-        Ss = [oracle.num_states(p) for p in ps]
-        target = sum(Ss)
-        bufs = {}
+    import threading
 
-        def one(k):
-            n, i, done = 0, (k * 37) % len(ps), 0
-            while done < target:
-                p, S = ps[i], Ss[i]
-                if i not in bufs:
-                    bufs[i] = (np.zeros(S), np.zeros(S))
-                n += oracle.sweep_states(p, bufs[i][0], bufs[i][1], k % stride, S, stride)
-                done += S
-                i = (i + 1) % len(ps)
-            return n
+    stride = 16  # one step: backups of every 16th state (1/16 of a sweep), on every host core
+    cores = os.cpu_count() or 1
+    if args.workload == "batched":
+        # the 512 instances dealt round-robin to the cores; each core backs up every 16th
+        # state of its instances
+        ps = inputs.batch_params(512, seed=2)
+        bufs = [(np.zeros(oracle.num_states(p)), np.zeros(oracle.num_states(p))) for p in ps]
+
+        def part(k, c):
+            return sum(oracle.sweep_states(ps[i], bufs[i][0], bufs[i][1], k % stride, oracle.num_states(ps[i]), stride)
+                       for i in range(c, len(ps), cores))
     else:
         p = inputs.workload(args.workload)
         S = oracle.num_states(p)
         V = np.zeros(S)
         Vn = np.zeros(S)
+        # contiguous state ranges aligned to the stride, one per core
+        chunk = (S + cores - 1) // cores
+        chunk = (chunk + stride - 1) // stride * stride
 
-        def one(k):
-            return oracle.sweep_states(p, V, Vn, k % stride, S, stride)
+        def part(k, c):
+            return oracle.sweep_states(p, V, Vn, c * chunk + k % stride, min(S, (c + 1) * chunk), stride)
+
+    def one(k):
+        counts = [0] * cores
+
+        def work(c):
+            counts[c] = part(k, c)
+
+        ts = [threading.Thread(target=work, args=(c,)) for c in range(cores)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        return sum(counts)
+
     for k in range(max(3, args.warmup)):
         one(k)
     ups, secs = 0, 0.0
@@ -721,11 +777,12 @@ def run_reference(args):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "strong" if args.workload == "batched" else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD_DESC[args.workload], "form": "oracle enumeration (FP64, single thread)",
-                   "tol": args.tol},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": {"workload": WORKLOAD_DESC[args.workload],
+                   "form": f"oracle enumeration (FP64, {cores} host threads)", "tol": args.tol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: Jacobi backups of every {stride}th state of the "
-                                   + ("512 instances" if args.workload == "batched" else "instance")},
+                                   + ("512 instances" if args.workload == "batched" else "instance")
+                                   + f", split over {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
