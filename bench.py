@@ -537,6 +537,23 @@ def comparisons(args, native, torch, dev, stream):
     out["grad_nnz_transpose"] = int(gs["nnz_transpose"])
     out["grad_max_abs_dJ_tol1e-6_minus_tol1e-11"] = float((dJ - dJ11).abs().max())
     m.close()
+
+    # the paper's comparison: the greedy heuristic (Algorithm 2 as a policy) against the
+    # optimum, on the large workload, J = uniform over the states with every host empty
+    p = inputs.workload("large")
+    m = native.MDP.build(p, fmt="implicit")
+    _, V64, _, st = m.value_iterate(tol=args.tol)
+    t_g, pig = _timed(torch, stream, lambda: m.greedy_policy(), 3)
+    t_e, (Vg, n_e) = _timed(torch, stream, lambda: m.evaluate_policy(pig, tol=args.tol), 2)
+    rho = torch.zeros(m.S, dtype=torch.float64, device=dev)
+    rho[: 2 * (p["Q"] + 1)] = 1.0 / (2 * (p["Q"] + 1))
+    out["greedy_J"] = float(rho @ Vg)
+    out["optimal_J"] = float(rho @ V64)
+    out["greedy_policy_ms"] = t_g
+    out["greedy_eval_ms"] = t_e
+    out["greedy_eval_sweeps"] = int(n_e)
+    out["greedy_never_above_optimum"] = bool(torch.all(Vg <= V64 + 2 * p["gamma"] / (1 - p["gamma"]) * args.tol))
+    m.close()
     return out
 
 

@@ -251,6 +251,16 @@ int vc_bellman64(vc_mdp* m, const double* V, double* V_out, int32_t* pi, double*
  * double, in: initial guess, out: result once the sweep change is below tol.
  * *sweeps_out (host, nullable) receives the sweep count.  Synchronises `stream`.
  */
+/*
+ * The paper's greedy heuristic (Algorithm 2, "efficient VM first") read as a policy on this
+ * MDP: pi[s] = the feasible host with the largest service rate mu_a when a task waits
+ * (ties to the lowest host index), else defer (a = H).  pi: [S] int32 device, written on
+ * `stream`.  Evaluating it with vc_evaluate_policy gives the heuristic's values, which
+ * never exceed the optimum (the paper's MDP-versus-greedy comparison).  VC_ERR_ARG for a
+ * handle built from a user CSR (no model to read rates from).
+ */
+int vc_greedy_policy(vc_mdp* m, int32_t* pi, void* stream);
+
 int vc_evaluate_policy(vc_mdp* m, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
                        int64_t* sweeps_out, void* stream);
 

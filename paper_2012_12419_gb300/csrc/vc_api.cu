@@ -515,6 +515,14 @@ int vc_bellman64(vc_mdp* mh, const double* V, double* V_out, int32_t* pi, double
     return launch_bellman64(m, V, V_out, pi, qgap, sc, st);
 }
 
+int vc_greedy_policy(vc_mdp* mh, int32_t* pi, void* stream) {
+    g_err.clear();
+    if (!mh || !pi) return fail(VC_ERR_ARG, "NULL argument");
+    Mdp* m = (Mdp*)mh;
+    if (!m->has_model) return fail(VC_ERR_ARG, "the greedy heuristic needs a handle built from model parameters");
+    return launch_greedy(m, pi, (cudaStream_t)stream);
+}
+
 int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
                        int64_t* sweeps_out, void* stream) {
     g_err.clear();

@@ -477,6 +477,8 @@ int launch_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_i
 // V64 += e (FP64 add of the FP32 correction).
 int launch_axpy64(double* V64, const float* e, int n, cudaStream_t st);
 int launch_f32_to_f64(const float* in, double* out, int n, cudaStream_t st);
+// Greedy heuristic policy (Algorithm 2 read as a policy) of a model handle.
+int launch_greedy(Mdp* m, int32_t* pi, cudaStream_t st);
 
 // out[0..n] = exclusive prefix sums of cnt (int32 -> int64), out[n] = total.
 int exclusive_scan(Mdp* m, const int32_t* cnt, int64_t n, int64_t* out, cudaStream_t st);

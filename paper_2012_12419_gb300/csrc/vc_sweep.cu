@@ -317,4 +317,43 @@ int launch_f32_to_f64(const float* in, double* out, int n, cudaStream_t st) {
     return VC_OK;
 }
 
+// ------------------------------------------------------------- greedy heuristic policy
+// Algorithm 2 read as a policy on this MDP: with a task waiting, place it on the feasible
+// host with the largest service rate (ties to the lowest index), else defer.
+struct ServiceRates {
+    double mu[kMaxH];
+};
+
+template <int MH>
+__global__ void __launch_bounds__(kThreads) k_greedy(Model md, ServiceRates r, int32_t* __restrict__ pi) {
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < md.S; s += gridDim.x * kThreads) {
+        Digits d;
+        decode<MH>(md, s, d);
+        int best = md.H;
+        double best_mu = -1.0;
+        if (d.q >= 1) {
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                if (k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1) && r.mu[k] > best_mu) {
+                    best_mu = r.mu[k];
+                    best = k;
+                }
+            }
+        }
+        pi[s] = best;
+    }
+}
+
+int launch_greedy(Mdp* m, int32_t* pi, cudaStream_t st) {
+    ServiceRates r;
+    for (int k = 0; k < kMaxH; k++) r.mu[k] = m->rates.mu[k];
+    count_launches(1);
+    by_h(m, [&](auto mh) {
+        k_greedy<decltype(mh)::value><<<state_grid(m), kThreads, 0, st>>>(m->md, r, pi);
+        return 0;
+    });
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
 }  // namespace vc

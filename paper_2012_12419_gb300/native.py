@@ -41,7 +41,7 @@ EXPORTS = [
     "vc_last_error", "vc_build_mdp", "vc_build_mdp_csr", "vc_mdp_info", "vc_value_iterate", "vc_extract_policy",
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
-    "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice",
+    "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
 ]
 
 
@@ -154,6 +154,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_batch_autotune_report.argtypes = [vp, ctypes.c_char_p, i64]
         L.vc_batch_destroy.argtypes = [vp]
         L.vc_mdp_slice.argtypes = [vp, vp]
+        L.vc_greedy_policy.argtypes = [vp, vp, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -363,6 +364,12 @@ class MDP:
         _check(load().vc_value_grad(self._h, _ptr(V64), _ptr(pi), _ptr(rho), _ptr(dJ), _ptr(lam), float(tol),
                                     int(max_sweeps), ctypes.byref(gs), _stream(stream)))
         return dJ, lam, gs.as_dict()
+
+    def greedy_policy(self, stream=None):
+        """The greedy heuristic (Algorithm 2 read as a policy) as an int32 CUDA tensor."""
+        pi = torch.empty(self.S, dtype=torch.int32, device=_dev())
+        _check(load().vc_greedy_policy(self._h, _ptr(pi), _stream(stream)))
+        return pi
 
     def evaluate_policy(self, pi, V0=None, tol: float = 1e-10, max_sweeps: int = 1_000_000, stream=None):
         dev = _dev()
