@@ -35,25 +35,32 @@ int state_grid(const Mdp* m) {
 template <int MH, typename T>
 __device__ __forceinline__ T expect_next(const Model& md, const Coef<T>& c, const T* __restrict__ V, int x,
                                          const Digits& d) {
+    // every gather first (independent loads in flight together), then the sum in a fixed order
     const T vx = V[x];
+    T v1[MH], v0[MH];
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        const int o = d.occ[k];
+        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : T(0);
+        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : T(0);
+    }
+    const T va = (d.q < md.Q) ? V[x + 2] : T(0);
+    const T vf = V[d.ph ? x - 1 : x + 1];
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < MH; k++) {
         if (k < md.H) {
             const int o = d.occ[k];
             if (o > 0) {
-                const T v1 = V[x - md.stride[k]];
                 if (o == 1) {
-                    acc += (c.pc[k] + c.pd[k]) * (v1 - vx);  // completion and departure both empty the host
+                    acc += (c.pc[k] + c.pd[k]) * (v1[k] - vx);  // completion and departure both empty the host
                 } else {
-                    const T v0 = V[x - o * md.stride[k]];
-                    acc += c.pc[k] * T(o) * (v1 - vx) + c.pd[k] * (v0 - vx);
+                    acc += c.pc[k] * T(o) * (v1[k] - vx) + c.pd[k] * (v0[k] - vx);
                 }
             }
         }
     }
-    if (d.q < md.Q) acc += c.pa * (V[x + 2] - vx);
-    const T vf = V[d.ph ? x - 1 : x + 1];
+    if (d.q < md.Q) acc += c.pa * (va - vx);
     acc += (d.ph ? c.pf1 : c.pf0) * (vf - vx);
     return vx + acc;
 }
@@ -100,22 +107,25 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
         decode<MH>(md, s, d);
         T best = -INFINITY, second = -INFINITY;
         int arg = md.H;
-        if (d.q >= 1) {
+        // every gather first (infeasible actions read nothing and count as -inf), then the
+        // max in action order
+        T uk[MH];
 #pragma unroll
-            for (int k = 0; k < MH; k++) {
-                if (k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1)) {
-                    const T u = U[s + md.stride[k] - 2];
-                    if (u > best) {
-                        second = best;
-                        best = u;
-                        arg = k;
-                    } else if (u > second) {
-                        second = u;
-                    }
-                }
+        for (int k = 0; k < MH; k++)
+            uk[k] = (d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1))
+                        ? U[s + md.stride[k] - 2]
+                        : T(-INFINITY);
+        const T u = U[s];  // defer: the post-decision state is s itself; highest index, so ties keep lower ones
+#pragma unroll
+        for (int k = 0; k < MH; k++) {
+            if (uk[k] > best) {
+                second = best;
+                best = uk[k];
+                arg = k;
+            } else if (uk[k] > second) {
+                second = uk[k];
             }
         }
-        const T u = U[s];  // defer: the post-decision state is s itself; highest index, so ties keep lower ones
         if (u > best) {
             second = best;
             best = u;
