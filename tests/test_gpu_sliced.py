@@ -193,3 +193,36 @@ def test_sliced_errors():
     with pytest.raises(native.VcError, match="A <= 31"):
         m.slice()
     m.close()
+
+
+def test_sliced_user_bf16_matrix_certified_on_its_own_values():
+    """A user CSR in BF16 with its FP32 row scales (the oracle's renormalised BF16 form of the
+    mid instance): the sliced sweep equals the CSR sweep bitwise, and a full solve with no
+    model certifies against the stored values, matching the oracle run on that matrix."""
+    native = native_or_skip()
+    import torch
+
+    p = MID
+    rp, col, val, R = oracle.build_csr(p)
+    bits, eff, scale = oracle.bf16_renormalised(rp, val, len(R))
+    S, A = oracle.num_states(p), oracle.num_actions(p)
+    R32 = R.astype(np.float32)
+    dev = "cuda"
+    vb = torch.tensor(bits.view(np.int16), device=dev).view(torch.bfloat16)
+    args = (S, A, torch.tensor(rp, device=dev), torch.tensor(col, device=dev), vb, torch.tensor(R32, device=dev),
+            p["gamma"])
+    kw = dict(row_scale=torch.tensor(scale, device=dev))
+    mc = native.MDP.from_csr(*args, **kw)
+    ms = native.MDP.from_csr(*args, **kw).slice()
+    assert ms.info()["nnz_sliced"] == _host_sliced_entries(rp, R32, S, A)
+    V = torch.rand(S, device=dev) * 40
+    for x, y in zip(_sweep(mc, V), _sweep(ms, V)):
+        assert torch.equal(x, y)
+    Vb, _ = oracle.vi_csr(S, A, rp, col, eff, R32.astype(np.float64), p["gamma"], tol=1e-12)
+    pib, gapb = oracle.policy_csr(S, A, rp, col, eff, R32.astype(np.float64), p["gamma"], Vb)
+    _, V64, pi, st = ms.value_iterate(tol=1e-6, accurate=True)
+    assert st["certified"] == 1
+    assert np.max(np.abs(V64.cpu().numpy() - Vb)) <= 5e-7 + 1e-9
+    assert policy_mismatches(pi.cpu().numpy(), pib, gapb)[0] == 0
+    mc.close()
+    ms.close()
