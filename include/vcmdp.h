@@ -246,12 +246,6 @@ int vc_bellman64(vc_mdp* m, const double* V, double* V_out, int32_t* pi, double*
                  void* stream);
 
 /*
- * FP64 policy evaluation V_pi = R_pi + gamma P_pi V_pi by Jacobi sweeps over the chosen
- * rows only.  pi: [S] int32 (must be feasible everywhere, else VC_ERR_ARG); V_pi: [S]
- * double, in: initial guess, out: result once the sweep change is below tol.
- * *sweeps_out (host, nullable) receives the sweep count.  Synchronises `stream`.
- */
-/*
  * The paper's greedy heuristic (Algorithm 2, "efficient VM first") read as a policy on this
  * MDP: pi[s] = the feasible host with the largest service rate mu_a when a task waits
  * (ties to the lowest host index), else defer (a = H).  pi: [S] int32 device, written on
@@ -260,6 +254,17 @@ int vc_bellman64(vc_mdp* m, const double* V, double* V_out, int32_t* pi, double*
  * handle built from a user CSR (no model to read rates from).
  */
 int vc_greedy_policy(vc_mdp* m, int32_t* pi, void* stream);
+
+/*
+ * Policy evaluation V_pi = R_pi + gamma P_pi V_pi (Eq. 18 with the action fixed) over the
+ * chosen rows only, by mixed-precision iterative refinement: the policy residual
+ * r = T_pi V - V and its maximum in FP64, the correction (I - gamma P_pi) e = r by FP32
+ * Jacobi sweeps, V += e in FP64, until max|r| < tol (the point where an FP64 Jacobi sweep
+ * would change V by less than tol).  pi: [S] int32 (feasible everywhere, else
+ * VC_ERR_ARG); V_pi: [S] double, in: initial guess, out: the result.  *sweeps_out (host,
+ * nullable) receives the FP32 correction sweeps.  VC_ERR_NOT_CONVERGED once max_sweeps
+ * correction sweeps are spent.  Synchronises `stream`.
+ */
 
 int vc_evaluate_policy(vc_mdp* m, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
                        int64_t* sweeps_out, void* stream);

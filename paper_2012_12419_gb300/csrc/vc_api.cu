@@ -131,36 +131,6 @@ static int loop32(Mdp* m, float* buf0, float* buf1, double tol, long long max_sw
 }
 
 // FP64 policy evaluation V <- R_pi + gamma P_pi V until the sweep change is below tol.
-static int loop_eval64(Mdp* m, const int32_t* pi, double* buf0, double* buf1, double tol, long long max_sweeps,
-                       cudaStream_t st, int* final_idx, long long* sweeps, int* error) {
-    Ctl& h = *m->ctl_host;
-    reset_ctl(h, tol, max_sweeps);
-    VC_CUDA(cudaMemcpyAsync(m->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
-    double* buf[2] = {buf0, buf1};
-    long long launched = 0, chunk = 16;
-    int rc;
-    for (;;) {
-        for (long long i = 0; i < chunk; i++) {
-            const int in = (int)(launched & 1);
-            SweepCtl sc{m->ctl, kModeLoop64, 1 - in, nullptr};
-            if ((rc = launch_eval64(m, pi, buf[in], buf[1 - in], sc, st))) return rc;
-            launched++;
-        }
-        if ((rc = read_ctl(m, st))) return rc;
-        if (h.done || h.error) break;
-        const int slot = (int)((h.sweeps - 1) % kRing);
-        double r;
-        memcpy(&r, &h.res64[slot], 8);
-        chunk = predict_sweeps(r, tol, m->gamma);
-        chunk = std::min<long long>(std::max<long long>(chunk, 4), 1024);
-        chunk = std::min<long long>(chunk, max_sweeps - h.sweeps + 1);
-    }
-    *final_idx = h.final_buf;
-    *sweeps = h.sweeps;
-    *error = h.error;
-    return VC_OK;
-}
-
 // One FP64 Bellman backup V_in -> V_out with argmax pi_out; returns max|V_out - V_in| and
 // the number of states whose argmax differs from pi_ref (if given).
 static int cert64(Mdp* m, const double* V_in, double* V_out, int32_t* pi_out, double* qgap,
@@ -530,16 +500,39 @@ int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, 
     if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
     Mdp* m = (Mdp*)mh;
     cudaStream_t st = (cudaStream_t)stream;
-    int fin = 0, err = 0;
-    long long sw = 0;
-    int rc = loop_eval64(m, pi, V_pi, m->V64b, tol, max_sweeps, st, &fin, &sw, &err);
-    if (rc) return rc;
-    if (fin == 1) VC_CUDA(cudaMemcpyAsync(V_pi, m->V64b, 8 * (size_t)m->S, cudaMemcpyDeviceToDevice, st));
+    // Mixed-precision iterative refinement of V_pi = R_pi + gamma P_pi V_pi: the policy
+    // residual r = T_pi V - V and its maximum in FP64, the correction (I - gamma P_pi) e = r
+    // by FP32 Jacobi sweeps to tol/2, V += e in FP64; stop when max|r| < tol (the FP64
+    // Jacobi criterion: the next sweep would change V by less than tol).
+    long long total = 0;
+    int rc;
+    for (int round = 0; round < 60; round++) {
+        VC_CUDA(cudaMemsetAsync(&m->ctl->cert64, 0, sizeof(unsigned long long), st));
+        VC_CUDA(cudaMemsetAsync(&m->ctl->error, 0, sizeof(int), st));
+        SweepCtl sc{m->ctl, kModeCert64, 0, nullptr};
+        if ((rc = launch_resid64(m, pi, V_pi, m->Rres, sc, st))) return rc;
+        if ((rc = read_ctl(m, st))) return rc;
+        if (m->ctl_host->error & kErrInfeasiblePolicy) return fail(VC_ERR_ARG, "the policy picks an infeasible action");
+        double r;
+        memcpy(&r, &m->ctl_host->cert64, 8);
+        if (r < tol) {
+            if (sweeps_out) *sweeps_out = total;
+            return VC_OK;
+        }
+        if (total >= max_sweeps) break;
+        VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * (size_t)m->S, st));
+        int efin = 0;
+        rc = loop32(m, m->E0, m->E1, 0.5 * tol, max_sweeps - total, st, &efin,
+                    [&](const float* in, float* o, SweepCtl s2) {
+                        return launch_correct32(m, pi, m->Rres, in, o, s2, st);
+                    });
+        if (rc) return rc;
+        total += m->ctl_host->sweeps;
+        if ((rc = launch_axpy64(V_pi, efin == 1 ? m->E1 : m->E0, m->S, st))) return rc;
+    }
     VC_CUDA(cudaStreamSynchronize(st));
-    if (sweeps_out) *sweeps_out = sw;
-    if (err & kErrInfeasiblePolicy) return fail(VC_ERR_ARG, "the policy picks an infeasible action");
-    if (m->ctl_host->done != 1) return fail(VC_ERR_NOT_CONVERGED, "policy evaluation hit max_sweeps");
-    return VC_OK;
+    if (sweeps_out) *sweeps_out = total;
+    return fail(VC_ERR_NOT_CONVERGED, "policy evaluation hit max_sweeps");
 }
 
 int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,

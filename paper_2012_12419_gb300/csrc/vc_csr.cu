@@ -414,36 +414,11 @@ __global__ void __launch_bounds__(kThreads) k_csr_bellman64(CsrArgs a, double ga
 }
 
 template <typename VT>
-__global__ void __launch_bounds__(kThreads) k_csr_eval64(CsrArgs a, double gamma, const int32_t* __restrict__ pi,
-                                                         const double* __restrict__ V_in, double* __restrict__ V_out,
-                                                         SweepCtl sc) {
-    if (loop_done(sc)) return;
-    const long long sweep = loop_sweep(sc);
-    const VT* val = reinterpret_cast<const VT*>(a.val);
-    double res = 0.0;
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
-        const int act = pi[s];
-        const int64_t r = (int64_t)s * a.A + act;
-        const float rr = (act >= 0 && act < a.A) ? a.R[r] : -INFINITY;
-        if (rr == -INFINITY) {
-            atomicOr(&sc.ctl->error, kErrInfeasiblePolicy);
-            V_out[s] = V_in[s];
-            continue;
-        }
-        const double v = (double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V_in);
-        V_out[s] = v;
-        res = fmax(res, fabs(v - V_in[s]));
-    }
-    if (sc.mode == kModeNone) return;
-    res = block_max<double, kThreads>(res);
-    finish_block<double>(sc, res, 0.0, sweep);
-}
-
-template <typename VT>
 __global__ void __launch_bounds__(kThreads) k_csr_resid64(CsrArgs a, double gamma, const int32_t* __restrict__ pi,
                                                           const double* __restrict__ V, float* __restrict__ r_out,
                                                           SweepCtl sc) {
     const VT* val = reinterpret_cast<const VT*>(a.val);
+    double mx = 0.0;
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
         const int act = pi[s];
         const int64_t r = (int64_t)s * a.A + act;
@@ -453,8 +428,14 @@ __global__ void __launch_bounds__(kThreads) k_csr_resid64(CsrArgs a, double gamm
             r_out[s] = 0.0f;
             continue;
         }
-        r_out[s] = (float)((double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V) - V[s]);
+        const double rd = (double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V) - V[s];
+        r_out[s] = (float)rd;
+        mx = fmax(mx, fabs(rd));
     }
+    // kModeCert64: max |T_pi V - V| in FP64 into the control block
+    if (sc.mode != kModeCert64) return;
+    mx = block_max<double, kThreads>(mx);
+    finish_block<double>(sc, mx, 0.0, 0);
 }
 
 template <typename VT>
@@ -708,17 +689,6 @@ int csr_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double
         k_csr_bellman64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc);
     else
         k_csr_bellman64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc);
-    VC_CUDA(cudaGetLastError());
-    return VC_OK;
-}
-
-int csr_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st) {
-    const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
-    count_launches(1);
-    if ((m->fmt & 0xF) == VC_CSR_BF16)
-        k_csr_eval64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V_in, V_out, sc);
-    else
-        k_csr_eval64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V_in, V_out, sc);
     VC_CUDA(cudaGetLastError());
     return VC_OK;
 }

@@ -467,8 +467,6 @@ int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* 
 // One FP64 full Bellman backup (exact model when available, else the stored CSR in FP64).
 int launch_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double* qgap, SweepCtl sc,
                      cudaStream_t st);
-// One FP64 policy-evaluation sweep over the chosen rows.
-int launch_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st);
 // r = (R_pi + gamma P_pi V64) - V64 in FP64, stored as float (policy residual).
 int launch_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl sc, cudaStream_t st);
 // One FP32 correction sweep e_out = r + gamma P_pi e_in.
@@ -498,7 +496,6 @@ int launch_grad_contract(Mdp* m, const int32_t* pi, const double* V, const doubl
 int csr_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st);
 int csr_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double* qgap, SweepCtl sc,
                   cudaStream_t st);
-int csr_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st);
 int csr_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl sc, cudaStream_t st);
 int csr_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_in, float* e_out, SweepCtl sc,
                   cudaStream_t st);

@@ -146,32 +146,6 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
     finish_block<T>(sc, res, vabs, sweep);
 }
 
-// --------------------------------------------------- implicit: policy evaluation sweep
-// V_out(s) = R(x_pi(s)) + gamma E[V_in(next) | x_pi(s)].
-template <int MH, typename T>
-__global__ void __launch_bounds__(kThreads) k_eval(Model md, Coef<T> c, const int32_t* __restrict__ pi,
-                                                   const T* __restrict__ V_in, T* __restrict__ V_out, SweepCtl sc) {
-    if (loop_done(sc)) return;
-    const long long sweep = loop_sweep(sc);
-    T res = T(0);
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < md.S; s += gridDim.x * kThreads) {
-        Digits d;
-        decode<MH>(md, s, d);
-        int x = s;
-        if (!apply_action<MH>(md, s, pi[s], d, x)) {
-            atomicOr(&sc.ctl->error, kErrInfeasiblePolicy);
-            V_out[s] = V_in[s];
-            continue;
-        }
-        const T v = post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V_in, x, d);
-        V_out[s] = v;
-        res = fmax(res, fabs(v - V_in[s]));
-    }
-    if (sc.mode == kModeNone) return;
-    res = block_max<T, kThreads>(res);
-    finish_block<T>(sc, res, T(0), sweep);
-}
-
 // ------------------------------------------------ implicit: mixed-precision refinement
 // Policy residual in FP64: r(s) = R(x_pi) + gamma E[V64(next) | x_pi] - V64(s), stored as
 // float (it is small once V64 is near V_pi, so FP32 keeps ~1e-7 of it).
@@ -179,6 +153,7 @@ template <int MH>
 __global__ void __launch_bounds__(kThreads) k_resid64(Model md, Coef<double> c, const int32_t* __restrict__ pi,
                                                       const double* __restrict__ V, float* __restrict__ r,
                                                       SweepCtl sc) {
+    double mx = 0.0;
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < md.S; s += gridDim.x * kThreads) {
         Digits d;
         decode<MH>(md, s, d);
@@ -188,8 +163,14 @@ __global__ void __launch_bounds__(kThreads) k_resid64(Model md, Coef<double> c, 
             r[s] = 0.0f;
             continue;
         }
-        r[s] = (float)(post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V, x, d) - V[s]);
+        const double rd = post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V, x, d) - V[s];
+        r[s] = (float)rd;
+        mx = fmax(mx, fabs(rd));
     }
+    // kModeCert64: max |T_pi V - V| in FP64 into the control block
+    if (sc.mode != kModeCert64) return;
+    mx = block_max<double, kThreads>(mx);
+    finish_block<double>(sc, mx, 0.0, 0);
 }
 
 // Correction sweep in FP32: e_out(s) = r(s) + gamma E[e_in(next) | x_pi(s)].  Its fixed
@@ -268,17 +249,6 @@ int launch_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, dou
         constexpr int MH = decltype(mh)::value;
         k_post<MH, double><<<g, kThreads, 0, st>>>(m->md, m->c64, V_in, m->U64, none);
         k_max<MH, double><<<g, kThreads, 0, st>>>(m->md, m->U64, V_in, V_out, pi, qgap, sc);
-        return 0;
-    });
-    VC_CUDA(cudaGetLastError());
-    return VC_OK;
-}
-
-int launch_eval64(Mdp* m, const int32_t* pi, const double* V_in, double* V_out, SweepCtl sc, cudaStream_t st) {
-    if (!m->has_model) return csr_eval64(m, pi, V_in, V_out, sc, st);
-    count_launches(1);
-    by_h(m, [&](auto mh) {
-        k_eval<decltype(mh)::value, double><<<state_grid(m), kThreads, 0, st>>>(m->md, m->c64, pi, V_in, V_out, sc);
         return 0;
     });
     VC_CUDA(cudaGetLastError());
