@@ -27,7 +27,7 @@
  *   - Array arguments are DEVICE pointers unless the comment says host.  They are
  *     borrowed for the duration of the call; the library never frees them.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is enqueued
- *     on it; calls that return statistics or a convergence verdict synchronise it.
+ *     on it; calls that return statistics or a convergence outcome synchronise it.
  *   - The library allocates device memory only inside handles it owns (vc_mdp,
  *     vc_batch); vc_destroy / vc_batch_destroy release it.
  *   - States are indexed with int32 (S < 2^31); CSR offsets are int64.
@@ -185,6 +185,18 @@ int vc_mdp_export_csr(const vc_mdp* m, int64_t* row_ptr, int32_t* col, void* val
  * VC_ERR_ARG for a VC_IMPLICIT handle or A > 31; VC_ERR_OOM.  Idempotent.
  */
 int vc_mdp_slice(vc_mdp* m, void* stream);
+
+/*
+ * Fault-injection hook for the bounded device waits (no paper counterpart).  The pipelined
+ * sweeps (CSR and sliced) wait on shared-memory barriers for their staged tiles with an
+ * iteration limit; polls >= 0 caps every such wait of this handle's later solves at that
+ * many polls (0: give up at once), polls < 0 restores the default (2^22).  A wait that
+ * gives up flags the sweep, the kernel drains its own copies in flight (with the default
+ * limit) and returns, and vc_value_iterate returns VC_ERR_TIMEOUT; the handle and the
+ * CUDA context stay usable.  Synchronous; applies to later launches on the handle.
+ * VC_ERR_ARG for NULL.
+ */
+int vc_set_wait_limit(vc_mdp* m, int64_t polls);
 
 /*
  * Value iteration (Algorithm 3).  V: [S] float, in: V^0 (zeros = the paper's step 1,

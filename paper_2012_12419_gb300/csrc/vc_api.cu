@@ -69,11 +69,12 @@ static int device_sms() {
 }
 
 // ------------------------------------------------------------------ loop drivers
-static void reset_ctl(Ctl& h, double tol, long long max_sweeps) {
+static void reset_ctl(Ctl& h, double tol, long long max_sweeps, long long spin_polls) {
     memset(&h, 0, sizeof(Ctl));
     h.tol = tol;
     h.max_sweeps = max_sweeps;
     h.best_res = INFINITY;
+    h.spin_limit = spin_polls < 0 ? 0 : spin_polls + 1;
 }
 
 static int read_ctl(Mdp* m, cudaStream_t st) {
@@ -99,7 +100,7 @@ template <typename Launch>
 static int loop32(Mdp* m, float* buf0, float* buf1, double tol, long long max_sweeps, cudaStream_t st,
                   int* final_idx, Launch&& launch) {
     Ctl& h = *m->ctl_host;
-    reset_ctl(h, tol, max_sweeps);
+    reset_ctl(h, tol, max_sweeps, m->spin_polls);
     VC_CUDA(cudaMemcpyAsync(m->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     float* buf[2] = {buf0, buf1};
     long long launched = 0, chunk = 16;
@@ -265,6 +266,17 @@ int vc_mdp_info(const vc_mdp* mh, vc_info* out) {
     else
         out->sweep_bytes = m->nnz_stored * ((base == VC_CSR_BF16 ? 2 : 4) + 4) + rows * (8 + 4) +
                            (base == VC_CSR_BF16 ? rows * 4 : 0) + 8 * (int64_t)m->S;
+    return VC_OK;
+}
+
+int vc_set_wait_limit(vc_mdp* mh, int64_t polls) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    Mdp* m = (Mdp*)mh;
+    m->spin_polls = polls < 0 ? -1 : polls;
+    // also the current control block, for sweeps launched outside a solve
+    const long long v = polls < 0 ? 0 : polls + 1;
+    VC_CUDA(cudaMemcpy(&m->ctl->spin_limit, &v, sizeof(v), cudaMemcpyHostToDevice));
     return VC_OK;
 }
 

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
     extern __shared__ __align__(128) unsigned char smem[];
     if (loop_done(sc)) return;
     const long long sweep = loop_sweep(sc);
+    const long long lim = wait_limit(sc);
     constexpr int SPW = 32 / APAD;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + a.stages;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
                 const int64_t e0 = ne0, e1 = ne1;
                 if (t + gridDim.x < a.ntiles) bounds(t + gridDim.x, ne0, ne1);
                 const int stg = i % a.stages;
-                if (i >= a.stages && !mbar_wait(&empty[stg], (uint32_t)(((i / a.stages) - 1) & 1))) {
+                if (i >= a.stages && !mbar_wait(&empty[stg], (uint32_t)(((i / a.stages) - 1) & 1), lim)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
         int i = 0;
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
             const int stg = i % a.stages;
-            if (!mbar_wait(&full[stg], (uint32_t)((i / a.stages) & 1))) {
+            if (!mbar_wait(&full[stg], (uint32_t)((i / a.stages) & 1), lim)) {
                 atomicExch(&s_fail, 1);
                 break;
             }

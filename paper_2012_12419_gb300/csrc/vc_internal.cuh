@@ -236,6 +236,7 @@ struct Ctl {
     unsigned long long cert64;          // FP64 residual bits of a standalone Bellman backup
     int error;                          // bit flags raised by kernels (infeasible policy, bad input)
     int pad2_;
+    long long spin_limit;               // polls + 1 of each bounded pipeline wait (0 = the default)
 };
 
 // Error flags raised on the device.
@@ -438,6 +439,7 @@ struct Mdp {
     Ctl* ctl_host = nullptr;    // pinned mirror
     int64_t device_bytes = 0;
     int num_sms = 0;
+    long long spin_polls = -1;  // bounded-wait cap for the pipelined sweeps (-1 = the default)
 };
 
 // Process-wide count of kernels this library has enqueued.

@@ -5,6 +5,8 @@
 
 #include <stdint.h>
 
+#include "vc_internal.cuh"
+
 namespace vc {
 
 constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier polling (~0.5-2 s worst case)
@@ -39,8 +41,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Polls the barrier phase with a hard iteration limit; false if it never completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
+    for (long long it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it >= 32) __nanosleep(64);
     }
@@ -60,6 +62,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             "r"(smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
+}
+
+// Poll limit of the pipeline waits of one sweep: the handle's cap when one was set (a
+// host-side fault-injection hook), else kSpinLimit.  Drains of in-flight copies always
+// use kSpinLimit.
+__device__ __forceinline__ long long wait_limit(const SweepCtl& sc) {
+    const long long v = *((volatile long long*)&sc.ctl->spin_limit);
+    return v > 0 ? v - 1 : kSpinLimit;
 }
 
 // Barrier `id` (1..15) over the first `threads` threads that reach it (a multiple of 32).

@@ -450,6 +450,7 @@ __global__ void __launch_bounds__((kMaxRW + 1) * 32, 1) k_sell_ring(SellArgs a, 
     extern __shared__ __align__(128) unsigned char smem[];
     if (loop_done(sc)) return;
     const long long sweep = loop_sweep(sc);
+    const long long lim = wait_limit(sc);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kSlots;
     int* done_cnt = reinterpret_cast<int*>(empty + kSlots);
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__((kMaxRW + 1) * 32, 1) k_sell_ring(SellArgs a, 
                     // reuse bytes (and the slot) only after the tiles holding them are released
                     while (oldest < i && (head + bytes - rel > (unsigned long long)t.ring || i - oldest >= kSlots)) {
                         const int os = oldest % kSlots;
-                        if (!mbar_wait(&empty[os], (uint32_t)((oldest / kSlots) & 1))) {
+                        if (!mbar_wait(&empty[os], (uint32_t)((oldest / kSlots) & 1), lim)) {
                             failed = 1;
                             break;
                         }
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__((kMaxRW + 1) * 32, 1) k_sell_ring(SellArgs a, 
             const int nb = ns * A;
             if (b >= nb) continue;  // the last tile may hold fewer slices
             const int s = i % kSlots;
-            if (!mbar_wait(&full[s], (uint32_t)((i / kSlots) & 1))) {
+            if (!mbar_wait(&full[s], (uint32_t)((i / kSlots) & 1), lim)) {
                 atomicExch(&s_fail, 1);
                 break;
             }

@@ -42,6 +42,7 @@ EXPORTS = [
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
     "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
+    "vc_set_wait_limit",
 ]
 
 
@@ -155,6 +156,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_batch_destroy.argtypes = [vp]
         L.vc_mdp_slice.argtypes = [vp, vp]
         L.vc_greedy_policy.argtypes = [vp, vp, vp]
+        L.vc_set_wait_limit.argtypes = [vp, i64]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -241,6 +243,11 @@ class MDP:
         _check(L.vc_build_mdp_csr(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), vdt, _ptr(row_scale),
                                   _ptr(R), float(gamma), _stream(stream), ctypes.byref(h)))
         return cls(h)
+
+    def set_wait_limit(self, polls: int = -1) -> None:
+        """Cap the bounded shared-memory waits of the pipelined sweeps (fault injection;
+        0 = give up at once, negative = the default)."""
+        _check(load().vc_set_wait_limit(self._h, int(polls)))
 
     def slice(self, stream=None) -> "MDP":
         """Add the sliced copy of the stored matrix and sweep it from now on."""
