@@ -182,6 +182,7 @@ static int use_sliced(Mdp* m, cudaStream_t st) {
 }
 
 int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
+    NvtxRange nv("vc_build_mdp");
     g_err.clear();
     if (!out) return fail(VC_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -281,6 +282,7 @@ int vc_set_wait_limit(vc_mdp* mh, int64_t polls) {
 }
 
 int vc_mdp_slice(vc_mdp* mh, void* stream) {
+    NvtxRange nv("vc_mdp_slice");
     g_err.clear();
     if (!mh) return fail(VC_ERR_ARG, "NULL handle");
     Mdp* m = (Mdp*)mh;
@@ -312,6 +314,7 @@ int vc_mdp_export_csr(const vc_mdp* mh, int64_t* row_ptr, int32_t* col, void* va
 
 int vc_value_grad(vc_mdp* mh, const double* V, const int32_t* pi, const double* rho, double* dJ_dtheta,
                   double* lambda_out, double tol, int64_t max_sweeps, vc_grad_stats* stats, void* stream) {
+    NvtxRange nv("vc_value_grad");
     g_err.clear();
     if (!mh || !V || !pi || !rho || !dJ_dtheta) return fail(VC_ERR_ARG, "NULL argument");
     if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
@@ -437,6 +440,7 @@ int vc_value_grad(vc_mdp* mh, const double* V, const int32_t* pi, const double* 
 }
 
 int vc_autotune(vc_mdp* mh, int reps, double* best_us, void* stream) {
+    NvtxRange nv("vc_autotune");
     g_err.clear();
     if (!mh) return fail(VC_ERR_ARG, "NULL handle");
     Mdp* m = (Mdp*)mh;
@@ -507,6 +511,7 @@ int vc_greedy_policy(vc_mdp* mh, int32_t* pi, void* stream) {
 
 int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,
                        int64_t* sweeps_out, void* stream) {
+    NvtxRange nv("vc_evaluate_policy");
     g_err.clear();
     if (!mh || !pi || !V_pi) return fail(VC_ERR_ARG, "NULL argument");
     if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
@@ -549,6 +554,7 @@ int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, 
 
 int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
                      int flags, vc_stats* stats, void* stream) {
+    NvtxRange nv("vc_value_iterate");
     g_err.clear();
     if (!mh || !V) return fail(VC_ERR_ARG, "NULL argument");
     if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");
@@ -563,9 +569,12 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
     const size_t S = (size_t)m->S;
 
     VC_CUDA(cudaEventRecord(ev[0], st));
-    rc = loop32(m, V, m->Vb, tol, max_sweeps, st, &fin, [&](const float* in, float* o, SweepCtl sc) {
-        return launch_sweep32(m, in, o, nullptr, nullptr, sc, st);
-    });
+    {
+        NvtxRange nv32("fp32 sweeps");
+        rc = loop32(m, V, m->Vb, tol, max_sweeps, st, &fin, [&](const float* in, float* o, SweepCtl sc) {
+            return launch_sweep32(m, in, o, nullptr, nullptr, sc, st);
+        });
+    }
     if (rc) goto out;
     if (fin == 1) VC_CUDA(cudaMemcpyAsync(V, m->Vb, 4 * S, cudaMemcpyDeviceToDevice, st));
     VC_CUDA(cudaEventRecord(ev[1], st));

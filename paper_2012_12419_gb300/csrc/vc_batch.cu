@@ -700,6 +700,7 @@ int vc_batch_offsets(const vc_batch* bh, int64_t* offsets) {
 
 int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
                            int flags, vc_batch_stats* per_inst, void* stream) {
+    NvtxRange nv("vc_value_iterate_batch");
     set_error("");
     if (!bh || !V) return fail(VC_ERR_ARG, "NULL argument");
     if (!(tol > 0.0) || max_sweeps < 1) return fail(VC_ERR_ARG, "tol must be > 0 and max_sweeps >= 1");

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/vcmdp.h"
 
 namespace vc {
@@ -444,6 +446,15 @@ struct Mdp {
 
 // Process-wide count of kernels this library has enqueued.
 void count_launches(int n);
+
+// Scoped NVTX range: names the library's phases on a profiler's timeline (a no-op when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Kernels / launchers implemented in the .cu files.
 int alloc_dev(Mdp* m, void** p, size_t bytes);
