@@ -761,7 +761,7 @@ int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
         char line[160];
         char kname[40];
         if (P.sliced && P.tma)
-            snprintf(kname, sizeof(kname), "sliced-pipelined-w%d", P.warps);
+            snprintf(kname, sizeof(kname), "sliced-pipelined-w%d-r%d", P.warps, P.minb);
         else
             snprintf(kname, sizeof(kname), "%s", P.sliced ? "sliced-direct" : (P.tma ? "pipelined" : "direct"));
         snprintf(line, sizeof(line), "%s %d %d %d %d %.2f\n", kname, P.sliced ? 32 * (P.tma ? P.ts : 1) : P.ts,

@@ -399,6 +399,7 @@ struct CsrPlan {
     int smem = 0;        // dynamic shared memory per CTA
     int64_t ntiles = 0;
     int warps = 0;       // consumer warps per CTA (sliced ring sweep)
+    int minb = 1;        // register budget of the sliced ring kernel (1: 80 registers, 2: 60)
 };
 
 struct Mdp {

@@ -338,14 +338,13 @@ __device__ __forceinline__ float ld_val<uint16_t>(const uint16_t* p) {
 // multiply-adds in column order onto acc.
 template <typename VT, int W>
 __device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, const float* __restrict__ V, float acc) {
-    float wv[W], gv[W];
+    float gv[W];
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-        wv[u] = ld_val<VT>(vp + u * kSellC);
-        gv[u] = __ldg(V + cp[u * kSellC]);
-    }
+    for (int u = 0; u < W; ++u) gv[u] = __ldg(V + cp[u * kSellC]);
+    // the values are read from shared memory only once the gathers are in flight, so
+    // they hold no registers meanwhile
 #pragma unroll
-    for (int u = 0; u < W; ++u) acc = fmaf(wv[u], gv[u], acc);
+    for (int u = 0; u < W; ++u) acc = fmaf(ld_val<VT>(vp + u * kSellC), gv[u], acc);
     return acc;
 }
 
@@ -445,8 +444,11 @@ struct SellRingArgs {
     int roff;         // byte offset of the ring
 };
 
-template <typename VT>
-__global__ void __launch_bounds__((kMaxRW + 1) * 32, 1) k_sell_ring(SellArgs a, SellRingArgs t, SweepCtl sc) {
+// MB = 1: up to 800 threads (24 consumer warps), 80 registers; MB = 2: two CTAs of up to
+// 17 warps per SM, 60 registers.
+template <typename VT, int MB>
+__global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_sell_ring(SellArgs a, SellRingArgs t,
+                                                                                        SweepCtl sc) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (loop_done(sc)) return;
     const long long sweep = loop_sweep(sc);
@@ -619,13 +621,9 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
     VC_CUDA(cudaGetDevice(&dev));
     VC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     VC_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const void* fn = bf16 ? (const void*)k_sell_ring<uint16_t> : (const void*)k_sell_ring<float>;
-    cudaFuncAttributes fa;
-    VC_CUDA(cudaFuncGetAttributes(&fa, fn));
-    const int dyn_max = smem_blk - (int)fa.sharedSizeBytes;
-    VC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
     const std::vector<int64_t>& rows = m->sell_slice_rows;
-    const int shapes[][2] = {{2, 12}, {1, 24}, {2, 8}, {3, 8}};
+    // (CTAs per SM, consumer warps, register budget), preferred first
+    const int shapes[][3] = {{2, 12, 1}, {2, 16, 2}, {3, 10, 2}, {1, 24, 1}, {2, 8, 1}, {3, 8, 1}};
     for (int TS : {1, 2, 4}) {
         long long max_tile = 0;  // largest tile of TS slice records
         for (int64_t g0 = 0; g0 < (int64_t)rows.size(); g0 += TS) {
@@ -635,7 +633,13 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             max_tile = std::max<long long>(max_tile, b);
         }
         for (auto& sh : shapes) {
-            const int ctas = sh[0], nrw = sh[1];
+            const int ctas = sh[0], nrw = sh[1], mb = sh[2];
+            const void* fn = bf16 ? (mb == 2 ? (const void*)k_sell_ring<uint16_t, 2> : (const void*)k_sell_ring<uint16_t, 1>)
+                                  : (mb == 2 ? (const void*)k_sell_ring<float, 2> : (const void*)k_sell_ring<float, 1>);
+            cudaFuncAttributes fa;
+            VC_CUDA(cudaFuncGetAttributes(&fa, fn));
+            const int dyn_max = smem_blk - (int)fa.sharedSizeBytes;
+            VC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
             const int threads = (nrw + 1) * 32;
             if (threads > fa.maxThreadsPerBlock || (long long)threads * fa.numRegs * ctas > 65536) continue;
             if (nrw > (kSlots - 2) * TS * A) continue;  // claimed blocks stay within kSlots tiles
@@ -655,6 +659,7 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             P.cap = ring;
             P.stages = kSlots;
             P.warps = nrw;
+            P.minb = mb;
             P.ctas_per_sm = per_sm < ctas ? per_sm : ctas;
             P.smem = need;
             P.ntiles = (m->sell_slices + TS - 1) / TS;
@@ -691,10 +696,14 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
         const unsigned grid = (unsigned)(t.ntiles < cap ? t.ntiles : cap);
         const unsigned threads = (unsigned)(m->plan.warps + 1) * 32;
         count_launches(1);
-        if (bf16)
-            k_sell_ring<uint16_t><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+        if (bf16 && m->plan.minb == 2)
+            k_sell_ring<uint16_t, 2><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+        else if (bf16)
+            k_sell_ring<uint16_t, 1><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+        else if (m->plan.minb == 2)
+            k_sell_ring<float, 2><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
         else
-            k_sell_ring<float><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+            k_sell_ring<float, 1><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
         VC_CUDA(cudaGetLastError());
         return VC_OK;
     }
