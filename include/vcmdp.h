@@ -96,8 +96,8 @@ typedef struct vc_info {
     int64_t device_bytes;   /* device memory owned by the handle */
     int64_t sweep_bytes;    /* algorithmic HBM bytes of one FP32 sweep */
     int32_t has_model;      /* 1 if built from vc_params (exact FP64 P available) */
-    int32_t csr_pipelined;  /* 1 if CSR sweeps stage tiles through shared memory */
-    int32_t csr_tile_states;/* states per staged tile */
+    int32_t csr_pipelined;  /* 1 if the FP32 sweep stages tiles through shared memory */
+    int32_t csr_tile_states;/* states per staged tile (sliced: 32 x slices per tile) */
     int32_t csr_stages;     /* tiles in flight per CTA */
     int32_t csr_ctas_per_sm;/* resident CTAs per SM of the CSR sweep */
     int32_t csr_smem_bytes; /* dynamic shared memory per CTA */

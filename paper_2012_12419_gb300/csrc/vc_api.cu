@@ -252,7 +252,7 @@ int vc_mdp_info(const vc_mdp* mh, vc_info* out) {
     out->device_bytes = m->device_bytes;
     out->has_model = m->has_model ? 1 : 0;
     out->csr_pipelined = m->plan.tma ? 1 : 0;
-    out->csr_tile_states = m->plan.ts;
+    out->csr_tile_states = m->plan.sliced ? 32 * (m->plan.tma ? m->plan.ts : 1) : m->plan.ts;
     out->csr_stages = m->plan.stages;
     out->csr_ctas_per_sm = m->plan.ctas_per_sm;
     out->csr_smem_bytes = m->plan.smem;
