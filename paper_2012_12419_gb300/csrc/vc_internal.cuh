@@ -224,7 +224,6 @@ __device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s
 struct Ctl {
     unsigned int res32[kRing];          // FP32 residual bits per sweep (atomicMax on >= 0 floats)
     unsigned int vmax32[kRing];         // max |V'| bits per sweep
-    unsigned long long res64[kRing];    // FP64 residual bits per sweep
     unsigned int ticket;                // arrival counter of the last-block pattern
     int done;                           // 0 running, 1 converged, 2 max sweeps, 3 stalled at the FP32 floor
     long long sweeps;                   // sweeps completed
@@ -254,7 +253,6 @@ constexpr int kErrTimeout = 64;
 enum SweepMode : int {
     kModeNone = 0,     // plain backup (policy extraction)
     kModeLoop32 = 1,   // FP32 loop: skip when done, residual ring, tolerance / stall test
-    kModeLoop64 = 2,   // FP64 policy-evaluation loop: skip when done, FP64 residual ring
     kModeCert64 = 3,   // FP64 standalone backup: residual into cert64, policy changes vs pi_ref
 };
 
@@ -317,21 +315,21 @@ __device__ __forceinline__ unsigned int fbits(float x) { return __float_as_uint(
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 __device__ __forceinline__ bool loop_done(const SweepCtl& sc) {
-    if (sc.mode != kModeLoop32 && sc.mode != kModeLoop64) return false;
+    if (sc.mode != kModeLoop32) return false;
     return *((volatile int*)&sc.ctl->done) != 0;
 }
 
 __device__ __forceinline__ long long loop_sweep(const SweepCtl& sc) {
-    if (sc.mode != kModeLoop32 && sc.mode != kModeLoop64) return 0;
+    if (sc.mode != kModeLoop32) return 0;
     return *((volatile long long*)&sc.ctl->sweeps);
 }
 
 // Residual bookkeeping, called by thread 0 of every block once its block maximum is known.
-// Loop modes: one atomicMax per block into the sweep's ring slot, then the last block to
+// Loop mode: one atomicMax per block into the sweep's ring slot, then the last block to
 // arrive (ticket counter) closes the sweep: advances the sweep count, records the output
-// buffer, clears the next slot and decides termination (tolerance max(tol, 4 ulp(max|V|))
-// for FP32, tol for FP64, FP32 stall, or max_sweeps).  Order independent, so every run
-// takes the same decisions.
+// buffer, clears the next slot and decides termination (tolerance max(tol, 4 ulp(max|V|)),
+// FP32 stall, or max_sweeps).  Order independent, so every run takes the same decisions.
+// Standalone FP64 mode: the block maximum into cert64.
 template <typename T>
 __device__ void finish_block(const SweepCtl& sc, T res, T vmax, long long sweep) {
     if (threadIdx.x != 0 || sc.mode == kModeNone) return;
@@ -341,12 +339,8 @@ __device__ void finish_block(const SweepCtl& sc, T res, T vmax, long long sweep)
         return;
     }
     const int slot = (int)(sweep % kRing);
-    if (sc.mode == kModeLoop32) {
-        atomicMax(&c->res32[slot], fbits((float)res));
-        atomicMax(&c->vmax32[slot], fbits((float)vmax));
-    } else {
-        atomicMax(&c->res64[slot], dbits((double)res));
-    }
+    atomicMax(&c->res32[slot], fbits((float)res));
+    atomicMax(&c->vmax32[slot], fbits((float)vmax));
     __threadfence();
     const unsigned int t = atomicAdd(&c->ticket, 1u);
     if (t != gridDim.x - 1) return;
@@ -357,27 +351,21 @@ __device__ void finish_block(const SweepCtl& sc, T res, T vmax, long long sweep)
     c->final_buf = sc.out_index;
     const int next = (int)(k % kRing);
     int done = 0;
-    if (sc.mode == kModeLoop32) {
-        const float r = __uint_as_float(*((volatile unsigned int*)&c->res32[slot]));
-        const float vm = __uint_as_float(*((volatile unsigned int*)&c->vmax32[slot]));
-        c->res32[next] = 0u;
-        c->vmax32[next] = 0u;
-        int e = 0;
-        frexpf(vm, &e);
-        const double ulp = (vm > 0.0f) ? ldexp(1.0, e - 24) : 0.0;
-        const double tol_eff = fmax(c->tol, 4.0 * ulp);
-        if ((double)r < tol_eff) {
-            done = 1;
-        } else if (r < c->best_res) {
-            c->best_res = r;
-            c->since_best = 0;
-        } else if (++c->since_best >= kStallSweeps) {
-            done = 3;
-        }
-    } else {
-        const double r = __longlong_as_double((long long)*((volatile unsigned long long*)&c->res64[slot]));
-        c->res64[next] = 0ull;
-        if (r < c->tol) done = 1;
+    const float r = __uint_as_float(*((volatile unsigned int*)&c->res32[slot]));
+    const float vm = __uint_as_float(*((volatile unsigned int*)&c->vmax32[slot]));
+    c->res32[next] = 0u;
+    c->vmax32[next] = 0u;
+    int e = 0;
+    frexpf(vm, &e);
+    const double ulp = (vm > 0.0f) ? ldexp(1.0, e - 24) : 0.0;
+    const double tol_eff = fmax(c->tol, 4.0 * ulp);
+    if ((double)r < tol_eff) {
+        done = 1;
+    } else if (r < c->best_res) {
+        c->best_res = r;
+        c->since_best = 0;
+    } else if (++c->since_best >= kStallSweeps) {
+        done = 3;
     }
     if (!done && k >= c->max_sweeps) done = 2;
     if (*((volatile int*)&c->error) & kErrTimeout) done = 4;

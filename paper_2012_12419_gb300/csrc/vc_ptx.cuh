@@ -1,6 +1,6 @@
 // vc_ptx.cuh -- inline-PTX helpers shared by the pipelined sweep kernels: mbarrier
 // phase waits with an iteration limit, bulk global->shared copies counted on an
-// mbarrier, the L2 evict-first cache policy, and a named barrier for a warp subset.
+// mbarrier, the L2 evict-first cache policy, and the poll limit of a sweep's waits.
 #pragma once
 
 #include <stdint.h>
@@ -70,11 +70,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ long long wait_limit(const SweepCtl& sc) {
     const long long v = *((volatile long long*)&sc.ctl->spin_limit);
     return v > 0 ? v - 1 : kSpinLimit;
-}
-
-// Barrier `id` (1..15) over the first `threads` threads that reach it (a multiple of 32).
-__device__ __forceinline__ void named_barrier(int id, int threads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 }  // namespace vc
