@@ -114,6 +114,7 @@ static int loop32(Mdp* m, float* buf0, float* buf1, double tol, long long max_sw
         }
         if ((rc = read_ctl(m, st))) return rc;
         if (h.error & kErrTimeout) return fail(VC_ERR_TIMEOUT, "a bounded device-side wait expired");
+        if (h.error & kErrBounds) return fail(VC_ERR_CUDA, "a device bounds check failed (bounds-checking build)");
         if (h.error) return fail(VC_ERR_ARG, "a kernel flagged invalid input (infeasible policy)");
         if (h.done) break;
         const int slot = (int)((h.sweeps - 1) % kRing);

@@ -247,8 +247,19 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
                     const float rr = Rs[rl];
                     if (rr != -INFINITY) {
                         const int64_t lo = rp[rl], hi = rp[rl + 1];
-                        const float acc = row_dot_smem<VT>(cs + (lo - c0), vs + (lo - v0), (int)(hi - lo), a.V_in);
-                        q = rr + a.gamma * (Ss ? Ss[rl] * acc : acc);
+                        bool ok = true;
+#ifdef VC_DEBUG_BOUNDS
+                        // the row lies inside the staged slices and its columns index V
+                        ok = VC_IN_BOUNDS(sc.ctl, lo >= c0 && hi >= lo &&
+                                                      (hi - c0) * 4 <= (int64_t)(a.L.off_val - a.L.off_col));
+                        for (int64_t j = lo; ok && j < hi; ++j)
+                            ok = VC_IN_BOUNDS(sc.ctl, cs[j - c0] >= 0 && cs[j - c0] < a.S);
+#endif
+                        if (ok) {
+                            const float acc =
+                                row_dot_smem<VT>(cs + (lo - c0), vs + (lo - v0), (int)(hi - lo), a.V_in);
+                            q = rr + a.gamma * (Ss ? Ss[rl] * acc : acc);
+                        }
                     }
                 }
                 float b1 = q, b2 = -INFINITY;
@@ -304,8 +315,15 @@ __global__ void __launch_bounds__(kThreads) k_csr_direct(CsrArgs a, SweepCtl sc)
             const float rr = __ldg(a.R + r);
             if (rr != -INFINITY) {
                 const int64_t lo = __ldg(a.row_ptr + r), hi = __ldg(a.row_ptr + r + 1);
-                const float acc = row_dot_global<VT>(a.col, val, lo, (int)(hi - lo), a.V_in);
-                q = rr + a.gamma * (a.scale ? __ldg(a.scale + r) * acc : acc);
+                bool ok = true;
+#ifdef VC_DEBUG_BOUNDS
+                for (int64_t j = lo; ok && j < hi; ++j)
+                    ok = VC_IN_BOUNDS(sc.ctl, a.col[j] >= 0 && a.col[j] < a.S);
+#endif
+                if (ok) {
+                    const float acc = row_dot_global<VT>(a.col, val, lo, (int)(hi - lo), a.V_in);
+                    q = rr + a.gamma * (a.scale ? __ldg(a.scale + r) * acc : acc);
+                }
             }
         }
         float b1 = q, b2 = -INFINITY;

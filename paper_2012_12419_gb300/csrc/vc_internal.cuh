@@ -248,6 +248,20 @@ constexpr int kErrRowSum = 8;
 constexpr int kErrNoFeasible = 16;
 constexpr int kErrRowPtr = 32;
 constexpr int kErrTimeout = 64;
+constexpr int kErrBounds = 128;  // a bounds check of the VC_DEBUG_BOUNDS build failed
+
+// Bounds checks of the VC_DEBUG_BOUNDS build (the library's stand-in for a memory checker):
+// a failed check raises kErrBounds in the control block and the caller skips the access.
+// In the normal build the check is compiled out (always true, condition unevaluated).
+#ifdef VC_DEBUG_BOUNDS
+__device__ __forceinline__ bool in_bounds(Ctl* ctl, bool ok) {
+    if (!ok && ctl) atomicOr(&ctl->error, kErrBounds);
+    return ok;
+}
+#define VC_IN_BOUNDS(ctl, cond) in_bounds((ctl), (cond))
+#else
+#define VC_IN_BOUNDS(ctl, cond) true
+#endif
 
 // Bookkeeping mode of a sweep kernel.
 enum SweepMode : int {

@@ -312,6 +312,7 @@ int64_t sell_sweep_bytes(const Mdp* m) { return m->sell_bytes + 8 * (m->sell_sli
 // ------------------------------------------------------------------------ sweeps
 struct SellArgs {
     int64_t G;
+    int S;
     int A;
     float gamma;
     bool has_scale;
@@ -370,7 +371,7 @@ __device__ __forceinline__ float row_dot(const int32_t* cp, const VT* vp, int w,
 // R + gamma (scale) sum_j val_j V[col_j], the sum in column order.
 template <typename VT>
 __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a, int lane, float gamma, bool has_scale,
-                                         const float* __restrict__ V) {
+                                         const float* __restrict__ V, int S, Ctl* ctl) {
     const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
     const float rr = reinterpret_cast<const float*>(rec + 256)[a * kSellC + lane];
     if (rr == -INFINITY) return -INFINITY;
@@ -379,6 +380,14 @@ __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a,
     const int r0 = hdr[a], w = hdr[a + 1] - r0;
     const int32_t* cp = reinterpret_cast<const int32_t*>(rec + L.col) + r0 * kSellC + lane;
     const VT* vp = reinterpret_cast<const VT*>(rec + L.val) + r0 * kSellC + lane;
+#ifdef VC_DEBUG_BOUNDS
+    if (!VC_IN_BOUNDS(ctl, r0 >= 0 && w >= 0 && hdr[a + 1] <= rows)) return -INFINITY;
+    for (int j = 0; j < w; ++j)
+        if (!VC_IN_BOUNDS(ctl, cp[j * kSellC] >= 0 && cp[j * kSellC] < S)) return -INFINITY;
+#else
+    (void)S;
+    (void)ctl;
+#endif
     const float acc = row_dot<VT>(cp, vp, w, V);
     const float sc = has_scale ? reinterpret_cast<const float*>(rec + L.scale)[a * kSellC + lane] : 1.0f;
     return rr + gamma * (has_scale ? sc * acc : acc);
@@ -396,8 +405,8 @@ __device__ __forceinline__ void top2_step(int act, float q, float& b1, float& b2
 }
 
 __device__ __forceinline__ void write_state(const SellArgs& a, int s, float b1, float b2, int ia, float& res,
-                                            float& vabs) {
-    if (s < 0) return;
+                                            float& vabs, Ctl* ctl) {
+    if (s < 0 || !VC_IN_BOUNDS(ctl, s < a.S)) return;
     if (a.V_out) a.V_out[s] = b1;
     if (a.pi) a.pi[s] = ia;
     if (a.qgap) a.qgap[s] = (b2 == -INFINITY) ? INFINITY : b1 - b2;
@@ -418,8 +427,8 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellArgs a, SweepCtl sc) {
         float b1 = -INFINITY, b2 = -INFINITY;
         int ia = 0;
         for (int act = 0; act < a.A; ++act)
-            top2_step(act, block_q<VT>(rec, a.A, act, lane, a.gamma, a.has_scale, a.V_in), b1, b2, ia);
-        write_state(a, reinterpret_cast<const int32_t*>(rec + 128)[lane], b1, b2, ia, res, vabs);
+            top2_step(act, block_q<VT>(rec, a.A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl), b1, b2, ia);
+        write_state(a, reinterpret_cast<const int32_t*>(rec + 128)[lane], b1, b2, ia, res, vabs, sc.ctl);
     }
     if (sc.mode == kModeNone) return;
     res = block_max<float, kThreads>(res);
@@ -508,6 +517,11 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                         head += (unsigned long long)t.ring - pos;  // skip the ring's tail
                         pos = 0;
                     }
+                    if (!VC_IN_BOUNDS(sc.ctl, bytes <= (unsigned long long)t.ring)) {
+                        failed = 1;
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
                     // reuse bytes (and the slot) only after the tiles holding them are released
                     while (oldest < i && (head + bytes - rel > (unsigned long long)t.ring || i - oldest >= kSlots)) {
                         const int os = oldest % kSlots;
@@ -566,7 +580,15 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
             for (int k = 0; k < sl; ++k)
                 roff += rec_layout(A, reinterpret_cast<const int32_t*>(base + roff)[A], (int)sizeof(VT), a.has_scale)
                             .bytes;
-            qb[b * kSellC + lane] = block_q<VT>(base + roff, A, act, lane, a.gamma, a.has_scale, a.V_in);
+#ifdef VC_DEBUG_BOUNDS
+            {
+                const long long tile_bytes = (a.rec[(tile * t.TS + ns)] - a.rec[tile * t.TS]) * 128;
+                const long long rb =
+                    rec_layout(A, reinterpret_cast<const int32_t*>(base + roff)[A], (int)sizeof(VT), a.has_scale).bytes;
+                if (!VC_IN_BOUNDS(sc.ctl, roff + rb <= tile_bytes)) roff = 0;
+            }
+#endif
+            qb[b * kSellC + lane] = block_q<VT>(base + roff, A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl);
             __threadfence_block();
             __syncwarp();
             int l = 0;
@@ -579,7 +601,7 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                     float b1 = -INFINITY, b2 = -INFINITY;
                     int ia = 0;
                     for (int c = 0; c < A; ++c) top2_step(c, qb[(k * A + c) * kSellC + lane], b1, b2, ia);
-                    write_state(a, reinterpret_cast<const int32_t*>(rec + 128)[lane], b1, b2, ia, res, vabs);
+                    write_state(a, reinterpret_cast<const int32_t*>(rec + 128)[lane], b1, b2, ia, res, vabs, sc.ctl);
                     ro += rec_layout(A, reinterpret_cast<const int32_t*>(rec)[A], (int)sizeof(VT), a.has_scale).bytes;
                 }
                 __syncwarp();
@@ -672,6 +694,7 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
 int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st) {
     SellArgs a;
     a.G = m->sell_slices;
+    a.S = m->S;
     a.A = m->A;
     a.gamma = (float)m->gamma;
     a.has_scale = (m->fmt & 0xF) == VC_CSR_BF16;

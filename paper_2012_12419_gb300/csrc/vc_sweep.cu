@@ -65,6 +65,19 @@ __device__ __forceinline__ T expect_next(const Model& md, const Coef<T>& c, cons
     return vx + acc;
 }
 
+#ifdef VC_DEBUG_BOUNDS
+// Every state expect_next reads from post-decision state x lies in [0, S).
+template <int MH>
+__device__ __forceinline__ bool successors_in_range(const Model& md, int x, const Digits& d, Ctl* ctl) {
+    bool ok = x >= 0 && x < md.S && (d.ph ? x - 1 : x + 1) >= 0 && (d.ph ? x - 1 : x + 1) < md.S &&
+              (d.q >= md.Q || x + 2 < md.S);
+#pragma unroll
+    for (int k = 0; k < MH; k++)
+        if (k < md.H && d.occ[k] > 0) ok = ok && x - d.occ[k] * md.stride[k] >= 0 && x - md.stride[k] >= 0;
+    return VC_IN_BOUNDS(ctl, ok);
+}
+#endif
+
 // Expected one-step reward of the post-decision state: occupancy, queue and losses
 // (departures lose their tasks, a full queue loses the arrival).
 template <int MH, typename T>
@@ -90,6 +103,9 @@ __global__ void __launch_bounds__(kThreads) k_post(Model md, Coef<T> c, const T*
     for (int x = blockIdx.x * kThreads + threadIdx.x; x < md.S; x += gridDim.x * kThreads) {
         Digits d;
         decode<MH>(md, x, d);
+#ifdef VC_DEBUG_BOUNDS
+        if (!successors_in_range<MH>(md, x, d, sc.ctl)) continue;
+#endif
         U[x] = post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V, x, d);
     }
 }
@@ -111,10 +127,11 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
         // max in action order
         T uk[MH];
 #pragma unroll
-        for (int k = 0; k < MH; k++)
-            uk[k] = (d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1))
-                        ? U[s + md.stride[k] - 2]
-                        : T(-INFINITY);
+        for (int k = 0; k < MH; k++) {
+            const bool f = d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1) &&
+                           VC_IN_BOUNDS(sc.ctl, s + md.stride[k] - 2 >= 0 && s + md.stride[k] - 2 < md.S);
+            uk[k] = f ? U[s + md.stride[k] - 2] : T(-INFINITY);
+        }
         const T u = U[s];  // defer: the post-decision state is s itself; highest index, so ties keep lower ones
 #pragma unroll
         for (int k = 0; k < MH; k++) {
@@ -163,6 +180,9 @@ __global__ void __launch_bounds__(kThreads) k_resid64(Model md, Coef<double> c, 
             r[s] = 0.0f;
             continue;
         }
+#ifdef VC_DEBUG_BOUNDS
+        if (!successors_in_range<MH>(md, x, d, sc.ctl)) continue;
+#endif
         const double rd = post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V, x, d) - V[s];
         r[s] = (float)rd;
         mx = fmax(mx, fabs(rd));
@@ -191,6 +211,9 @@ __global__ void __launch_bounds__(kThreads) k_correct32(Model md, Coef<float> c,
             e_out[s] = e_in[s];
             continue;
         }
+#ifdef VC_DEBUG_BOUNDS
+        if (!successors_in_range<MH>(md, x, d, sc.ctl)) continue;
+#endif
         const float v = r[s] + c.gamma * expect_next<MH>(md, c, e_in, x, d);
         e_out[s] = v;
         res = fmaxf(res, fabsf(v - e_in[s]));

@@ -123,9 +123,11 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing and not _build.up_to_date():
-            _build.build()
+        # VC_DEBUG_BOUNDS=1 selects the bounds-checking build of the same library
+        debug = os.environ.get("VC_DEBUG_BOUNDS", "") == "1"
+        path = _build.LIB_DEBUG if debug else _build.LIB
+        if build_if_missing and not _build.up_to_date(debug):
+            _build.build(debug=debug)
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
         L = ctypes.CDLL(path)
