@@ -110,7 +110,7 @@ typedef struct vc_info {
 typedef struct vc_stats {
     int64_t sweeps;         /* FP32 Bellman sweeps performed */
     double residual;        /* last FP32 residual max|V^{k+1}-V^k| */
-    int64_t eval_sweeps;    /* FP64 policy-evaluation sweeps */
+    int64_t eval_sweeps;    /* FP32 correction sweeps of the policy-evaluation refinement */
     int64_t bellman64;      /* FP64 full Bellman backups (certification checks) */
     int32_t policy_rounds;  /* policy-improvement rounds inside the refinement */
     int32_t certified;      /* 1 if residual64 < tol */
@@ -356,7 +356,7 @@ typedef struct vc_batch_stats {
  * Build a batch of n independent instances (p: HOST array of n vc_params, each validated
  * as in vc_build_mdp; implicit form).  Instance i occupies states [off_i, off_i + S_i) of
  * the concatenated arrays, off from vc_batch_offsets.  The schedule (tile size, persistent
- * grid) starts at 256 states per tile and 4 blocks per SM; vc_batch_autotune picks one by
+ * grid) starts at 2048 states per tile and 8 blocks per SM; vc_batch_autotune picks one by
  * timing.  Two CUDA graphs are captured once per schedule: the FP32 value-iteration loop
  * and the refinement's correction loop, each a device-side WHILE loop.  Algorithm 3 for
  * every instance, applied to many cells of a vehicular cloud at once (the paper's BSDI
@@ -374,7 +374,8 @@ int vc_batch_offsets(const vc_batch* b, int64_t* offsets);
  * (max(tol, 4 ulp(max|V_i|)) or FP32 stall) and sweep count, in one graph launch; then,
  * unless VC_ITER_FP32_ONLY, every instance's argmax policy is evaluated by FP64 residual +
  * FP32 correction (one graph launch) + FP64 update and certified by one FP64 Bellman backup
- * (repeated while an instance fails).  V: [total] float in (warm start) / out (FP32
+ * (repeated while an instance fails); VC_ITER_ACCURATE certifies each instance's error
+ * (residual below tol (1 - gamma_i) / (2 gamma_i)).  V: [total] float in (warm start) / out (FP32
  * iterate); V64_out [total] double and pi_out [total] int32 nullable (pi is local to the
  * instance: 0..H_i); per_inst: HOST array of n stats (nullable).  Synchronises `stream`.
  * VC_ERR_NOT_CONVERGED if an instance is not certified (or, FP32 only, hit max_sweeps).
