@@ -61,14 +61,19 @@ def test_full_size_certificate_and_sampled_backups(name, fmt, padded, sliced):
     m.close()
 
 
-def test_large_logical_nnz_matches_closed_count():
-    # canonical successor count of the large workload, counted independently when the
-    # workload was specified: 130,468,750
+@pytest.mark.parametrize("name,nnz", [("large", 130_468_750), ("precision", 790_546_875), ("grad", 14_168_750)])
+def test_logical_nnz_matches_closed_count(name, nnz):
+    # canonical successor counts of the workloads, counted independently when they were
+    # specified, and recounted by the oracle's own enumeration
     native = native_or_skip()
-    m = native.MDP.build(inputs.workload("large"), fmt="implicit")
-    assert m.info()["nnz_logical"] == 130_468_750
-    m2 = native.MDP.build(inputs.workload("large"), fmt="csr_f32")
-    assert m2.info()["nnz_stored"] == 130_468_750
+    p = inputs.workload(name)
+    assert oracle.csr_nnz(p) == nnz
+    m = native.MDP.build(p, fmt="implicit")
+    assert m.info()["nnz_logical"] == nnz
+    m.close()
+    m2 = native.MDP.build(p, fmt="csr_f32")
+    assert m2.info()["nnz_stored"] == nnz
+    m2.close()
 
 
 def test_headline_configuration_equals_the_csr_kernel_bitwise():
