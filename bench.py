@@ -216,7 +216,9 @@ def run_native(args):
         },
         "time_to_residual_ms": statistics.median(ms),
         "sweeps_per_step": statistics.median(sweeps),
-        "fp64_eval_sweeps_per_step": statistics.median([s["eval_sweeps"] for s in stats]),
+        "fp32_correction_products_per_step": statistics.median([s["eval_sweeps"] for s in stats]),
+        "fp64_backups_per_step": statistics.median([s["bellman64"] for s in stats]),
+        "policy_rounds_per_step": statistics.median([s["policy_rounds"] for s in stats]),
         "ms_fp32_sweeps": statistics.median([s["ms_fp32"] for s in stats]),
         "ms_fp64_refine": statistics.median([s["ms_fp64"] for s in stats]),
         "certified": all(s["certified"] == 1 for s in stats),

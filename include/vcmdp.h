@@ -72,6 +72,8 @@ extern "C" {
 #define VC_ITER_ACCURATE 2   /* certify the error, not the residual: refine until the FP64
                                 residual is below tol (1-gamma)/(2 gamma), so that
                                 max|V64 - V*| <= gamma/(1-gamma) * residual <= tol/2 */
+#define VC_ITER_PLAIN_CORRECTION 4  /* solve the refinement's correction equation by
+                                       fixed-point sweeps instead of BiCGSTAB */
 
 /* Model parameters (host struct; mu and delta are HOST arrays of length H). */
 typedef struct vc_params {
@@ -110,7 +112,7 @@ typedef struct vc_info {
 typedef struct vc_stats {
     int64_t sweeps;         /* FP32 Bellman sweeps performed */
     double residual;        /* last FP32 residual max|V^{k+1}-V^k| */
-    int64_t eval_sweeps;    /* FP32 correction sweeps of the policy-evaluation refinement */
+    int64_t eval_sweeps;    /* FP32 products by P_pi in the refinement's correction solves */
     int64_t bellman64;      /* FP64 full Bellman backups (certification checks) */
     int32_t policy_rounds;  /* policy-improvement rounds inside the refinement */
     int32_t certified;      /* 1 if residual64 < tol */
@@ -203,10 +205,12 @@ int vc_set_wait_limit(vc_mdp* m, int64_t polls);
  * anything else = warm start / resume), out: the last FP32 iterate.  FP32 Jacobi sweeps
  * run until the sweep residual is below max(tol, 4 ulp(max|V|)), stops improving for
  * 64 sweeps (FP32 floor), or max_sweeps is reached.  Then, unless VC_ITER_FP32_ONLY,
- * the FP64 refinement: pi = argmax of the FP32 values, FP64 Jacobi evaluation of pi
- * until its sweep change is below tol, and an FP64 full Bellman backup V64 = T(V)
- * whose residual max|T V - V| is the certificate (policy improvement repeats if the
- * backup changes pi).  V64_out ([S] double, nullable) receives that backup, pi_out
+ * the FP64 refinement: pi = argmax of the FP32 values, evaluated by mixed-precision
+ * iterative refinement (FP64 policy residual, FP32 correction solve by BiCGSTAB -- or
+ * fixed-point sweeps with VC_ITER_PLAIN_CORRECTION or when BiCGSTAB breaks down -- FP64
+ * update) until the policy residual is below tol, and an FP64 full Bellman backup
+ * V64 = T(V) whose residual max|T V - V| is the certificate (policy improvement repeats
+ * if the backup changes pi).  V64_out ([S] double, nullable) receives that backup, pi_out
  * ([S] int32, nullable) its argmax.  Synchronises `stream`.
  * Errors: VC_ERR_NOT_CONVERGED if max_sweeps ran out (outputs still written),
  * VC_ERR_ARG for tol <= 0 or max_sweeps < 1.
@@ -270,12 +274,13 @@ int vc_greedy_policy(vc_mdp* m, int32_t* pi, void* stream);
 /*
  * Policy evaluation V_pi = R_pi + gamma P_pi V_pi (Eq. 18 with the action fixed) over the
  * chosen rows only, by mixed-precision iterative refinement: the policy residual
- * r = T_pi V - V and its maximum in FP64, the correction (I - gamma P_pi) e = r by FP32
- * Jacobi sweeps, V += e in FP64, until max|r| < tol (the point where an FP64 Jacobi sweep
- * would change V by less than tol).  pi: [S] int32 (feasible everywhere, else
- * VC_ERR_ARG); V_pi: [S] double, in: initial guess, out: the result.  *sweeps_out (host,
- * nullable) receives the FP32 correction sweeps.  VC_ERR_NOT_CONVERGED once max_sweeps
- * correction sweeps are spent.  Synchronises `stream`.
+ * r = T_pi V - V and its maximum in FP64, the correction (I - gamma P_pi) e = r solved in
+ * FP32 by BiCGSTAB (fixed-point sweeps if it breaks down) until its residual is below
+ * tol/2, V += e in FP64, until max|r| < tol (the point where an FP64 Jacobi sweep would
+ * change V by less than tol).  pi: [S] int32 (feasible everywhere, else VC_ERR_ARG);
+ * V_pi: [S] double, in: initial guess, out: the result.  *sweeps_out (host, nullable)
+ * receives the FP32 products by P_pi spent.  VC_ERR_NOT_CONVERGED once max_sweeps such
+ * products are spent.  Synchronises `stream`.
  */
 
 int vc_evaluate_policy(vc_mdp* m, const int32_t* pi, double* V_pi, double tol, int64_t max_sweeps,

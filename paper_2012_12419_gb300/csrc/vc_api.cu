@@ -10,6 +10,7 @@
 #include <string>
 
 #include "vc_internal.cuh"
+#include "vc_krylov.cuh"
 
 namespace vc {
 
@@ -34,10 +35,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 static void free_mdp(Mdp* m) {
     if (!m) return;
     void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64, m->V64a,
-                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->ctl, m->sell_rec, m->sell_slab};
+                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->kr, m->kr_part, m->kctl, m->ctl,
+                    m->sell_rec, m->sell_slab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->ctl_host) cudaFreeHost(m->ctl_host);
+    if (m->kctl_host) cudaFreeHost(m->kctl_host);
     delete m;
 }
 
@@ -54,6 +57,10 @@ static int alloc_work(Mdp* m) {
     if ((rc = alloc_dev(m, (void**)&m->Rres, 4 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->pi, 4 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->pi2, 4 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->kr, 20 * S))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->kr_part, 24 * (size_t)state_grid(m)))) return rc;
+    if ((rc = alloc_dev(m, (void**)&m->kctl, sizeof(KrylovCtl)))) return rc;
+    VC_CUDA(cudaMallocHost((void**)&m->kctl_host, sizeof(KrylovCtl)));
     if ((rc = alloc_dev(m, (void**)&m->ctl, sizeof(Ctl)))) return rc;
     VC_CUDA(cudaMallocHost((void**)&m->ctl_host, sizeof(Ctl)));
     memset(m->ctl_host, 0, sizeof(Ctl));
@@ -144,6 +151,38 @@ static int cert64(Mdp* m, const double* V_in, double* V_out, int32_t* pi_out, do
     if ((rc = read_ctl(m, st))) return rc;
     memcpy(residual, &m->ctl_host->cert64, 8);
     if (changes) *changes = m->ctl_host->changes;
+    return VC_OK;
+}
+
+// Correction solve of the refinement, (I - gamma P_pi) e = Rres until the recurrence
+// residual max |Rres - (I - gamma P_pi) e| is below target: BiCGSTAB (unless `plain`),
+// else, or when BiCGSTAB breaks down or reaches its iteration cap, fixed-point sweeps
+// e <- Rres + gamma P_pi e from e = 0 (each sweep's change is that residual).  *e_out
+// receives the buffer holding e, *products the products by P_pi spent.
+constexpr long long kKrylovMaxIter = 1000;
+
+static int correction_solve(Mdp* m, const int32_t* pi, double target, long long max_products, bool plain,
+                            cudaStream_t st, float** e_out, long long* products) {
+    *products = 0;
+    int rc;
+    if (!plain) {
+        bool conv = false;
+        long long prods = 0;
+        const long long iters = std::min<long long>(kKrylovMaxIter, std::max<long long>(max_products / 2, 1));
+        if ((rc = krylov_correct(m, pi, m->Rres, m->E0, target, iters, st, &prods, &conv))) return rc;
+        *products = prods;
+        if (conv) {
+            *e_out = m->E0;
+            return VC_OK;
+        }
+    }
+    VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * (size_t)m->S, st));
+    int efin = 0;
+    rc = loop32(m, m->E0, m->E1, target, std::max<long long>(max_products - *products, 1), st, &efin,
+                [&](const float* in, float* o, SweepCtl s2) { return launch_correct32(m, pi, m->Rres, in, o, s2, st); });
+    if (rc) return rc;
+    *products += m->ctl_host->sweeps;
+    *e_out = efin == 1 ? m->E1 : m->E0;
     return VC_OK;
 }
 
@@ -520,8 +559,9 @@ int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, 
     cudaStream_t st = (cudaStream_t)stream;
     // Mixed-precision iterative refinement of V_pi = R_pi + gamma P_pi V_pi: the policy
     // residual r = T_pi V - V and its maximum in FP64, the correction (I - gamma P_pi) e = r
-    // by FP32 Jacobi sweeps to tol/2, V += e in FP64; stop when max|r| < tol (the FP64
-    // Jacobi criterion: the next sweep would change V by less than tol).
+    // in FP32 (BiCGSTAB, fixed-point sweeps as the fallback) until its residual is below
+    // tol/2, V += e in FP64; stop when max|r| < tol (the FP64 Jacobi criterion: the next
+    // sweep would change V by less than tol).  max_sweeps caps the products by P_pi.
     long long total = 0;
     int rc;
     for (int round = 0; round < 60; round++) {
@@ -538,15 +578,12 @@ int vc_evaluate_policy(vc_mdp* mh, const int32_t* pi, double* V_pi, double tol, 
             return VC_OK;
         }
         if (total >= max_sweeps) break;
-        VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * (size_t)m->S, st));
-        int efin = 0;
-        rc = loop32(m, m->E0, m->E1, 0.5 * tol, max_sweeps - total, st, &efin,
-                    [&](const float* in, float* o, SweepCtl s2) {
-                        return launch_correct32(m, pi, m->Rres, in, o, s2, st);
-                    });
+        float* e = nullptr;
+        long long prods = 0;
+        rc = correction_solve(m, pi, 0.5 * tol, max_sweeps - total, false, st, &e, &prods);
+        total += prods;
         if (rc) return rc;
-        total += m->ctl_host->sweeps;
-        if ((rc = launch_axpy64(V_pi, efin == 1 ? m->E1 : m->E0, m->S, st))) return rc;
+        if ((rc = launch_axpy64(V_pi, e, m->S, st))) return rc;
     }
     VC_CUDA(cudaStreamSynchronize(st));
     if (sweeps_out) *sweeps_out = total;
@@ -602,12 +639,13 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
         }
         // ---- refinement: the argmax policy of the FP32 values (Algorithm 3, step 4) is
         // evaluated by mixed-precision iterative refinement -- policy residual
-        // r = T_pi V64 - V64 in FP64, correction (I - gamma P_pi) e = r solved by FP32
-        // Jacobi sweeps, V64 += e -- and certified by one FP64 Bellman backup whose
-        // residual is the step-3 test.  If the backup's argmax differs, the loop repeats
-        // with it (a policy-improvement step).  Since T_pi(V64 + e_k) - (V64 + e_k) equals
-        // the next correction change, stopping the correction at tol/2 leaves a policy
-        // residual below tol.
+        // r = T_pi V64 - V64 in FP64, correction (I - gamma P_pi) e = r solved in FP32 by
+        // BiCGSTAB (or fixed-point sweeps: VC_ITER_PLAIN_CORRECTION, and the fallback),
+        // V64 += e -- and certified by one FP64 Bellman backup whose residual is the
+        // step-3 test.  If the backup's argmax differs, the loop repeats with it (a
+        // policy-improvement step).  Since T_pi(V64 + e) - (V64 + e) = r - (I - gamma P_pi) e
+        // is the correction's own residual, solving it to tol/2 leaves a policy residual
+        // below tol (up to FP32 rounding of e).
         int32_t* pcur = m->pi;
         int32_t* pnew = m->pi2;
         {
@@ -629,15 +667,15 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
                 VC_CUDA(cudaMemsetAsync(&m->ctl->error, 0, sizeof(int), st));
                 if ((rc = launch_resid64(m, pcur, cur, m->Rres, sc, st))) goto out;
             }
-            VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * S, st));
-            int efin = 0;
-            rc = loop32(m, m->E0, m->E1, 0.5 * r_target, eval_max, st, &efin,
-                        [&](const float* in, float* o, SweepCtl sc) {
-                            return launch_correct32(m, pcur, m->Rres, in, o, sc, st);
-                        });
-            if (rc) goto out;
-            sx.eval_sweeps += m->ctl_host->sweeps;
-            if ((rc = launch_axpy64(cur, efin == 1 ? m->E1 : m->E0, m->S, st))) goto out;
+            {
+                float* e = nullptr;
+                long long prods = 0;
+                rc = correction_solve(m, pcur, 0.5 * r_target, eval_max, (flags & VC_ITER_PLAIN_CORRECTION) != 0, st,
+                                      &e, &prods);
+                sx.eval_sweeps += prods;
+                if (rc) goto out;
+                if ((rc = launch_axpy64(cur, e, m->S, st))) goto out;
+            }
             unsigned long long changes = 0;
             if ((rc = cert64(m, cur, other, pnew, nullptr, pcur, st, &r64, &changes))) goto out;
             sx.bellman64++;

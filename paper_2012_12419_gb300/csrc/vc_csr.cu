@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "vc_internal.cuh"
+#include "vc_krylov.cuh"
 #include "vc_ptx.cuh"
 
 namespace vc {
@@ -488,6 +489,32 @@ __global__ void __launch_bounds__(kThreads) k_csr_correct32(CsrArgs a, const int
     finish_block<float>(sc, res, vabs, sweep);
 }
 
+// Product by the correction matrix for the BiCGSTAB solve from the stored rows of pi:
+// y(s) = x(s) - gamma (scale) sum_j val_j x[col_j], with the stage's partial sums.
+template <typename VT>
+__global__ void __launch_bounds__(kThreads) k_csr_apply32(CsrArgs a, const int32_t* __restrict__ pi,
+                                                          const float* __restrict__ xin, float* __restrict__ y,
+                                                          const float* __restrict__ w, int stage, KrylovArgs k) {
+    if (kr_done(k)) return;
+    const VT* val = reinterpret_cast<const VT*>(a.val);
+    float d0 = 0.0f, d1 = 0.0f;
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
+        const int act = pi[s];
+        float yv = xin[s];
+        if (act >= 0 && act < a.A) {
+            const int64_t r = (int64_t)s * a.A + act;
+            float acc = 0.0f;
+            for (int64_t j = a.row_ptr[r]; j < a.row_ptr[r + 1]; j++) acc = fmaf(ldg_v<VT>(val, j), xin[a.col[j]], acc);
+            if (a.scale) acc *= a.scale[r];
+            yv -= a.gamma * acc;
+        }
+        y[s] = yv;
+        d0 = fmaf(w[s], yv, d0);
+        d1 = fmaf(yv, yv, d1);
+    }
+    kr_finish<kThreads>(k, stage, d0, d1, 0.0f);
+}
+
 // ------------------------------------------------------------------------- planning
 __global__ void k_tile_cap(const int64_t* __restrict__ row_ptr, int S, int A, int ts, int64_t ntiles,
                            unsigned long long* out) {
@@ -719,6 +746,18 @@ int csr_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl
         k_csr_resid64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc);
     else
         k_csr_resid64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc);
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+int csr_apply32(Mdp* m, const int32_t* pi, const float* x, float* y, const float* w, int stage,
+                const KrylovArgs& k, cudaStream_t st) {
+    const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
+    count_launches(1);
+    if ((m->fmt & 0xF) == VC_CSR_BF16)
+        k_csr_apply32<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, pi, x, y, w, stage, k);
+    else
+        k_csr_apply32<float><<<state_grid(m), kThreads, 0, st>>>(a, pi, x, y, w, stage, k);
     VC_CUDA(cudaGetLastError());
     return VC_OK;
 }

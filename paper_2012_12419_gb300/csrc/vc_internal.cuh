@@ -404,6 +404,8 @@ struct CsrPlan {
     int minb = 1;        // register budget of the sliced ring kernel (1: 80 registers, 2: 60)
 };
 
+struct KrylovCtl;  // vc_krylov.cuh
+
 struct Mdp {
     int fmt;              // VC_IMPLICIT / VC_CSR_F32 / VC_CSR_BF16 (| VC_PADDED)
     bool has_model;
@@ -440,6 +442,10 @@ struct Mdp {
     float* Rres = nullptr;      // FP32 copy of the FP64 policy residual
     int32_t* pi = nullptr;      // policy under refinement
     int32_t* pi2 = nullptr;
+    float* kr = nullptr;        // BiCGSTAB vectors of the correction solve: r, p, v, s, t ([5][S])
+    double* kr_part = nullptr;  // BiCGSTAB per-block partials ([3][grid])
+    KrylovCtl* kctl = nullptr;  // BiCGSTAB scalars (device) and their pinned mirror
+    KrylovCtl* kctl_host = nullptr;
     Ctl* ctl = nullptr;         // device control block
     Ctl* ctl_host = nullptr;    // pinned mirror
     int64_t device_bytes = 0;

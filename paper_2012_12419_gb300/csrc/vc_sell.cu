@@ -48,7 +48,8 @@ namespace vc {
 
 constexpr int kSellC = 32;
 constexpr int kSellSigma = 4096;
-constexpr int kSellBatch = 16;
+constexpr int kSellBatch = 16;  // gathers per batch of a row longer than kSellLast
+constexpr int kSellLast = 24;   // rows (and remainders) up to this length: one batch
 constexpr int kSellMaxA = 31;  // hdr holds A + 1 row offsets in 32 slots
 
 __host__ __device__ inline long long round128(long long x) { return (x + 127) & ~127LL; }
@@ -349,23 +350,26 @@ __device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, cons
     return acc;
 }
 
-// Row sum of w entries in column order: batches of 16, then one exactly sized batch for
-// the rest (no predicated slots).
+// Row sum of w entries in column order: rows of up to kSellLast entries in one exactly
+// sized batch (every gather of the row in flight at once), longer rows in batches of 16
+// until the rest fits one batch (no predicated slots).
 template <typename VT>
 __device__ __forceinline__ float row_dot(const int32_t* cp, const VT* vp, int w, const float* __restrict__ V) {
     float acc = 0.0f;
-    for (; w > kSellBatch; w -= kSellBatch, cp += kSellBatch * kSellC, vp += kSellBatch * kSellC)
+    for (; w > kSellLast; w -= kSellBatch, cp += kSellBatch * kSellC, vp += kSellBatch * kSellC)
         acc = dot_fixed<VT, kSellBatch>(cp, vp, V, acc);
     switch (w) {
 #define VC_DOT_CASE(n) \
     case n: return dot_fixed<VT, n>(cp, vp, V, acc);
         VC_DOT_CASE(1) VC_DOT_CASE(2) VC_DOT_CASE(3) VC_DOT_CASE(4) VC_DOT_CASE(5) VC_DOT_CASE(6) VC_DOT_CASE(7)
         VC_DOT_CASE(8) VC_DOT_CASE(9) VC_DOT_CASE(10) VC_DOT_CASE(11) VC_DOT_CASE(12) VC_DOT_CASE(13)
-        VC_DOT_CASE(14) VC_DOT_CASE(15) VC_DOT_CASE(16)
+        VC_DOT_CASE(14) VC_DOT_CASE(15) VC_DOT_CASE(16) VC_DOT_CASE(17) VC_DOT_CASE(18) VC_DOT_CASE(19)
+        VC_DOT_CASE(20) VC_DOT_CASE(21) VC_DOT_CASE(22) VC_DOT_CASE(23) VC_DOT_CASE(24)
 #undef VC_DOT_CASE
         default: return acc;
     }
 }
+static_assert(kSellLast >= kSellBatch, "a remainder must fit one batch");
 
 // Q value of lane `lane` in block `a` of a slice record (shared or global memory):
 // R + gamma (scale) sum_j val_j V[col_j], the sum in column order.
@@ -440,6 +444,7 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellArgs a, SweepCtl sc) {
 constexpr int kSlots = 12;      // tiles in flight per CTA
 constexpr int kMaxRW = 24;      // most consumer warps per CTA
 constexpr int kHead = 512;      // barriers and per-slot words at the start of shared memory
+constexpr int kMaxTS = 4;       // most slices per tile (the planner's tile sizes are 1, 2, 4)
 static_assert(kSlots * (8 + 8 + 4 + 4) <= 384 && 384 + 8 * kSlots <= kHead, "slot words exceed the header");
 
 struct SellRingArgs {
@@ -594,15 +599,28 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
             int l = 0;
             if (lane == 0) l = (atomicAdd(&done_cnt[s], 1) == nb - 1);
             if (__shfl_sync(0xffffffffu, l, 0)) {
+                // the tile's last block: the max over actions and the state map come out
+                // of shared memory first, the tile is released, and only then the state
+                // writes and the residual's read of V_in (global memory) follow, so the
+                // ring slot is not held over a global-memory round trip
                 __threadfence_block();
+                float b1v[kMaxTS], b2v[kMaxTS];
+                int iav[kMaxTS], sv[kMaxTS];
                 long long ro = 0;
-                for (int k = 0; k < ns; ++k) {
-                    const unsigned char* rec = base + ro;
-                    float b1 = -INFINITY, b2 = -INFINITY;
-                    int ia = 0;
-                    for (int c = 0; c < A; ++c) top2_step(c, qb[(k * A + c) * kSellC + lane], b1, b2, ia);
-                    write_state(a, reinterpret_cast<const int32_t*>(rec + 128)[lane], b1, b2, ia, res, vabs, sc.ctl);
-                    ro += rec_layout(A, reinterpret_cast<const int32_t*>(rec)[A], (int)sizeof(VT), a.has_scale).bytes;
+#pragma unroll
+                for (int k = 0; k < kMaxTS; ++k) {
+                    sv[k] = -1;
+                    if (k < ns) {
+                        const unsigned char* rec = base + ro;
+                        float b1 = -INFINITY, b2 = -INFINITY;
+                        int ia = 0;
+                        for (int c = 0; c < A; ++c) top2_step(c, qb[(k * A + c) * kSellC + lane], b1, b2, ia);
+                        b1v[k] = b1;
+                        b2v[k] = b2;
+                        iav[k] = ia;
+                        sv[k] = reinterpret_cast<const int32_t*>(rec + 128)[lane];
+                        ro += rec_layout(A, reinterpret_cast<const int32_t*>(rec)[A], (int)sizeof(VT), a.has_scale).bytes;
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -610,6 +628,9 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                     __threadfence_block();
                     mbar_arrive(&empty[s]);
                 }
+#pragma unroll
+                for (int k = 0; k < kMaxTS; ++k)
+                    if (k < ns) write_state(a, sv[k], b1v[k], b2v[k], iav[k], res, vabs, sc.ctl);
             }
         }
         if (lane == 0) atomicMin(&s_consumed, i);
@@ -647,6 +668,7 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
     // (CTAs per SM, consumer warps, register budget), preferred first
     const int shapes[][3] = {{2, 12, 1}, {2, 16, 2}, {3, 10, 2}, {1, 24, 1}, {2, 8, 1}, {3, 8, 1}};
     for (int TS : {1, 2, 4}) {
+        static_assert(kMaxTS >= 4, "the last block's registers cover every planned tile size");
         long long max_tile = 0;  // largest tile of TS slice records
         for (int64_t g0 = 0; g0 < (int64_t)rows.size(); g0 += TS) {
             long long b = 0;

@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "vc_internal.cuh"
+#include "vc_krylov.cuh"
 
 namespace vc {
 
@@ -225,6 +226,33 @@ __global__ void __launch_bounds__(kThreads) k_correct32(Model md, Coef<float> c,
     finish_block<float>(sc, res, vabs, sweep);
 }
 
+// Product by the correction matrix for the BiCGSTAB solve: y(s) = x(s) - gamma
+// E[x(next) | x_pi(s)], with the stage's partial sums <w, y> and <y, y>.  The policy was
+// checked feasible by the residual pass; an infeasible entry would act as the identity.
+template <int MH>
+__global__ void __launch_bounds__(kThreads) k_apply32(Model md, Coef<float> c, const int32_t* __restrict__ pi,
+                                                      const float* __restrict__ xin, float* __restrict__ y,
+                                                      const float* __restrict__ w, int stage, KrylovArgs k) {
+    if (kr_done(k)) return;
+    float d0 = 0.0f, d1 = 0.0f;
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < md.S; s += gridDim.x * kThreads) {
+        Digits d;
+        decode<MH>(md, s, d);
+        int x = s;
+        float yv = xin[s];
+        if (apply_action<MH>(md, s, pi[s], d, x)) {
+#ifdef VC_DEBUG_BOUNDS
+            if (successors_in_range<MH>(md, x, d, k.ctl))
+#endif
+                yv -= c.gamma * expect_next<MH>(md, c, xin, x, d);
+        }
+        y[s] = yv;
+        d0 = fmaf(w[s], yv, d0);
+        d1 = fmaf(yv, yv, d1);
+    }
+    kr_finish<kThreads>(k, stage, d0, d1, 0.0f);
+}
+
 __global__ void k_axpy64(double* __restrict__ V, const float* __restrict__ e, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) V[i] += (double)e[i];
 }
@@ -295,6 +323,18 @@ int launch_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_i
     count_launches(1);
     by_h(m, [&](auto mh) {
         k_correct32<decltype(mh)::value><<<state_grid(m), kThreads, 0, st>>>(m->md, m->c32, pi, r, e_in, e_out, sc);
+        return 0;
+    });
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
+int launch_apply32(Mdp* m, const int32_t* pi, const float* x, float* y, const float* w, int stage,
+                   const KrylovArgs& k, cudaStream_t st) {
+    if (!m->has_model) return csr_apply32(m, pi, x, y, w, stage, k, st);
+    count_launches(1);
+    by_h(m, [&](auto mh) {
+        k_apply32<decltype(mh)::value><<<state_grid(m), kThreads, 0, st>>>(m->md, m->c32, pi, x, y, w, stage, k);
         return 0;
     });
     VC_CUDA(cudaGetLastError());

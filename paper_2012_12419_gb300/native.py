@@ -34,6 +34,7 @@ VC_VAL_F32 = 0
 VC_VAL_BF16 = 1
 VC_ITER_FP32_ONLY = 1
 VC_ITER_ACCURATE = 2
+VC_ITER_PLAIN_CORRECTION = 4
 
 FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF16}
 
@@ -287,10 +288,12 @@ class MDP:
     # ------------------------------------------------------------------------- solve
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
                       want_v64: bool = True, want_pi: bool = True, stream=None, raise_on_nonconvergence=True,
-                      accurate: bool = False):
+                      accurate: bool = False, plain_correction: bool = False):
         """Algorithm 3 on the device.  Returns (V fp32, V64 fp64 or None, pi int32 or None, stats dict).
 
-        accurate=True certifies the error rather than the residual: max|V64 - V*| <= tol / 2."""
+        accurate=True certifies the error rather than the residual: max|V64 - V*| <= tol / 2.
+        plain_correction=True solves the refinement's correction equation by fixed-point
+        sweeps instead of BiCGSTAB."""
         dev = _dev()
         S = self.S
         if V is None:
@@ -298,7 +301,8 @@ class MDP:
         V64 = torch.empty(S, dtype=torch.float64, device=dev) if want_v64 else None
         pi = torch.empty(S, dtype=torch.int32, device=dev) if want_pi else None
         st = Stats()
-        flags = (VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
+        flags = ((VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
+                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0))
         rc = load().vc_value_iterate(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                      flags, ctypes.byref(st), _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
