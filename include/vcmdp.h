@@ -351,7 +351,7 @@ typedef struct vc_batch_info_t {
 /* Per-instance result of vc_value_iterate_batch (host struct array of length n). */
 typedef struct vc_batch_stats {
     int64_t sweeps;            /* FP32 sweeps of this instance */
-    int64_t correction_sweeps; /* FP32 correction sweeps of its refinement */
+    int64_t correction_sweeps; /* FP32 products by P_pi in its refinement's correction solves */
     double residual64;         /* FP64 max|T V - V| of its certified values */
     int32_t certified;         /* residual64 < tol */
     int32_t termination;       /* FP32 loop: 1 tolerance, 2 max_sweeps, 3 FP32 floor stall */
@@ -378,8 +378,10 @@ int vc_batch_offsets(const vc_batch* b, int64_t* offsets);
  * Value iteration of every instance (Algorithm 3), each with its own gamma, tolerance test
  * (max(tol, 4 ulp(max|V_i|)) or FP32 stall) and sweep count, in one graph launch; then,
  * unless VC_ITER_FP32_ONLY, every instance's argmax policy is evaluated by FP64 residual +
- * FP32 correction (one graph launch) + FP64 update and certified by one FP64 Bellman backup
- * (repeated while an instance fails); VC_ITER_ACCURATE certifies each instance's error
+ * FP32 correction (BiCGSTAB for every instance in one graph launch; fixed-point sweeps with
+ * VC_ITER_PLAIN_CORRECTION or if an instance breaks down) + FP64 update and certified by
+ * one FP64 Bellman backup (repeated while an instance fails); VC_ITER_ACCURATE certifies
+ * each instance's error
  * (residual below tol (1 - gamma_i) / (2 gamma_i)).  V: [total] float in (warm start) / out (FP32
  * iterate); V64_out [total] double and pi_out [total] int32 nullable (pi is local to the
  * instance: 0..H_i); per_inst: HOST array of n stats (nullable).  Synchronises `stream`.

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "vc_internal.cuh"
+#include "vc_krylov.cuh"
 
 namespace vc {
 
@@ -321,6 +322,229 @@ __global__ void k_bcorr(const InstDesc* __restrict__ descs, const BatchTile* __r
     }
 }
 
+// ------------------------------------------------ batched BiCGSTAB correction solve
+// The refinement's correction equations (I - gamma_i P_pi,i) e_i = r_i of every instance,
+// solved together by BiCGSTAB (one iteration = five kernels over the tile table, one
+// graph-loop pass).  Every reducing kernel writes one partial per tile; the instance's
+// last tile (ticket) sums the instance's tile partials in tile order and advances the
+// instance's scalars, and retires the instance once its residual is below its target.
+struct BatchKrylov {
+    double *rho, *alpha, *omega, *beta, *target;  // [n] per-instance scalars
+    float* rmax;                                  // [n] max |r| after the last iteration
+    int* done;                                    // [n] 0 running, 1 converged, 2 cap, 5 breakdown
+    int* iter;                                    // [n] iterations completed
+    unsigned int* ticket;                         // [n] arrivals of the current kernel
+    const int* tiles_of;                          // [n] tiles per instance
+    const int* tile_first;                        // [n] first tile of each instance
+    double* part;                                 // [ntiles][3] tile partials
+    int* active;                                  // instances still iterating
+    long long* iters;                             // graph-loop passes
+    const long long* max_iter;
+    const float* b;                               // right-hand sides (policy residuals)
+    float *x, *r, *p, *v, *s, *t;                 // concatenated vectors
+};
+
+// Scalars of instance i after `stage`, from its totals (one thread).
+__device__ void bkr_advance(const BatchKrylov& K, int i, int stage, double d0, double d1, double mx) {
+    int done = 0;
+    if (stage == kKrInit) {
+        K.rho[i] = d0;
+        K.rmax[i] = (float)mx;
+        K.alpha[i] = K.omega[i] = 1.0;
+        K.beta[i] = 0.0;
+        K.iter[i] = 0;
+        K.target[i] = fmax(K.target[i], ldexp(mx, -18));  // the reach of one FP32 solve
+        if (mx < K.target[i]) done = 1;
+        else if (!(d0 > 0.0)) done = 5;
+    } else if (stage == kKrV) {
+        if (d0 == 0.0 || !isfinite(d0)) done = 5;
+        else K.alpha[i] = K.rho[i] / d0;
+    } else if (stage == kKrT) {
+        const double om = (d1 > 0.0) ? d0 / d1 : 0.0;
+        K.omega[i] = om;
+        if (!isfinite(om)) done = 5;
+    } else {
+        K.rmax[i] = (float)mx;
+        const int it = K.iter[i] + 1;
+        K.iter[i] = it;
+        if (mx < K.target[i]) {
+            done = 1;
+        } else if (it >= *K.max_iter) {
+            done = 2;
+        } else if (K.omega[i] == 0.0 || K.rho[i] == 0.0 || !isfinite(mx)) {
+            done = 5;
+        } else {
+            const double be = (d0 / K.rho[i]) * (K.alpha[i] / K.omega[i]);
+            K.beta[i] = be;
+            K.rho[i] = d0;
+            if (!isfinite(be) || d0 == 0.0) done = 5;
+        }
+    }
+    K.ticket[i] = 0;
+    if (done) {
+        K.done[i] = done;
+        atomicSub(K.active, 1);
+    }
+    __threadfence();
+}
+
+// Tile epilogue of a reducing kernel: every thread of the block calls it once per tile.
+__device__ void bkr_tile_finish(const BatchKrylov& K, int tile, int inst, int stage, float d0, float d1, float mx) {
+    __shared__ int last;
+    const double s0 = block_sum<kThreads>((double)d0);
+    const double s1 = block_sum<kThreads>((double)d1);
+    const float m = block_max<float, kThreads>(mx);
+    if (threadIdx.x == 0) {
+        K.part[3 * (long long)tile] = s0;
+        K.part[3 * (long long)tile + 1] = s1;
+        K.part[3 * (long long)tile + 2] = (double)m;
+        __threadfence();
+        last = (atomicAdd(&K.ticket[inst], 1u) == (unsigned)K.tiles_of[inst] - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const long long t0 = K.tile_first[inst];
+    const int nt = K.tiles_of[inst];
+    double a0 = 0.0, a1 = 0.0, am = 0.0;
+    for (int j = threadIdx.x; j < nt; j += kThreads) {
+        a0 += __ldcg(K.part + 3 * (t0 + j));
+        a1 += __ldcg(K.part + 3 * (t0 + j) + 1);
+        am = fmax(am, __ldcg(K.part + 3 * (t0 + j) + 2));
+    }
+    a0 = block_sum<kThreads>(a0);
+    a1 = block_sum<kThreads>(a1);
+    am = block_max<double, kThreads>(am);
+    if (threadIdx.x == 0) bkr_advance(K, inst, stage, a0, a1, am);
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool bkr_skip(const BatchKrylov& K, int inst) {
+    __shared__ int skip;
+    if (threadIdx.x == 0) skip = *((volatile int*)&K.done[inst]) != 0;
+    __syncthreads();
+    const bool r = skip != 0;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bkr_init(const InstDesc* __restrict__ descs,
+                                                       const BatchTile* __restrict__ tiles, int ntiles, BatchKrylov K) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (bkr_skip(K, tl.inst)) continue;
+        const long long off = descs[tl.inst].off + tl.start;
+        float d0 = 0.0f, mx = 0.0f;
+        for (int j = threadIdx.x; j < tl.count; j += kThreads) {
+            const float bv = K.b[off + j];
+            K.r[off + j] = bv;
+            K.x[off + j] = 0.0f;
+            d0 = fmaf(bv, bv, d0);
+            mx = fmaxf(mx, fabsf(bv));
+        }
+        bkr_tile_finish(K, t, tl.inst, kKrInit, d0, 0.0f, mx);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bkr_p(const InstDesc* __restrict__ descs,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, BatchKrylov K) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (bkr_skip(K, tl.inst)) continue;
+        const long long off = descs[tl.inst].off + tl.start;
+        const bool first = K.iter[tl.inst] == 0;
+        const float be = (float)K.beta[tl.inst], om = (float)K.omega[tl.inst];
+        for (int j = threadIdx.x; j < tl.count; j += kThreads)
+            K.p[off + j] = first ? K.r[off + j] : fmaf(be, fmaf(-om, K.v[off + j], K.p[off + j]), K.r[off + j]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bkr_s(const InstDesc* __restrict__ descs,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, BatchKrylov K) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (bkr_skip(K, tl.inst)) continue;
+        const long long off = descs[tl.inst].off + tl.start;
+        const float al = (float)K.alpha[tl.inst];
+        for (int j = threadIdx.x; j < tl.count; j += kThreads) K.s[off + j] = fmaf(-al, K.v[off + j], K.r[off + j]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_bkr_x(const InstDesc* __restrict__ descs,
+                                                    const BatchTile* __restrict__ tiles, int ntiles, BatchKrylov K) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (bkr_skip(K, tl.inst)) continue;
+        const long long off = descs[tl.inst].off + tl.start;
+        const float al = (float)K.alpha[tl.inst], om = (float)K.omega[tl.inst];
+        float d0 = 0.0f, mx = 0.0f;
+        for (int j = threadIdx.x; j < tl.count; j += kThreads) {
+            const long long g = off + j;
+            const float sv = K.s[g];
+            K.x[g] += fmaf(al, K.p[g], om * sv);
+            const float rv = fmaf(-om, K.t[g], sv);
+            K.r[g] = rv;
+            d0 = fmaf(K.b[g], rv, d0);
+            mx = fmaxf(mx, fabsf(rv));
+        }
+        bkr_tile_finish(K, t, tl.inst, kKrX, d0, 0.0f, mx);
+    }
+}
+
+// y = x - gamma_i E[x(next) | x_pi(s)] per instance, with the stage's partial sums <w, y>
+// and <y, y>.  The policy was checked feasible by k_bresid64.
+template <int MH>
+__global__ void __launch_bounds__(kThreads) k_bkr_apply(const InstDesc* __restrict__ descs,
+                                                        const BatchTile* __restrict__ tiles, int ntiles,
+                                                        const int32_t* __restrict__ pi, const float* __restrict__ xin,
+                                                        float* __restrict__ y, const float* __restrict__ w, int stage,
+                                                        BatchKrylov K) {
+    __shared__ InstDesc sd;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (bkr_skip(K, tl.inst)) continue;
+        load_desc(descs, tl.inst, sd);
+        __syncthreads();
+        const float* Xi = xin + sd.off;
+        float d0 = 0.0f, d1 = 0.0f;
+        for (int j = threadIdx.x; j < tl.count; j += kThreads) {
+            const int s = tl.start + j;
+            const long long g = sd.off + s;
+            Digits d;
+            decode<MH>(sd.md, s, d);
+            int x = s;
+            float yv = Xi[s];
+            if (apply_action<MH>(sd.md, s, pi[g], d, x)) yv -= sd.c32.gamma * b_expect<MH>(sd.md, sd.c32, Xi, x, d);
+            y[g] = yv;
+            d0 = fmaf(w[g], yv, d0);
+            d1 = fmaf(yv, yv, d1);
+        }
+        bkr_tile_finish(K, t, tl.inst, stage, d0, d1, 0.0f);
+    }
+}
+
+// Keeps the BiCGSTAB graph loop running while instances iterate and the budget lasts.
+__global__ void k_bkr_cond(cudaGraphConditionalHandle h, BatchKrylov K) {
+    const long long it = *K.iters + 1;
+    *K.iters = it;
+    const int go = (*((volatile int*)K.active) > 0) && (it < *K.max_iter);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Per-instance start of a solve: target (x tol_scale), counters cleared.
+__global__ void k_bkr_reset(BatchKrylov K, int n, double target, const float* tol_scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        K.done[i] = 0;
+        K.iter[i] = 0;
+        K.ticket[i] = 0u;
+        K.target[i] = target * (double)tol_scale[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *K.active = n;
+        *K.iters = 0;
+    }
+}
+
 // Per-instance selection of the final ping-pong buffer into out (float or double).
 template <typename TI, typename TO>
 __global__ void k_bselect(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
@@ -400,8 +624,17 @@ struct Batch {
     long long* max_d = nullptr;
     double* tol_d = nullptr;
     float* tol_scale = nullptr;  // per-instance factor of the correction loop's tolerance
-    cudaGraph_t g_vi = nullptr, g_corr = nullptr;
-    cudaGraphExec_t x_vi = nullptr, x_corr = nullptr;
+    // BiCGSTAB correction solve: vectors r, p, v, s, t ([5][total]; x is E0), tile partials,
+    // per-instance scalars
+    float* kr = nullptr;
+    double* kr_part = nullptr;  // [ntiles][3], sized with the tile table
+    double *kr_rho = nullptr, *kr_alpha = nullptr, *kr_omega = nullptr, *kr_beta = nullptr, *kr_target = nullptr;
+    float* kr_rmax = nullptr;
+    int *kr_done = nullptr, *kr_iter = nullptr, *tile_first = nullptr;
+    unsigned int* kr_ticket = nullptr;
+    long long* kr_max_d = nullptr;
+    cudaGraph_t g_vi = nullptr, g_corr = nullptr, g_kry = nullptr;
+    cudaGraphExec_t x_vi = nullptr, x_corr = nullptr, x_kry = nullptr;
     std::vector<void*> owned;
     int64_t device_bytes = 0;
     std::string tune_report;
@@ -439,6 +672,34 @@ static BatchCtl ctl_of(Batch* b, bool scaled = false) {
     return c;
 }
 
+static BatchKrylov kry_of(Batch* b) {
+    BatchKrylov K;
+    const size_t T = (size_t)b->total;
+    K.rho = b->kr_rho;
+    K.alpha = b->kr_alpha;
+    K.omega = b->kr_omega;
+    K.beta = b->kr_beta;
+    K.target = b->kr_target;
+    K.rmax = b->kr_rmax;
+    K.done = b->kr_done;
+    K.iter = b->kr_iter;
+    K.ticket = b->kr_ticket;
+    K.tiles_of = b->tiles_of;
+    K.tile_first = b->tile_first;
+    K.part = b->kr_part;
+    K.active = b->active;
+    K.iters = b->iters;
+    K.max_iter = b->kr_max_d;
+    K.b = b->Rr;
+    K.x = b->E0;
+    K.r = b->kr;
+    K.p = b->kr + T;
+    K.v = b->kr + 2 * T;
+    K.s = b->kr + 3 * T;
+    K.t = b->kr + 4 * T;
+    return K;
+}
+
 // Tile table for tile size ts; tiles of an instance are contiguous in the table.
 static int build_tiles(Batch* b, cudaStream_t st) {
     std::vector<BatchTile> tiles;
@@ -456,10 +717,17 @@ static int build_tiles(Batch* b, cudaStream_t st) {
         }
     }
     b->ntiles = (int)tiles.size();
+    std::vector<int> first(b->n, 0);
+    for (int i = 1; i < b->n; i++) first[i] = first[i - 1] + b->h_tiles_of[i - 1];
     if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->kr_part) cudaFree(b->kr_part);
+    b->d_tiles = nullptr;
+    b->kr_part = nullptr;
     VC_CUDA(cudaMalloc((void**)&b->d_tiles, sizeof(BatchTile) * tiles.size()));
+    VC_CUDA(cudaMalloc((void**)&b->kr_part, 3 * sizeof(double) * tiles.size()));
     VC_CUDA(cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, st));
     VC_CUDA(cudaMemcpyAsync(b->tiles_of, b->h_tiles_of.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(b->tile_first, first.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, st));
     VC_CUDA(cudaStreamSynchronize(st));
     b->grid = std::max(1, std::min(b->ntiles, b->num_sms * b->bps));
     return VC_OK;
@@ -469,6 +737,8 @@ static int build_tiles(Batch* b, cudaStream_t st) {
 // passes x this after every graph launch, since the graph runs them without a host call.
 constexpr int kViBodyKernels = 5;
 constexpr int kCorrBodyKernels = 3;
+constexpr int kKryBodyKernels = 6;      // one BiCGSTAB iteration per pass
+constexpr long long kKrylovMaxIter = 1000;
 
 template <int MH>
 static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
@@ -488,6 +758,17 @@ static void enqueue_corr_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHan
     k_bcorr<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 0, b->pi, b->Rr, b->E0, b->E1);
     k_bcorr<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, b->pi, b->Rr, b->E1, b->E0);
     k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
+}
+
+template <int MH>
+static void enqueue_kry_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
+    const BatchKrylov K = kry_of(b);
+    k_bkr_p<<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, K);
+    k_bkr_apply<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, K.p, K.v, K.b, kKrV, K);
+    k_bkr_s<<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, K);
+    k_bkr_apply<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, K.s, K.t, K.s, kKrT, K);
+    k_bkr_x<<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, K);
+    k_bkr_cond<<<1, 1, 0, cs>>>(h, K);
 }
 
 // One graph: a WHILE node (default condition 1 at every launch) whose body is built by
@@ -539,8 +820,17 @@ static int build_graphs(Batch* b) {
         else
             enqueue_corr_body<16>(b, cs, h);
     };
+    auto kry = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        if (b->mh == 4)
+            enqueue_kry_body<4>(b, cs, h);
+        else if (b->mh == 8)
+            enqueue_kry_body<8>(b, cs, h);
+        else
+            enqueue_kry_body<16>(b, cs, h);
+    };
     if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, vi))) return rc;
     if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, corr))) return rc;
+    if ((rc = make_loop_graph(&b->g_kry, &b->x_kry, kry))) return rc;
     return VC_OK;
 }
 
@@ -550,8 +840,11 @@ static void free_batch(Batch* b) {
     if (b->g_vi) cudaGraphDestroy(b->g_vi);
     if (b->x_corr) cudaGraphExecDestroy(b->x_corr);
     if (b->g_corr) cudaGraphDestroy(b->g_corr);
+    if (b->x_kry) cudaGraphExecDestroy(b->x_kry);
+    if (b->g_kry) cudaGraphDestroy(b->g_kry);
     for (void* p : b->owned) cudaFree(p);
     if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->kr_part) cudaFree(b->kr_part);
     delete b;
 }
 
@@ -660,6 +953,21 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
     if (!rc) rc = balloc(b, (void**)&b->max_d, 16);
     if (!rc) rc = balloc(b, (void**)&b->tol_d, 16);
     if (!rc) rc = balloc(b, (void**)&b->tol_scale, 4 * N);
+    if (!rc) rc = balloc(b, (void**)&b->kr, 20 * T);
+    void** kd[] = {(void**)&b->kr_rho, (void**)&b->kr_alpha, (void**)&b->kr_omega, (void**)&b->kr_beta,
+                   (void**)&b->kr_target};
+    for (void** pp : kd)
+        if (!rc) rc = balloc(b, pp, 8 * N);
+    void** k4[] = {(void**)&b->kr_rmax, (void**)&b->kr_done, (void**)&b->kr_iter, (void**)&b->kr_ticket,
+                   (void**)&b->tile_first};
+    for (void** pp : k4)
+        if (!rc) rc = balloc(b, pp, 4 * N);
+    if (!rc) rc = balloc(b, (void**)&b->kr_max_d, 16);
+    if (!rc) {
+        const long long mi = kKrylovMaxIter;
+        cudaError_t e = cudaMemcpy(b->kr_max_d, &mi, sizeof(mi), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpy(iteration cap)");
+    }
     if (!rc) rc = balloc(b, (void**)&b->d_desc, sizeof(InstDesc) * N);
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc.data(), sizeof(InstDesc) * N, cudaMemcpyHostToDevice, st);
@@ -727,7 +1035,8 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     bool all_cert = false;
     if (!(flags & VC_ITER_FP32_ONLY)) {
         // ---- refinement of every instance: argmax policy, FP64 residual, FP32 correction
-        // (one graph launch), FP64 update, FP64 Bellman certificate; repeat on failures.
+        // by BiCGSTAB (one graph launch; fixed-point sweeps as the fallback), FP64 update,
+        // FP64 Bellman certificate; repeat on failures.
         by_mh(b->mh, [&](auto m) { enqueue_extract<decltype(m)::value>(b, V, b->pi, st); });
         count_launches(3);
         k_f32_to_f64_n<<<b->grid, kThreads, 0, st>>>(V, b->V64, (long long)T);
@@ -741,21 +1050,55 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
                 scale[i] = (float)((1.0 - g) / (2.0 * g));
             }
         VC_CUDA(cudaMemcpyAsync(b->tol_scale, scale.data(), 4 * N, cudaMemcpyHostToDevice, st));
+        const bool plain = (flags & VC_ITER_PLAIN_CORRECTION) != 0;
         for (int round = 0; round < 20; round++) {
             VC_CUDA(cudaMemsetAsync(b->err, 0, 4, st));
             count_launches(1);
             by_mh(b->mh, [&](auto m) { enqueue_resid<decltype(m)::value>(b, st); });
-            VC_CUDA(cudaMemsetAsync(b->E0, 0, 4 * T, st));
-            if ((rc = reset_loop(b, 0.5 * tol, eval_max, st))) return rc;
             int herr = 0;
             VC_CUDA(cudaMemcpyAsync(&herr, b->err, 4, cudaMemcpyDeviceToHost, st));
-            VC_CUDA(cudaGraphLaunch(b->x_corr, st));
-            VC_CUDA(cudaMemcpyAsync(&corr_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
-            count_launches(1);
-            k_baxpy<<<b->grid, kThreads, 0, st>>>(b->E0, b->E1, b->d_desc, b->d_tiles, b->ntiles, b->final_buf,
-                                                  b->V64);
-            std::vector<int> cs(N);
-            VC_CUDA(cudaMemcpyAsync(cs.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
+            std::vector<int> cs(N, 0);
+            bool solved = false;
+            if (!plain) {
+                // BiCGSTAB for every instance's correction equation: one graph launch
+                const BatchKrylov K = kry_of(b);
+                count_launches(2);
+                k_bkr_reset<<<(b->n + 255) / 256, 256, 0, st>>>(K, b->n, 0.5 * tol, b->tol_scale);
+                k_bkr_init<<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, K);
+                VC_CUDA(cudaGetLastError());
+                VC_CUDA(cudaGraphLaunch(b->x_kry, st));
+                long long kit = 0;
+                std::vector<int> kd(N), ki(N);
+                VC_CUDA(cudaMemcpyAsync(&kit, b->iters, 8, cudaMemcpyDeviceToHost, st));
+                VC_CUDA(cudaMemcpyAsync(kd.data(), b->kr_done, 4 * N, cudaMemcpyDeviceToHost, st));
+                VC_CUDA(cudaMemcpyAsync(ki.data(), b->kr_iter, 4 * N, cudaMemcpyDeviceToHost, st));
+                VC_CUDA(cudaStreamSynchronize(st));
+                count_launches((int)(kit * kKryBodyKernels));
+                if (herr) return fail(VC_ERR_CUDA, "internal: batched refinement policy infeasible");
+                solved = true;
+                for (size_t i = 0; i < N; i++) {
+                    cs[i] = 2 * ki[i];
+                    solved = solved && kd[i] == 1;
+                }
+                if (solved && (rc = launch_axpy64(b->V64, b->E0, (int)T, st))) return rc;
+            }
+            if (!solved) {
+                // fixed-point correction sweeps (VC_ITER_PLAIN_CORRECTION, or BiCGSTAB broke
+                // down for an instance): e <- r + gamma P_pi e from e = 0 for every instance
+                VC_CUDA(cudaMemsetAsync(b->E0, 0, 4 * T, st));
+                if ((rc = reset_loop(b, 0.5 * tol, eval_max, st))) return rc;
+                VC_CUDA(cudaGraphLaunch(b->x_corr, st));
+                VC_CUDA(cudaMemcpyAsync(&corr_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
+                count_launches(1);
+                k_baxpy<<<b->grid, kThreads, 0, st>>>(b->E0, b->E1, b->d_desc, b->d_tiles, b->ntiles, b->final_buf,
+                                                      b->V64);
+                std::vector<int> cs2(N);
+                VC_CUDA(cudaMemcpyAsync(cs2.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
+                VC_CUDA(cudaStreamSynchronize(st));
+                count_launches((int)(corr_iters / 2 * kCorrBodyKernels));
+                corr_iters = 0;
+                for (size_t i = 0; i < N; i++) cs[i] += cs2[i];
+            }
             VC_CUDA(cudaMemsetAsync(b->res64, 0, 8 * N, st));
             count_launches(2);
             by_mh(b->mh, [&](auto m) { enqueue_cert<decltype(m)::value>(b, st); });
@@ -764,7 +1107,6 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             VC_CUDA(cudaMemcpyAsync(b->V64, b->V64b, 8 * T, cudaMemcpyDeviceToDevice, st));
             VC_CUDA(cudaMemcpyAsync(b->pi, b->pi2, 4 * T, cudaMemcpyDeviceToDevice, st));
             VC_CUDA(cudaStreamSynchronize(st));
-            count_launches((int)(corr_iters / 2 * kCorrBodyKernels));
             if (herr) return fail(VC_ERR_CUDA, "internal: batched refinement policy infeasible");
             all_cert = true;
             for (size_t i = 0; i < N; i++) {

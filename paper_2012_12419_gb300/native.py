@@ -439,17 +439,20 @@ class Batch:
         return int(self.offsets[-1])
 
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
-                      stream=None, raise_on_nonconvergence=True, accurate: bool = False):
+                      stream=None, raise_on_nonconvergence=True, accurate: bool = False,
+                      plain_correction: bool = False):
         """Returns (V fp32 [total], V64 [total] or None, pi [total] or None, list of per-instance dicts, status).
 
-        accurate=True certifies every instance's error: max|V64_i - V*_i| <= tol / 2."""
+        accurate=True certifies every instance's error: max|V64_i - V*_i| <= tol / 2.
+        plain_correction=True solves the correction equations by fixed-point sweeps."""
         dev = _dev()
         if V is None:
             V = torch.zeros(self.total, dtype=torch.float32, device=dev)
         V64 = torch.empty(self.total, dtype=torch.float64, device=dev)
         pi = torch.empty(self.total, dtype=torch.int32, device=dev)
         st = (BatchStats * self.n)()
-        flags = (VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
+        flags = ((VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
+                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0))
         rc = load().vc_value_iterate_batch(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                            flags, st, _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))

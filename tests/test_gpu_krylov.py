@@ -9,6 +9,8 @@ and against the oracle.
 * The solve is deterministic: two runs give bitwise equal V64 and the same product count.
 * vc_evaluate_policy (BiCGSTAB inside) evaluates a fixed policy of a user CSR to the
   oracle's value iteration of the single-action MDP that keeps only the policy's rows.
+* The batched refinement (BiCGSTAB for every instance in one graph) against its fixed-point
+  sweeps and the oracle.
 """
 import numpy as np
 import pytest
@@ -100,3 +102,35 @@ def test_user_csr_stored_rows_and_policy_evaluation():
     assert n > 0
     assert np.max(np.abs(Vp.cpu().numpy() - Vpol) / np.maximum(np.abs(Vpol), 1.0)) <= 1e-9
     m.close()
+
+
+def test_batched_bicgstab_against_sweeps_and_oracle():
+    """Batched refinement: BiCGSTAB for every instance (one graph) against the fixed-point
+    sweeps, on small uneven instances with gamma in {0.9, 0.95, 0.99}: both certified in
+    accuracy mode and within tol/2 of the oracle's optimum; BiCGSTAB spends fewer products
+    on the gamma = 0.99 instances; two BiCGSTAB runs are bitwise equal."""
+    native = native_or_skip()
+    ps = [p for p in inputs.batch_params(512, seed=2) if inputs.num_states(p["H"], p["C"], p["Q"]) <= 4000][:18]
+    assert {p["gamma"] for p in ps} == {0.9, 0.95, 0.99}
+    b = native.Batch(ps)
+    res = {}
+    for plain in (False, True):
+        V, V64, pi, stats, rc = b.value_iterate(tol=1e-6, accurate=True, plain_correction=plain)
+        assert rc == native.VC_OK
+        assert all(s["certified"] == 1 for s in stats)
+        res[plain] = (V64.cpu().numpy(), pi.cpu().numpy(), stats)
+    off = b.offsets
+    prods = {False: 0, True: 0}
+    for i, p in enumerate(ps):
+        sl = slice(off[i], off[i + 1])
+        Vs, pis, gaps, _ = oracle.solve(p, tol=1e-12)
+        for plain in (False, True):
+            V64, pi, stats = res[plain]
+            assert np.max(np.abs(V64[sl] - Vs)) <= 5e-7 + 1e-9
+            assert policy_mismatches(pi[sl], pis, gaps)[0] == 0
+            if p["gamma"] == 0.99:
+                prods[plain] += stats[i]["correction_sweeps"]
+    assert prods[False] < prods[True]
+    _, V64b, pib, _, _ = b.value_iterate(tol=1e-6, accurate=True)
+    assert np.array_equal(V64b.cpu().numpy(), res[False][0]) and np.array_equal(pib.cpu().numpy(), res[False][1])
+    b.close()
