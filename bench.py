@@ -537,7 +537,7 @@ def comparisons(args, native, torch, dev, stream):
     out["grad_adjoint_ms"] = t_adj
     out["grad_adjoint_over_forward"] = t_adj / t_fwd
     out["grad_adjoint_tol1e-11_ms"] = t_adj11
-    out["grad_adjoint_sweeps"] = int(gs["sweeps"])
+    out["grad_adjoint_products"] = int(gs["sweeps"]) + int(gs["correction_sweeps"])
     out["grad_forward_sweeps"] = int(st["sweeps"])
     out["grad_nnz_transpose"] = int(gs["nnz_transpose"])
     out["grad_max_abs_dJ_tol1e-6_minus_tol1e-11"] = float((dJ - dJ11).abs().max())

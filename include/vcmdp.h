@@ -306,8 +306,8 @@ int64_t vc_autotune_report(const vc_mdp* m, char* buf, int64_t len);
 
 /* Statistics of vc_value_grad (host struct). */
 typedef struct vc_grad_stats {
-    int64_t sweeps;          /* FP32 adjoint sweeps (first solve) */
-    int64_t correction_sweeps; /* FP32 correction sweeps of the FP64 refinement */
+    int64_t sweeps;          /* FP32 products by P_pi^T in the first solve */
+    int64_t correction_sweeps; /* FP32 products by P_pi^T in the FP64 refinement's corrections */
     int32_t rounds;          /* refinement rounds */
     int32_t reserved;
     double residual64;       /* FP64 max|rho + gamma P_pi^T lam - lam| of the returned lam */
@@ -324,8 +324,9 @@ typedef struct vc_grad_stats {
  * optimum when pi is optimal: then this is the derivative of the optimal J wherever the
  * optimal action is unique), pi its
  * policy ([S] int32, feasible everywhere, else VC_ERR_ARG), rho [S] double weights.
- * lam is solved with pull sweeps over an explicit transpose P_pi^T (FP32, then FP64
- * residual + FP32 correction rounds until the FP64 residual is below tol).
+ * lam is solved with products by an explicit transpose P_pi^T (one pull over its rows):
+ * an FP32 BiCGSTAB solve (fixed-point sweeps lam <- rho + gamma P^T lam if it breaks
+ * down), then FP64 residual + FP32 correction rounds until the FP64 residual is below tol.
  * dJ_dtheta: [2H+5] double on the device; lambda_out: [S] double (nullable).  Temporary
  * device memory for P_pi^T is stream-ordered (cudaMallocAsync) and released before
  * return.  Synchronises `stream`.  VC_ERR_ARG for a handle built from an explicit CSR.

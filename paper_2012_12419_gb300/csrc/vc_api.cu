@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 static void free_mdp(Mdp* m) {
     if (!m) return;
-    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->Vb, m->U32, m->U64, m->V64a,
+    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->rate_tab, m->Vb, m->U32, m->U64, m->V64a,
                     m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->kr, m->kr_part, m->kctl, m->ctl,
                     m->sell_rec, m->sell_slab};
     for (void* p : ptrs)
@@ -237,6 +237,7 @@ int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
     m->num_sms = device_sms();
     cudaStream_t st = (cudaStream_t)stream;
     int rc = build_model(p, m);
+    if (!rc) rc = upload_rate_table(m, st);
     if (!rc && base != VC_IMPLICIT) rc = build_csr_from_model(m, st);
     if (!rc && base == VC_IMPLICIT) rc = count_model_rows(m, st);  // logical nnz, nothing stored
     if (!rc) rc = alloc_work(m);
@@ -432,13 +433,35 @@ int vc_value_grad(vc_mdp* mh, const double* V, const int32_t* pi, const double* 
     T.ctl = m->ctl;
     T.ctl_host = m->ctl_host;
     T.num_sms = m->num_sms;
+    T.kr = m->kr;  // BiCGSTAB work space of the handle
+    T.kr_part = m->kr_part;
+    T.kctl = m->kctl;
+    T.kctl_host = m->kctl_host;
     auto sweep_T = [&](const float* in, float* o, SweepCtl sc) { return csr_sweep32(&T, in, o, nullptr, nullptr, sc, st); };
-    VC_TRY(cudaMemsetAsync(m->E0, 0, 4 * (size_t)S, st));
-    int fin = 0;
-    if ((rc = loop32(m, m->E0, m->E1, tol, max_sweeps, st, &fin, sweep_T))) return bail(rc);
-    gs.sweeps = m->ctl_host->sweeps;
+    // (I - gamma P_pi^T) x = b in FP32: BiCGSTAB, or fixed-point sweeps x <- b + gamma P^T x
+    // from x = 0 (T.R = b) when it breaks down; *xo receives the buffer holding x
+    auto solve_T = [&](float* b, double target, float** xo, long long* prods) -> int {
+        bool conv = false;
+        int r = krylov_correct(&T, nullptr, b, m->E0, target, std::min<long long>(kKrylovMaxIter, max_sweeps), st,
+                               prods, &conv);
+        if (r || conv) {
+            *xo = m->E0;
+            return r;
+        }
+        T.R = b;
+        VC_CUDA(cudaMemsetAsync(m->E0, 0, 4 * (size_t)S, st));
+        int fin = 0;
+        if ((r = loop32(m, m->E0, m->E1, target, max_sweeps, st, &fin, sweep_T))) return r;
+        *prods += m->ctl_host->sweeps;
+        *xo = fin == 1 ? m->E1 : m->E0;
+        return VC_OK;
+    };
+    float* lamF = nullptr;
+    long long prods = 0;
+    if ((rc = solve_T(rhoF, tol, &lamF, &prods))) return bail(rc);
+    gs.sweeps = prods;
     double* lam = m->V64b;
-    if ((rc = launch_f32_to_f64(fin == 1 ? m->E1 : m->E0, lam, S, st))) return bail(rc);
+    if ((rc = launch_f32_to_f64(lamF, lam, S, st))) return bail(rc);
 
     // ---- FP64 residual + FP32 correction rounds
     bool ok = false;
@@ -456,11 +479,12 @@ int vc_value_grad(vc_mdp* mh, const double* V, const int32_t* pi, const double* 
             break;
         }
         gs.rounds++;
-        T.R = m->Rres;  // correction e = r + gamma P^T e
-        VC_TRY(cudaMemsetAsync(m->E0, 0, 4 * (size_t)S, st));
-        if ((rc = loop32(m, m->E0, m->E1, 0.5 * tol, max_sweeps, st, &fin, sweep_T))) return bail(rc);
-        gs.correction_sweeps += m->ctl_host->sweeps;
-        if ((rc = launch_axpy64(lam, fin == 1 ? m->E1 : m->E0, S, st))) return bail(rc);
+        // correction (I - gamma P^T) e = r
+        float* e = nullptr;
+        long long cp = 0;
+        if ((rc = solve_T(m->Rres, 0.5 * tol, &e, &cp))) return bail(rc);
+        gs.correction_sweeps += cp;
+        if ((rc = launch_axpy64(lam, e, S, st))) return bail(rc);
     }
 
     // ---- contraction over states, reduced in a fixed order

@@ -74,6 +74,12 @@ int build_model(const vc_params* p, Mdp* m) {
     r.w_occ = p->w_occ;
     r.w_loss = p->w_loss;
     r.w_q = p->w_q;
+    for (int k = 0; k < kMaxH; k++) r.pdep[k] = r.delta[k] / r.Lam;
+    r.parr = r.lambda / r.Lam;
+    r.pflip[0] = r.f / r.Lam;
+    r.pflip[1] = (1.0 - r.f) / r.Lam;
+    r.occ_tab = nullptr;  // upload_rate_table
+    r.tab_c1 = C + 1;
 
     Coef<double>& c = m->c64;
     c.gamma = p->gamma;
@@ -124,6 +130,25 @@ __device__ __forceinline__ uint16_t bf16_rne_from_double(double x) {
 __device__ __forceinline__ double bf16_to_double(uint16_t b) { return (double)__uint_as_float((uint32_t)b << 16); }
 
 // ------------------------------------------------------------------------- build kernels
+// The per-occupancy probabilities mu_k o / Lam and delta_k o / Lam of every host, formed
+// on the host (the same FP64 operations as the device formula) and placed in device
+// memory, so the row kernels read them instead of dividing in FP64.
+int upload_rate_table(Mdp* m, cudaStream_t st) {
+    const int c1 = m->rates.tab_c1;
+    std::vector<double> tab((size_t)2 * kMaxH * c1, 0.0);
+    for (int k = 0; k < kMaxH; k++)
+        for (int o = 0; o < c1; o++) {
+            tab[(size_t)k * c1 + o] = m->rates.mu[k] * (double)o / m->rates.Lam;
+            tab[(size_t)(kMaxH + k) * c1 + o] = m->rates.delta[k] * (double)o / m->rates.Lam;
+        }
+    int rc;
+    if ((rc = alloc_dev(m, (void**)&m->rate_tab, sizeof(double) * tab.size()))) return rc;
+    VC_CUDA(cudaMemcpyAsync(m->rate_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaStreamSynchronize(st));  // tab is pageable host memory
+    m->rates.occ_tab = m->rate_tab;
+    return VC_OK;
+}
+
 __global__ void k_row_count(Model md, Rates rt, int64_t nrows, int32_t* cnt, unsigned long long* tallies) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long feas = 0, nz = 0;

@@ -489,7 +489,8 @@ __global__ void __launch_bounds__(kThreads) k_csr_correct32(CsrArgs a, const int
     finish_block<float>(sc, res, vabs, sweep);
 }
 
-// Product by the correction matrix for the BiCGSTAB solve from the stored rows of pi:
+// Product by the correction matrix for the BiCGSTAB solve from the stored rows of pi
+// (pi = nullptr: action 0, the one row of a single-action system such as the adjoint's):
 // y(s) = x(s) - gamma (scale) sum_j val_j x[col_j], with the stage's partial sums.
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) k_csr_apply32(CsrArgs a, const int32_t* __restrict__ pi,
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) k_csr_apply32(CsrArgs a, const int32
     const VT* val = reinterpret_cast<const VT*>(a.val);
     float d0 = 0.0f, d1 = 0.0f;
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
-        const int act = pi[s];
+        const int act = pi ? pi[s] : 0;
         float yv = xin[s];
         if (act >= 0 && act < a.A) {
             const int64_t r = (int64_t)s * a.A + act;

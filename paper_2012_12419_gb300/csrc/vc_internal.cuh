@@ -89,6 +89,13 @@ struct Rates {
     double mu[kMaxH], delta[kMaxH];
     double lambda, f, Lam;
     double w_occ, w_loss, w_q;
+    // probabilities formed once on the host with the same FP64 operations the rows use
+    // (IEEE division and multiplication are correctly rounded, so the values are equal):
+    double pdep[kMaxH];      // delta_k / Lam
+    double parr;             // lambda / Lam
+    double pflip[2];         // f / Lam, (1 - f) / Lam
+    const double* occ_tab;   // device [2][kMaxH][C+1]: mu_k o / Lam, delta_k o / Lam (or null)
+    int tab_c1;              // C + 1
 };
 
 // Digits of a state code.
@@ -163,11 +170,11 @@ __device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s
     double total = 0.0, self_extra = 0.0, occ_sum = 0.0, lost = 0.0;
     for (int k = 0; k < md.H; k++) {
         const int o = d.occ[k];
-        const double pcomp = rt.mu[k] * o / Lam;
-        const double pdep = rt.delta[k] / Lam;
+        const double pcomp = rt.occ_tab ? __ldg(rt.occ_tab + (size_t)k * rt.tab_c1 + o) : rt.mu[k] * o / Lam;
+        const double pdep = rt.pdep[k];
         total += pcomp + pdep;
         occ_sum += o;
-        lost += rt.delta[k] * o / Lam;
+        lost += rt.occ_tab ? __ldg(rt.occ_tab + (size_t)(kMaxH + k) * rt.tab_c1 + o) : rt.delta[k] * o / Lam;
         if (o == 0) {
             self_extra += pdep;  // departure of an empty host changes nothing
         } else if (o == 1) {
@@ -180,7 +187,7 @@ __device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s
             probs[n++] = pdep;
         }
     }
-    const double parr = rt.lambda / Lam;
+    const double parr = rt.parr;
     total += parr;
     if (d.q < md.Q) {
         cols[n] = x + 2;
@@ -189,7 +196,7 @@ __device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s
         self_extra += parr;  // blocked arrival
         lost += parr;
     }
-    const double pflip = (d.ph ? 1.0 - rt.f : rt.f) / Lam;
+    const double pflip = rt.pflip[d.ph];
     total += pflip;
     cols[n] = d.ph ? x - 1 : x + 1;
     probs[n++] = pflip;
@@ -422,6 +429,7 @@ struct Mdp {
     void* val = nullptr;        // float or uint16 (bf16)
     float* scale = nullptr;     // BF16 per-row scale
     float* R = nullptr;         // [S*A], -inf = infeasible
+    double* rate_tab = nullptr; // rates.occ_tab (device, owned)
     CsrPlan plan;
     std::string tune_report;    // candidates and times of the last autotune
     // sliced copy of the stored matrix (SELL-C-sigma, C = 32 states per slice): one
@@ -468,6 +476,7 @@ struct NvtxRange {
 // Kernels / launchers implemented in the .cu files.
 int alloc_dev(Mdp* m, void** p, size_t bytes);
 int build_model(const vc_params* p, Mdp* m);
+int upload_rate_table(Mdp* m, cudaStream_t st);
 int build_csr_from_model(Mdp* m, cudaStream_t st);
 int count_model_rows(Mdp* m, cudaStream_t st);
 int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
