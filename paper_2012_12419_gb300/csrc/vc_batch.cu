@@ -258,16 +258,18 @@ __global__ void k_bcond(cudaGraphConditionalHandle h, BatchCtl c, int sweeps_per
     cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
-// Policy residual in FP64: r = R(x_pi) + gamma E[V64(next) | x_pi] - V64 (as float).
+// Policy residual in FP64: r = U64(x_pi) - V64 (as float), U64 from the FP64 pass-1
+// kernel over every post-decision state (one gather per state here).
 template <int MH>
 __global__ void k_bresid64(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
-                           const int32_t* __restrict__ pi, const double* __restrict__ V, float* __restrict__ r,
-                           int* err) {
+                           const int32_t* __restrict__ pi, const double* __restrict__ U, const double* __restrict__ V,
+                           float* __restrict__ r, int* err) {
     __shared__ InstDesc sd;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
         load_desc(descs, tl.inst, sd);
         __syncthreads();
+        const double* Ui = U + sd.off;
         const double* Vi = V + sd.off;
         for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
             const int s = tl.start + j;
@@ -279,7 +281,7 @@ __global__ void k_bresid64(const InstDesc* __restrict__ descs, const BatchTile* 
                 r[sd.off + s] = 0.0f;
                 continue;
             }
-            r[sd.off + s] = (float)(b_reward<MH>(sd.md, sd.c64, d) + sd.c64.gamma * b_expect<MH>(sd.md, sd.c64, Vi, x, d) - Vi[s]);
+            r[sd.off + s] = (float)(Ui[x] - Vi[s]);
         }
         __syncthreads();
     }
@@ -875,7 +877,9 @@ static void enqueue_cert(Batch* b, cudaStream_t st) {
 
 template <int MH>
 static void enqueue_resid(Batch* b, cudaStream_t st) {
-    k_bresid64<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, b->V64, b->Rr, b->err);
+    k_bpost<MH, double><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64, b->U64);
+    k_bresid64<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, b->U64, b->V64, b->Rr,
+                                                 b->err);
 }
 
 template <typename F>
@@ -1053,7 +1057,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
         const bool plain = (flags & VC_ITER_PLAIN_CORRECTION) != 0;
         for (int round = 0; round < 20; round++) {
             VC_CUDA(cudaMemsetAsync(b->err, 0, 4, st));
-            count_launches(1);
+            count_launches(2);
             by_mh(b->mh, [&](auto m) { enqueue_resid<decltype(m)::value>(b, st); });
             int herr = 0;
             VC_CUDA(cudaMemcpyAsync(&herr, b->err, 4, cudaMemcpyDeviceToHost, st));

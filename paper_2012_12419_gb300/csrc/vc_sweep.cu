@@ -165,12 +165,14 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
 }
 
 // ------------------------------------------------ implicit: mixed-precision refinement
-// Policy residual in FP64: r(s) = R(x_pi) + gamma E[V64(next) | x_pi] - V64(s), stored as
-// float (it is small once V64 is near V_pi, so FP32 keeps ~1e-7 of it).
+// Policy residual in FP64, r(s) = U64(x_pi(s)) - V64(s) with U64 = R + gamma E[V64(next) | x]
+// from the FP64 pass-1 kernel over every post-decision state (coalesced: thread x gathers
+// around x), so this kernel makes one gather per state.  r is stored as float (it is small
+// once V64 is near V_pi, so FP32 keeps ~1e-7 of it).
 template <int MH>
-__global__ void __launch_bounds__(kThreads) k_resid64(Model md, Coef<double> c, const int32_t* __restrict__ pi,
-                                                      const double* __restrict__ V, float* __restrict__ r,
-                                                      SweepCtl sc) {
+__global__ void __launch_bounds__(kThreads) k_resid64(Model md, const int32_t* __restrict__ pi,
+                                                      const double* __restrict__ U, const double* __restrict__ V,
+                                                      float* __restrict__ r, SweepCtl sc) {
     double mx = 0.0;
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < md.S; s += gridDim.x * kThreads) {
         Digits d;
@@ -182,9 +184,9 @@ __global__ void __launch_bounds__(kThreads) k_resid64(Model md, Coef<double> c, 
             continue;
         }
 #ifdef VC_DEBUG_BOUNDS
-        if (!successors_in_range<MH>(md, x, d, sc.ctl)) continue;
+        if (!VC_IN_BOUNDS(sc.ctl, x >= 0 && x < md.S)) continue;
 #endif
-        const double rd = post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V, x, d) - V[s];
+        const double rd = U[x] - V[s];
         r[s] = (float)rd;
         mx = fmax(mx, fabs(rd));
     }
@@ -308,9 +310,14 @@ int launch_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, dou
 
 int launch_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl sc, cudaStream_t st) {
     if (!m->has_model) return csr_resid64(m, pi, V64, r, sc, st);
-    count_launches(1);
+    const int g = state_grid(m);
+    SweepCtl none = sc;
+    none.mode = kModeNone;
+    count_launches(2);
     by_h(m, [&](auto mh) {
-        k_resid64<decltype(mh)::value><<<state_grid(m), kThreads, 0, st>>>(m->md, m->c64, pi, V64, r, sc);
+        constexpr int MH = decltype(mh)::value;
+        k_post<MH, double><<<g, kThreads, 0, st>>>(m->md, m->c64, V64, m->U64, none);
+        k_resid64<MH><<<g, kThreads, 0, st>>>(m->md, pi, m->U64, V64, r, sc);
         return 0;
     });
     VC_CUDA(cudaGetLastError());
