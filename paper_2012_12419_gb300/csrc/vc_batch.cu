@@ -600,6 +600,23 @@ __global__ void k_f32_to_f64_n(const float* __restrict__ in, double* __restrict_
         out[i] = (double)in[i];
 }
 
+// Calls f with std::integral_constant<int, MH>: MH = the batch's largest H when it is at
+// most 8 (per-host loops unrolled to exactly that bound), else 16.
+template <typename F>
+static void by_mh(int mh, F&& f) {
+    switch (mh) {
+        case 1: f(std::integral_constant<int, 1>()); break;
+        case 2: f(std::integral_constant<int, 2>()); break;
+        case 3: f(std::integral_constant<int, 3>()); break;
+        case 4: f(std::integral_constant<int, 4>()); break;
+        case 5: f(std::integral_constant<int, 5>()); break;
+        case 6: f(std::integral_constant<int, 6>()); break;
+        case 7: f(std::integral_constant<int, 7>()); break;
+        case 8: f(std::integral_constant<int, 8>()); break;
+        default: f(std::integral_constant<int, 16>()); break;
+    }
+}
+
 // ------------------------------------------------------------------------ batch handle
 struct Batch {
     int n = 0;
@@ -807,28 +824,13 @@ static int make_loop_graph(cudaGraph_t* g, cudaGraphExec_t* x, Body&& body) {
 static int build_graphs(Batch* b) {
     int rc;
     auto vi = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
-        if (b->mh == 4)
-            enqueue_vi_body<4>(b, cs, h);
-        else if (b->mh == 8)
-            enqueue_vi_body<8>(b, cs, h);
-        else
-            enqueue_vi_body<16>(b, cs, h);
+        by_mh(b->mh, [&](auto m) { enqueue_vi_body<decltype(m)::value>(b, cs, h); });
     };
     auto corr = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
-        if (b->mh == 4)
-            enqueue_corr_body<4>(b, cs, h);
-        else if (b->mh == 8)
-            enqueue_corr_body<8>(b, cs, h);
-        else
-            enqueue_corr_body<16>(b, cs, h);
+        by_mh(b->mh, [&](auto m) { enqueue_corr_body<decltype(m)::value>(b, cs, h); });
     };
     auto kry = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
-        if (b->mh == 4)
-            enqueue_kry_body<4>(b, cs, h);
-        else if (b->mh == 8)
-            enqueue_kry_body<8>(b, cs, h);
-        else
-            enqueue_kry_body<16>(b, cs, h);
+        by_mh(b->mh, [&](auto m) { enqueue_kry_body<decltype(m)::value>(b, cs, h); });
     };
     if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, vi))) return rc;
     if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, corr))) return rc;
@@ -882,15 +884,6 @@ static void enqueue_resid(Batch* b, cudaStream_t st) {
                                                  b->err);
 }
 
-template <typename F>
-static void by_mh(int mh, F&& f) {
-    if (mh == 4)
-        f(std::integral_constant<int, 4>());
-    else if (mh == 8)
-        f(std::integral_constant<int, 8>());
-    else
-        f(std::integral_constant<int, 16>());
-}
 
 }  // namespace vc
 
@@ -932,7 +925,7 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
         delete b;
         return rc;
     }
-    b->mh = maxH <= 4 ? 4 : (maxH <= 8 ? 8 : 16);
+    b->mh = maxH <= 8 ? maxH : 16;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);

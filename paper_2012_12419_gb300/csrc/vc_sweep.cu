@@ -13,8 +13,8 @@
 // per block, order independent) and, in loop mode, the termination test of the last
 // block (finish_block), so the host never reads the residual per sweep.  All grids are
 // persistent (a few blocks per SM, grid-stride over states) to keep the per-sweep atomics
-// on the control block few.  Kernels are instantiated for H <= 4, 8 and 16 (MH) so the
-// per-host loops do not issue dead iterations.
+// on the control block few.  Kernels are instantiated for every H <= 8 and for H <= 16
+// (MH) so the per-host loops issue no dead iterations up to 8 hosts.
 #include <math.h>
 
 #include <type_traits>
@@ -266,12 +266,21 @@ __global__ void k_f32_to_f64(const float* __restrict__ in, double* __restrict__ 
 // ------------------------------------------------------------------------ dispatch
 static inline bool implicit_sweeps(const Mdp* m) { return (m->fmt & 0xF) == VC_IMPLICIT; }
 
-// Calls f.template operator()<MH>() with the smallest instantiated bound >= H.
+// Calls f with std::integral_constant<int, MH>: MH = H for H <= 8 (the per-host loops are
+// unrolled to MH, so an exact bound issues no predicated-off iterations), else 16.
 template <typename F>
 static int by_h(const Mdp* m, F&& f) {
-    if (m->md.H <= 4) return f(std::integral_constant<int, 4>());
-    if (m->md.H <= 8) return f(std::integral_constant<int, 8>());
-    return f(std::integral_constant<int, 16>());
+    switch (m->md.H) {
+        case 1: return f(std::integral_constant<int, 1>());
+        case 2: return f(std::integral_constant<int, 2>());
+        case 3: return f(std::integral_constant<int, 3>());
+        case 4: return f(std::integral_constant<int, 4>());
+        case 5: return f(std::integral_constant<int, 5>());
+        case 6: return f(std::integral_constant<int, 6>());
+        case 7: return f(std::integral_constant<int, 7>());
+        case 8: return f(std::integral_constant<int, 8>());
+        default: return f(std::integral_constant<int, 16>());
+    }
 }
 
 int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc,
