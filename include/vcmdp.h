@@ -362,7 +362,7 @@ typedef struct vc_batch_stats {
  * Build a batch of n independent instances (p: HOST array of n vc_params, each validated
  * as in vc_build_mdp; implicit form).  Instance i occupies states [off_i, off_i + S_i) of
  * the concatenated arrays, off from vc_batch_offsets.  The schedule (tile size, persistent
- * grid) starts at 2048 states per tile and 8 blocks per SM; vc_batch_autotune picks one by
+ * grid) starts at 4096 states per tile and 8 blocks per SM; vc_batch_autotune picks one by
  * timing.  Two CUDA graphs are captured once per schedule: the FP32 value-iteration loop
  * and the refinement's correction loop, each a device-side WHILE loop.  Algorithm 3 for
  * every instance, applied to many cells of a vehicular cloud at once (the paper's BSDI
@@ -393,7 +393,7 @@ int vc_value_iterate_batch(vc_batch* b, float* V, double* V64_out, int32_t* pi_o
 
 /*
  * Autotuner of the batched schedule: times the FP32 loop graph for `sweeps` sweeps of every
- * (tile size in {256, 512, 1024, 2048}, blocks per SM in {2, 4, 8}) and keeps the fastest,
+ * (tile size in {256, 512, ..., 8192}, blocks per SM in {2, 4, 8}) and keeps the fastest,
  * recapturing the graphs.  *best_ms (host, nullable) receives its time.  Results do not
  * depend on the schedule.
  */
