@@ -291,3 +291,28 @@ def test_pipelined_csr_sweep_equals_direct_sweep(fmt, padded):
     mt.bellman32(V, Vo)
     torch.cuda.synchronize()
     assert torch.equal(Vo, outs[0][0])
+
+
+@pytest.mark.parametrize("H", [9, 12])
+def test_more_than_eight_hosts(H):
+    """Instances with H > 8 run the kernels instantiated for 16 hosts (every H <= 8 has its
+    own instantiation): implicit, CSR and sliced handles and a batch mixing H = 3 and H
+    agree with the oracle's optimum within 1e-6 relative."""
+    native = native_or_skip()
+    p = inputs.make_params(H, 1, 1, 0.9, seed=11)
+    Vs, pis, gaps, _ = oracle.solve(p, tol=1e-12)
+    for kw in (dict(fmt="implicit"), dict(fmt="csr_f32"), dict(fmt="csr_f32", sliced=True)):
+        m = native.MDP.build(p, **kw)
+        _, V64, pi, st = m.value_iterate(tol=1e-6)
+        assert st["certified"] == 1, kw
+        assert rel_err(V64.cpu().numpy(), Vs) <= 1e-6, kw
+        assert policy_mismatches(pi.cpu().numpy(), pis, gaps)[0] == 0, kw
+        m.close()
+    q = inputs.make_params(3, 2, 3, 0.95, seed=4)
+    b = native.Batch([q, p])
+    _, V64, pi, stats, rc = b.value_iterate(tol=1e-6)
+    assert rc == native.VC_OK and all(s["certified"] == 1 for s in stats)
+    off = b.offsets
+    assert rel_err(V64.cpu().numpy()[off[1]:off[2]], Vs) <= 1e-6
+    assert rel_err(V64.cpu().numpy()[off[0]:off[1]], oracle.solve(q, tol=1e-12)[0]) <= 1e-6
+    b.close()
