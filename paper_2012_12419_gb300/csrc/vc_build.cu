@@ -174,12 +174,11 @@ __global__ void k_row_count(Model md, Rates rt, int64_t nrows, int32_t* cnt, uns
     }
 }
 
+// One row of the CSR fill; returns the row's non-zero successors (-1: infeasible).
 template <bool kBf16>
-__global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const int64_t* __restrict__ row_ptr,
-                           int32_t* __restrict__ col, void* __restrict__ val, float* __restrict__ scale,
-                           float* __restrict__ R) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
+__device__ __forceinline__ int fill_row(const Model& md, const Rates& rt, int64_t r, int padded,
+                                        const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                                        void* __restrict__ val, float* __restrict__ scale, float* __restrict__ R) {
     const int s = (int)(r / md.A), a = (int)(r % md.A);
     int cols[kMaxRow];
     double probs[kMaxRow], Rv;
@@ -198,7 +197,7 @@ __global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const 
                     ((float*)val)[base + j] = 0.0f;
             }
         }
-        return;
+        return -1;
     }
     R[r] = (float)Rv;
     double tot = 0.0;
@@ -221,6 +220,33 @@ __global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const 
             else
                 ((float*)val)[base + j] = 0.0f;
         }
+    }
+    return n;
+}
+
+// Fills every row; with tallies (padded rows, where no count pass precedes the fill) it
+// also adds up the feasible rows and their non-zero successors.
+template <bool kBf16>
+__global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const int64_t* __restrict__ row_ptr,
+                           int32_t* __restrict__ col, void* __restrict__ val, float* __restrict__ scale,
+                           float* __restrict__ R, unsigned long long* tallies) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long feas = 0, nz = 0;
+    if (r < nrows) {
+        const int n = fill_row<kBf16>(md, rt, r, padded, row_ptr, col, val, scale, R);
+        if (n >= 0) {
+            feas = 1;
+            nz = (unsigned long long)n;
+        }
+    }
+    if (!tallies) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        feas += __shfl_xor_sync(0xffffffffu, feas, o);
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&tallies[0], feas);
+        atomicAdd(&tallies[1], nz);
     }
 }
 
@@ -347,20 +373,23 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     const unsigned nb = (unsigned)((nrows + T - 1) / T);
     int rc;
 
-    // counts (always: they give the logical nnz and the feasible-row tally)
+    // counts: canonical rows need them for the offsets (and give the logical nnz and the
+    // feasible-row tally); padded rows have fixed offsets, so the fill tallies instead
     int32_t* cnt = nullptr;
     unsigned long long* tallies = nullptr;
-    VC_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * nrows, st));
+    unsigned long long th[2] = {0, 0};
     VC_CUDA(cudaMallocAsync((void**)&tallies, sizeof(unsigned long long) * 2, st));
     VC_CUDA(cudaMemsetAsync(tallies, 0, sizeof(unsigned long long) * 2, st));
-    count_launches(1);
-    k_row_count<<<nb, T, 0, st>>>(m->md, m->rates, nrows, cnt, tallies);
-    VC_CUDA(cudaGetLastError());
-    unsigned long long th[2];
-    VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
-    VC_CUDA(cudaStreamSynchronize(st));
-    m->feasible_rows = (int64_t)th[0];
-    m->nnz_logical = (int64_t)th[1];
+    if (!padded) {
+        VC_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * nrows, st));
+        count_launches(1);
+        k_row_count<<<nb, T, 0, st>>>(m->md, m->rates, nrows, cnt, tallies);
+        VC_CUDA(cudaGetLastError());
+        VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
+        VC_CUDA(cudaStreamSynchronize(st));
+        m->feasible_rows = (int64_t)th[0];
+        m->nnz_logical = (int64_t)th[1];
+    }
     m->nnz_stored = padded ? nrows * width : m->nnz_logical;
 
     if ((rc = alloc_dev(m, (void**)&m->row_ptr, sizeof(int64_t) * (nrows + 3)))) return rc;
@@ -375,15 +404,22 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     } else {
         if ((rc = exclusive_scan(m, cnt, nrows, m->row_ptr, st))) return rc;
     }
+    unsigned long long* fill_tallies = padded ? tallies : nullptr;
     count_launches(1);
     if (bf16)
         k_row_fill<true><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val, m->scale,
-                                          m->R);
+                                          m->R, fill_tallies);
     else
         k_row_fill<false><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val, nullptr,
-                                           m->R);
+                                           m->R, fill_tallies);
     VC_CUDA(cudaGetLastError());
-    VC_CUDA(cudaFreeAsync(cnt, st));
+    if (padded) {
+        VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
+        VC_CUDA(cudaStreamSynchronize(st));
+        m->feasible_rows = (int64_t)th[0];
+        m->nnz_logical = (int64_t)th[1];
+    }
+    if (cnt) VC_CUDA(cudaFreeAsync(cnt, st));
     VC_CUDA(cudaFreeAsync(tallies, st));
     VC_CUDA(cudaStreamSynchronize(st));
     return plan_csr(m, st);

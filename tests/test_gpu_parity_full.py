@@ -73,7 +73,12 @@ def test_logical_nnz_matches_closed_count(name, nnz):
     m.close()
     m2 = native.MDP.build(p, fmt="csr_f32")
     assert m2.info()["nnz_stored"] == nnz
+    feasible = m2.info()["feasible_rows"]
     m2.close()
+    # padded rows: fixed offsets, the fill itself tallies the logical entries
+    m3 = native.MDP.build(p, fmt="csr_f32", padded=True)
+    assert m3.info()["nnz_logical"] == nnz and m3.info()["feasible_rows"] == feasible
+    m3.close()
 
 
 def test_headline_configuration_equals_the_csr_kernel_bitwise():
