@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "vc_internal.cuh"
@@ -149,14 +150,14 @@ int upload_rate_table(Mdp* m, cudaStream_t st) {
     return VC_OK;
 }
 
+template <int MH>
 __global__ void k_row_count(Model md, Rates rt, int64_t nrows, int32_t* cnt, unsigned long long* tallies) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long feas = 0, nz = 0;
     if (r < nrows) {
         const int s = (int)(r / md.A), a = (int)(r % md.A);
-        int cols[kMaxRow];
-        double probs[kMaxRow], R;
-        const int n = model_row(md, rt, s, a, cols, probs, &R);
+        double R;
+        const int n = model_row_emit<MH>(md, rt, s, a, &R, [](int, int, double) {});
         if (cnt) cnt[r] = n < 0 ? 0 : n;
         if (n >= 0) {
             feas = 1;
@@ -174,17 +175,28 @@ __global__ void k_row_count(Model md, Rates rt, int64_t nrows, int32_t* cnt, uns
     }
 }
 
-// One row of the CSR fill; returns the row's non-zero successors (-1: infeasible).
-template <bool kBf16>
+// One row of the CSR fill, written as the row's entries come (ascending columns); returns
+// the row's non-zero successors (-1: infeasible).
+template <int MH, bool kBf16>
 __device__ __forceinline__ int fill_row(const Model& md, const Rates& rt, int64_t r, int padded,
                                         const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
                                         void* __restrict__ val, float* __restrict__ scale, float* __restrict__ R) {
     const int s = (int)(r / md.A), a = (int)(r % md.A);
-    int cols[kMaxRow];
-    double probs[kMaxRow], Rv;
-    const int n = model_row(md, rt, s, a, cols, probs, &Rv);
     const int64_t base = row_ptr[r];
     const int width = 2 * md.H + 3;
+    double Rv, tot = 0.0;
+    int last = s;
+    const int n = model_row_emit<MH>(md, rt, s, a, &Rv, [&](int j, int c, double p) {
+        col[base + j] = c;
+        if (kBf16) {
+            const uint16_t b = bf16_rne_from_double(p);
+            ((uint16_t*)val)[base + j] = b;
+            tot += bf16_to_double(b);
+        } else {
+            ((float*)val)[base + j] = (float)p;
+        }
+        last = c;
+    });
     if (n < 0) {
         R[r] = -INFINITY;
         if (kBf16) scale[r] = 0.0f;
@@ -200,21 +212,10 @@ __device__ __forceinline__ int fill_row(const Model& md, const Rates& rt, int64_
         return -1;
     }
     R[r] = (float)Rv;
-    double tot = 0.0;
-    for (int j = 0; j < n; j++) {
-        col[base + j] = cols[j];
-        if (kBf16) {
-            const uint16_t b = bf16_rne_from_double(probs[j]);
-            ((uint16_t*)val)[base + j] = b;
-            tot += bf16_to_double(b);
-        } else {
-            ((float*)val)[base + j] = (float)probs[j];
-        }
-    }
     if (kBf16) scale[r] = (float)(1.0 / tot);
     if (padded) {
         for (int j = n; j < width; j++) {
-            col[base + j] = cols[n - 1];
+            col[base + j] = last;
             if (kBf16)
                 ((uint16_t*)val)[base + j] = 0;
             else
@@ -226,14 +227,14 @@ __device__ __forceinline__ int fill_row(const Model& md, const Rates& rt, int64_
 
 // Fills every row; with tallies (padded rows, where no count pass precedes the fill) it
 // also adds up the feasible rows and their non-zero successors.
-template <bool kBf16>
+template <int MH, bool kBf16>
 __global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const int64_t* __restrict__ row_ptr,
                            int32_t* __restrict__ col, void* __restrict__ val, float* __restrict__ scale,
                            float* __restrict__ R, unsigned long long* tallies) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long feas = 0, nz = 0;
     if (r < nrows) {
-        const int n = fill_row<kBf16>(md, rt, r, padded, row_ptr, col, val, scale, R);
+        const int n = fill_row<MH, kBf16>(md, rt, r, padded, row_ptr, col, val, scale, R);
         if (n >= 0) {
             feas = 1;
             nz = (unsigned long long)n;
@@ -344,6 +345,22 @@ int exclusive_scan(Mdp* m, const int32_t* cnt, int64_t n, int64_t* out, cudaStre
 }
 
 // Feasible rows and logical successor count of a model without storing anything.
+// Calls f with std::integral_constant<int, MH>: MH = H for H <= 8, else 16.
+template <typename F>
+static void by_h_build(int H, F&& f) {
+    switch (H) {
+        case 1: f(std::integral_constant<int, 1>()); break;
+        case 2: f(std::integral_constant<int, 2>()); break;
+        case 3: f(std::integral_constant<int, 3>()); break;
+        case 4: f(std::integral_constant<int, 4>()); break;
+        case 5: f(std::integral_constant<int, 5>()); break;
+        case 6: f(std::integral_constant<int, 6>()); break;
+        case 7: f(std::integral_constant<int, 7>()); break;
+        case 8: f(std::integral_constant<int, 8>()); break;
+        default: f(std::integral_constant<int, 16>()); break;
+    }
+}
+
 int count_model_rows(Mdp* m, cudaStream_t st) {
     const int64_t nrows = (int64_t)m->S * m->A;
     const int T = 256;
@@ -351,7 +368,10 @@ int count_model_rows(Mdp* m, cudaStream_t st) {
     VC_CUDA(cudaMallocAsync((void**)&tallies, sizeof(unsigned long long) * 2, st));
     VC_CUDA(cudaMemsetAsync(tallies, 0, sizeof(unsigned long long) * 2, st));
     count_launches(1);
-    k_row_count<<<(unsigned)((nrows + T - 1) / T), T, 0, st>>>(m->md, m->rates, nrows, nullptr, tallies);
+    by_h_build(m->md.H, [&](auto mh) {
+        k_row_count<decltype(mh)::value><<<(unsigned)((nrows + T - 1) / T), T, 0, st>>>(m->md, m->rates, nrows,
+                                                                                        nullptr, tallies);
+    });
     VC_CUDA(cudaGetLastError());
     unsigned long long th[2];
     VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
@@ -383,7 +403,9 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     if (!padded) {
         VC_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * nrows, st));
         count_launches(1);
-        k_row_count<<<nb, T, 0, st>>>(m->md, m->rates, nrows, cnt, tallies);
+        by_h_build(m->md.H, [&](auto mh) {
+            k_row_count<decltype(mh)::value><<<nb, T, 0, st>>>(m->md, m->rates, nrows, cnt, tallies);
+        });
         VC_CUDA(cudaGetLastError());
         VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
         VC_CUDA(cudaStreamSynchronize(st));
@@ -406,12 +428,15 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     }
     unsigned long long* fill_tallies = padded ? tallies : nullptr;
     count_launches(1);
-    if (bf16)
-        k_row_fill<true><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val, m->scale,
-                                          m->R, fill_tallies);
-    else
-        k_row_fill<false><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val, nullptr,
-                                           m->R, fill_tallies);
+    by_h_build(m->md.H, [&](auto mh) {
+        constexpr int MH = decltype(mh)::value;
+        if (bf16)
+            k_row_fill<MH, true><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val,
+                                                  m->scale, m->R, fill_tallies);
+        else
+            k_row_fill<MH, false><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val,
+                                                   nullptr, m->R, fill_tallies);
+    });
     VC_CUDA(cudaGetLastError());
     if (padded) {
         VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));

@@ -152,78 +152,81 @@ __device__ __forceinline__ bool apply_action(const Model& md, int s, int a, Digi
 // --------------------------------------------------------- device: one model row (FP64)
 constexpr int kMaxRow = 2 * kMaxH + 3;
 
-// Successors of (s, a), merged and sorted by column, zero probabilities dropped.
-// Returns the count, or -1 if a is infeasible in s.  R receives the expected reward.
-__device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s, int a, int* cols, double* probs, double* R) {
+// Probability of host k's completion event at occupancy o (mu_k o / Lam).
+__device__ __forceinline__ double p_comp(const Rates& rt, int k, int o) {
+    return rt.occ_tab ? __ldg(rt.occ_tab + (size_t)k * rt.tab_c1 + o) : rt.mu[k] * o / rt.Lam;
+}
+
+// Successors of (s, a), merged, zero probabilities dropped, passed to emit(j, column, p)
+// in ascending column order for j = 0, 1, ...: host k's entries x - o_k s_k (departure)
+// and x - s_k (completion) lie above every entry of host k + 1, since o_k s_k <= C s_k <
+// s_{k+1}, and below x - 1, since s_0 = 2(Q + 1) >= 2; then the phase flip (x - 1 or
+// x + 1), the self-loop x and the arrival x + 2.  So no sort is needed.  Returns the count,
+// or -1 if a is infeasible in s; R receives the expected reward.  The probabilities and
+// the reward are summed host 0 first, in one fixed order.
+// MH: a compile-time bound on H (loops unrolled, digits in registers).
+template <int MH = kMaxH, typename Emit>
+__device__ __forceinline__ int model_row_emit(const Model& md, const Rates& rt, int s, int a, double* R, Emit&& emit) {
     Digits d;
-    decode(md, s, d);
+    decode<MH>(md, s, d);
     int x = s;
-    if (a < md.H) {
-        const bool ok = d.q >= 1 && d.occ[a] < md.C && (a == md.H - 1 || d.ph == 1);
-        if (!ok) return -1;
-        d.occ[a] += 1;
-        d.q -= 1;
-        x = s + md.stride[a] - 2;
-    }
-    const double Lam = rt.Lam;
-    int n = 0;
+    if (a < md.H && !apply_action<MH>(md, s, a, d, x)) return -1;
     double total = 0.0, self_extra = 0.0, occ_sum = 0.0, lost = 0.0;
-    for (int k = 0; k < md.H; k++) {
-        const int o = d.occ[k];
-        const double pcomp = rt.occ_tab ? __ldg(rt.occ_tab + (size_t)k * rt.tab_c1 + o) : rt.mu[k] * o / Lam;
-        const double pdep = rt.pdep[k];
-        total += pcomp + pdep;
-        occ_sum += o;
-        lost += rt.occ_tab ? __ldg(rt.occ_tab + (size_t)(kMaxH + k) * rt.tab_c1 + o) : rt.delta[k] * o / Lam;
-        if (o == 0) {
-            self_extra += pdep;  // departure of an empty host changes nothing
-        } else if (o == 1) {
-            cols[n] = x - md.stride[k];  // completion and departure both empty the host
-            probs[n++] = pcomp + pdep;
-        } else {
-            cols[n] = x - md.stride[k];
-            probs[n++] = pcomp;
-            cols[n] = x - o * md.stride[k];
-            probs[n++] = pdep;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            const double pcomp = p_comp(rt, k, o);
+            const double pdep = rt.pdep[k];
+            total += pcomp + pdep;
+            occ_sum += o;
+            lost += rt.occ_tab ? __ldg(rt.occ_tab + (size_t)(kMaxH + k) * rt.tab_c1 + o) : rt.delta[k] * o / rt.Lam;
+            if (o == 0) self_extra += pdep;  // departure of an empty host changes nothing
         }
     }
     const double parr = rt.parr;
     total += parr;
-    if (d.q < md.Q) {
-        cols[n] = x + 2;
-        probs[n++] = parr;
-    } else {
+    if (d.q >= md.Q) {
         self_extra += parr;  // blocked arrival
         lost += parr;
     }
-    const double pflip = rt.pflip[d.ph];
+    const double pflip = d.ph ? rt.pflip[1] : rt.pflip[0];
     total += pflip;
-    cols[n] = d.ph ? x - 1 : x + 1;
-    probs[n++] = pflip;
-    cols[n] = x;
-    probs[n++] = (1.0 - total) + self_extra;
-    // insertion sort by column (at most 2H+3 entries, all columns distinct)
-    for (int i = 1; i < n; i++) {
-        const int c = cols[i];
-        const double v = probs[i];
-        int j = i - 1;
-        while (j >= 0 && cols[j] > c) {
-            cols[j + 1] = cols[j];
-            probs[j + 1] = probs[j];
-            j--;
-        }
-        cols[j + 1] = c;
-        probs[j + 1] = v;
-    }
-    int m = 0;
-    for (int i = 0; i < n; i++) {
-        if (probs[i] != 0.0) {
-            cols[m] = cols[i];
-            probs[m++] = probs[i];
-        }
-    }
+    const double pself = (1.0 - total) + self_extra;
     *R = rt.w_occ * occ_sum + rt.w_q * d.q + rt.w_loss * lost;
-    return m;
+    int n = 0;
+#pragma unroll
+    for (int k = MH - 1; k >= 0; k--) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o == 1) {
+                const double p = p_comp(rt, k, 1) + rt.pdep[k];  // completion and departure both empty the host
+                if (p != 0.0) emit(n++, x - md.stride[k], p);
+            } else if (o > 1) {
+                if (rt.pdep[k] != 0.0) emit(n++, x - o * md.stride[k], rt.pdep[k]);
+                const double pc = p_comp(rt, k, o);
+                if (pc != 0.0) emit(n++, x - md.stride[k], pc);
+            }
+        }
+    }
+    if (d.ph) {
+        if (pflip != 0.0) emit(n++, x - 1, pflip);
+        if (pself != 0.0) emit(n++, x, pself);
+    } else {
+        if (pself != 0.0) emit(n++, x, pself);
+        if (pflip != 0.0) emit(n++, x + 1, pflip);
+    }
+    if (d.q < md.Q && parr != 0.0) emit(n++, x + 2, parr);
+    return n;
+}
+
+// The same row into arrays (cols, probs of at least kMaxRow entries).
+__device__ __forceinline__ int model_row(const Model& md, const Rates& rt, int s, int a, int* cols, double* probs,
+                                         double* R) {
+    return model_row_emit(md, rt, s, a, R, [&](int j, int c, double p) {
+        cols[j] = c;
+        probs[j] = p;
+    });
 }
 
 // --------------------------------------------------------------------------- control
