@@ -134,3 +134,20 @@ def test_batched_bicgstab_against_sweeps_and_oracle():
     _, V64b, pib, _, _ = b.value_iterate(tol=1e-6, accurate=True)
     assert np.array_equal(V64b.cpu().numpy(), res[False][0]) and np.array_equal(pib.cpu().numpy(), res[False][1])
     b.close()
+
+
+def test_product_budget_and_fallback_path():
+    """A product budget too small for BiCGSTAB sends the correction to the fixed-point
+    fallback and then reports VC_ERR_NOT_CONVERGED; the same call with a large budget
+    evaluates the policy to the oracle's values (the handle stays usable)."""
+    native = native_or_skip()
+    p = inputs.make_params(3, 4, 8, 0.99, seed=5)
+    m = native.MDP.build(p, fmt="implicit")
+    pi = m.greedy_policy()
+    with pytest.raises(native.VcError):
+        m.evaluate_policy(pi, tol=1e-10, max_sweeps=10)
+    Vg, n = m.evaluate_policy(pi, tol=1e-10)
+    Vgo = oracle.policy_eval_iter(p, pi.cpu().numpy(), tol=1e-13)
+    assert n > 0
+    assert np.max(np.abs(Vg.cpu().numpy() - Vgo) / np.maximum(np.abs(Vgo), 1.0)) <= 1e-9
+    m.close()
