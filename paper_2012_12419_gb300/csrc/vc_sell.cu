@@ -33,6 +33,10 @@
 // bank conflicts) and the V gathers of a warp fall on a few cache lines because the
 // lanes' successors share offsets.  Q values go to a per-tile shared buffer; the warp
 // that completes a tile's last block takes the max over actions and releases the tile.
+// Sweeps are launched as programmatic dependents of the previous sweep: a CTA that starts
+// while the previous grid drains stages its first tiles (the slab never changes), then
+// waits for that grid (griddepcontrol.wait) before it reads V or the loop's control
+// block; if the loop has ended by then it drains its copies and returns.
 //
 // k_sell (direct): one warp per slice straight from global memory, for comparison and
 // as the fallback when no tile fits in shared memory.
@@ -464,8 +468,10 @@ template <typename VT, int MB>
 __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_sell_ring(SellArgs a, SellRingArgs t,
                                                                                         SweepCtl sc) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (loop_done(sc)) return;
-    const long long sweep = loop_sweep(sc);
+    // the next sweep may be scheduled now: it stages its first tiles (the slab does not
+    // change) and waits for this grid before it reads V or the control block
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    long long sweep = 0;
     const long long lim = wait_limit(sc);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kSlots;
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
     unsigned long long* slot_end = reinterpret_cast<unsigned long long*>(smem + 384);
     float* qbuf = reinterpret_cast<float*>(smem + t.qoff);
     unsigned char* ring = smem + t.roff;
-    __shared__ int s_fail, s_consumed, s_next;
+    __shared__ int s_fail, s_consumed, s_next, s_abort;
     __shared__ long long s_bounds[2][32];
     const int nrw = (int)(blockDim.x >> 5) - 1;  // consumer warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -490,6 +496,7 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
         s_fail = 0;
         s_consumed = 0x7fffffff;
         s_next = 0;
+        s_abort = 0;
     }
     __syncthreads();
     float res = 0.0f, vabs = 0.0f;
@@ -502,6 +509,7 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
         int oldest = 0;                         // oldest tile not yet released
         int i = 0;
         int failed = 0;
+        bool pre = true;  // before the wait for the previous grid (only tiles, no V read)
         for (int64_t c0 = blockIdx.x; c0 < t.ntiles && !failed; c0 += 32LL * gridDim.x) {
             const int64_t tk = c0 + (int64_t)lane * gridDim.x;
             if (tk < t.ntiles) {
@@ -526,6 +534,17 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                         failed = 1;
                         atomicExch(&s_fail, 1);
                         break;
+                    }
+                    // the first time the ring is full: wait for the previous grid, and stop
+                    // if the loop has ended
+                    if (pre && oldest < i && (head + bytes - rel > (unsigned long long)t.ring || i - oldest >= kSlots)) {
+                        pre = false;
+                        asm volatile("griddepcontrol.wait;" ::: "memory");
+                        if (loop_done(sc)) {
+                            atomicExch(&s_abort, 1);
+                            failed = 1;
+                            break;
+                        }
                     }
                     // reuse bytes (and the slot) only after the tiles holding them are released
                     while (oldest < i && (head + bytes - rel > (unsigned long long)t.ring || i - oldest >= kSlots)) {
@@ -553,6 +572,10 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
             failed = __shfl_sync(0xffffffffu, failed, 0);
             __syncwarp();
         }
+        if (lane == 0 && pre) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            if (loop_done(sc)) atomicExch(&s_abort, 1);
+        }
     } else {
         // ---------------- consumers: every warp takes the CTA's next unclaimed block (a
         // shared counter over the blocks of the CTA's tile sequence), so blocks finish
@@ -561,7 +584,10 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
         // multiples, so claimed blocks never run kSlots tiles ahead of the oldest one.
         const int64_t nt_cta = (blockIdx.x < t.ntiles) ? (t.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         int i = 0;
-        while (true) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const bool ended = loop_done(sc);
+        sweep = loop_sweep(sc);
+        while (!ended) {
             int gb = 0;
             if (lane == 0) gb = atomicAdd(&s_next, 1);
             gb = __shfl_sync(0xffffffffu, gb, 0);
@@ -636,15 +662,15 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
         if (lane == 0) atomicMin(&s_consumed, i);
     }
     __syncthreads();
-    if (s_fail) {
+    if (s_fail || s_abort) {
         // drain this CTA's copies still in flight before shared memory is released
         if (warp == nrw && lane == 0) {
             for (int j = (s_consumed < issued ? s_consumed : issued); j < issued; ++j)
                 mbar_wait(&full[j % kSlots], (uint32_t)((j / kSlots) & 1));
-            atomicOr(&sc.ctl->error, kErrTimeout);
+            if (s_fail) atomicOr(&sc.ctl->error, kErrTimeout);
         }
     }
-    if (sc.mode == kModeNone) return;
+    if (s_abort || sc.mode == kModeNone) return;
     res = block_max_dyn(res);
     vabs = block_max_dyn(vabs);
     finish_block<float>(sc, res, vabs, sweep);
@@ -741,15 +767,24 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
         const unsigned grid = (unsigned)(t.ntiles < cap ? t.ntiles : cap);
         const unsigned threads = (unsigned)(m->plan.warps + 1) * 32;
         count_launches(1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = (size_t)m->plan.smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
         if (bf16 && m->plan.minb == 2)
-            k_sell_ring<uint16_t, 2><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<uint16_t, 2>, a, t, sc));
         else if (bf16)
-            k_sell_ring<uint16_t, 1><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<uint16_t, 1>, a, t, sc));
         else if (m->plan.minb == 2)
-            k_sell_ring<float, 2><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
+            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<float, 2>, a, t, sc));
         else
-            k_sell_ring<float, 1><<<grid, threads, m->plan.smem, st>>>(a, t, sc);
-        VC_CUDA(cudaGetLastError());
+            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<float, 1>, a, t, sc));
         return VC_OK;
     }
     const int bps = m->plan.ctas_per_sm > 0 ? m->plan.ctas_per_sm : 4;
