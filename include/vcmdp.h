@@ -272,6 +272,27 @@ int vc_bellman64(vc_mdp* m, const double* V, double* V_out, int32_t* pi, double*
 int vc_greedy_policy(vc_mdp* m, int32_t* pi, void* stream);
 
 /*
+ * The AAA multichannel timer update (Section II, Algorithm 1 with Eqs. 1-9) over a trace of
+ * synchronisation intervals (SIs): the SCHI fraction f it produces is the `f` of
+ * vc_params.  Host routine (no device work, no handle).
+ *   S_v, D_v, R_v: HOST arrays [n_si][n_vehicles], row j = SI j: BSMs each vehicle sent
+ *       and had acknowledged (Eq. 2), the total end-to-end delay in ms of the BSMs it
+ *       received (the numerator of Eq. 3), and how many it received (R_vhBSM).
+ *   si_per_second: SIs per UTC second (10 for the standard's 100 ms SI); si_ms the SI,
+ *       dcchi_ms + dschi_ms = si_ms the IEEE 1609.4 defaults (50 + 50 ms).
+ *   In an SI that is not the last of its second: S_V2V <- (S_V2V + sum_h S_vh)/(1 + N_V),
+ *   D_V2V <- (D_V2V + sum_h D_vh)/(1 + sum_h R_vh).  In the last SI of each second:
+ *   U_CCH = S_V2V D_V2V, I_CCH = CCHI - U_CCH; if U_CCH < DCCHI then CCHI = U_CCH and
+ *   SCHI = SCHI + I_CCH, else both return to the defaults; S_V2V = D_V2V = 0.
+ *   cchi_out, schi_out ([n_si / si_per_second] doubles, host) receive the intervals after
+ *   each second's update; f_out (nullable) SCHI / SI.  CCHI + SCHI stays equal to the SI.
+ * VC_ERR_ARG for NULL arrays, sizes < 1, or defaults that do not sum to the SI.
+ */
+int vc_aaa_intervals(const double* S_v, const double* D_v, const double* R_v, int32_t n_vehicles, int32_t n_si,
+                     int32_t si_per_second, double si_ms, double dcchi_ms, double dschi_ms, double* cchi_out,
+                     double* schi_out, double* f_out);
+
+/*
  * Policy evaluation V_pi = R_pi + gamma P_pi V_pi (Eq. 18 with the action fixed) over the
  * chosen rows only, by mixed-precision iterative refinement: the policy residual
  * r = T_pi V - V and its maximum in FP64, the correction (I - gamma P_pi) e = r solved in

@@ -12,7 +12,8 @@ Two layers:
   evaluation, analytic transition derivatives and a bfloat16 rounding routine.
 * numpy helpers below for tiny problems: dense policy evaluation by a linear solve,
   exhaustive policy enumeration, value iteration on dense random MDPs and the
-  dense-solve adjoint gradient.
+  dense-solve adjoint gradient; and the AAA timer update of Section II (Algorithm 1)
+  in plain Python.
 
 Parity status: every function here is pinned by a CPU test (``tests/test_oracle_*``)
 against hand-derived transition rows, closed forms, brute force, or invariants.
@@ -494,3 +495,54 @@ def adjoint_apply(p: dict, pi, lam) -> np.ndarray:
     if L.or_adjoint_apply(ctypes.byref(_params(p)), _ptr(pi), _ptr(lam), _ptr(out)) != 0:
         raise ValueError("policy infeasible")
     return out
+
+
+# ------------------------------------------------------ AAA multichannel timers (Section II)
+
+
+def aaa_intervals(S_v, D_v, R_v, si_per_second: int = 10, si_ms: float = 100.0, dcchi_ms: float = 50.0,
+                  dschi_ms: float = 50.0):
+    """Algorithm 1 (AAA multi-channel steps) over a trace, step by step in the paper's order.
+
+    S_v[j][h], D_v[j][h], R_v[j][h]: BSMs vehicle h sent and had acknowledged in SI j
+    (Eq. 2), the total end-to-end delay (ms) of the BSMs it received (the numerator of
+    Eq. 3), and how many it received.  Every SI that is not the last of its UTC second
+    updates the running S_V2V and D_V2V (Algorithm 1, the two averaging lines); the last SI
+    of each second computes U_CCH = S_V2V * D_V2V (Eq. 4) and I_CCH = CCHI - U_CCH (Eq. 7),
+    sets CCHI = U_CCH and SCHI = SCHI + I_CCH when U_CCH < DCCHI (else both defaults), and
+    clears S_V2V and D_V2V.  Returns lists (CCHI, SCHI, SCHI / SI), one entry per second.
+    """
+    n_si = len(S_v)
+    cchi, schi = float(dcchi_ms), float(dschi_ms)
+    s_v2v = 0.0
+    d_v2v = 0.0
+    out_c, out_s, out_f = [], [], []
+    for j in range(n_si):
+        n_v = len(S_v[j])
+        utc_second = (j + 1) % si_per_second == 0
+        if not utc_second:
+            sent = 0.0
+            for h in range(n_v):
+                sent += float(S_v[j][h])
+            s_v2v = (s_v2v + sent) / (1 + n_v)
+            delay = 0.0
+            received = 0.0
+            for h in range(n_v):
+                delay += float(D_v[j][h])
+                received += float(R_v[j][h])
+            d_v2v = (d_v2v + delay) / (1 + received)
+        else:
+            u_cch = s_v2v * d_v2v
+            i_cch = cchi - u_cch
+            if u_cch < dcchi_ms:
+                cchi = u_cch
+                schi = schi + i_cch
+            else:
+                cchi = float(dcchi_ms)
+                schi = float(dschi_ms)
+            out_c.append(cchi)
+            out_s.append(schi)
+            out_f.append(schi / si_ms)
+            s_v2v = 0.0
+            d_v2v = 0.0
+    return out_c, out_s, out_f

@@ -131,3 +131,23 @@ def random_csr_mdp(S: int, A: int, max_succ: int, seed: int, infeasible_frac: fl
             row_ptr.append(row_ptr[-1] + n)
     return dict(S=S, A=A, gamma=gamma, row_ptr=np.array(row_ptr, np.int64), col=np.array(cols, np.int32),
                 val=np.array(vals, np.float64), R=R)
+
+
+def aaa_trace(n_vehicles: int, n_seconds: int, seed: int, si_per_second: int = 10):
+    """A synthetic BSM trace for the AAA timer update: per SI (row) and vehicle (column),
+    BSMs sent and acknowledged (one generated per 100 ms SI, each acknowledged with
+    probability 0.9), BSMs received from the other vehicles (delivery ratio U[0.7, 1]), and
+    their total end-to-end delay in ms (per BSM U[0.2, 2] ms scaled by n_vehicles / 10,
+    so denser networks are slower).  Returns three float64 arrays [n_si, n_vehicles]."""
+    rng = SplitMix64(seed)
+    n_si = n_seconds * si_per_second
+    S = np.zeros((n_si, n_vehicles))
+    R = np.zeros((n_si, n_vehicles))
+    D = np.zeros((n_si, n_vehicles))
+    for j in range(n_si):
+        for h in range(n_vehicles):
+            S[j, h] = 1.0 if rng.uniform() < 0.9 else 0.0
+            r = float(int((n_vehicles - 1) * rng.uniform(0.7, 1.0)))
+            R[j, h] = r
+            D[j, h] = r * rng.uniform(0.2, 2.0) * n_vehicles / 10.0
+    return S, D, R

@@ -43,7 +43,7 @@ EXPORTS = [
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
     "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
-    "vc_set_wait_limit",
+    "vc_set_wait_limit", "vc_aaa_intervals",
 ]
 
 
@@ -160,6 +160,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_mdp_slice.argtypes = [vp, vp]
         L.vc_greedy_policy.argtypes = [vp, vp, vp]
         L.vc_set_wait_limit.argtypes = [vp, i64]
+        L.vc_aaa_intervals.argtypes = [vp, vp, vp, i32, i32, i32, dbl, dbl, dbl, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -492,6 +493,28 @@ def bellman32_noalloc(params: dict, V, V_out, pi=None, residual=None, stream=Non
                                        _stream(stream)))
     del keep
     return V_out
+
+
+def aaa_intervals(S_v, D_v, R_v, si_per_second: int = 10, si_ms: float = 100.0, dcchi_ms: float = 50.0,
+                  dschi_ms: float = 50.0):
+    """The AAA timer update (Algorithm 1) over a trace: S_v, D_v, R_v are [n_si, n_vehicles]
+    arrays (BSMs sent and acknowledged, total delay in ms of the BSMs received, BSMs
+    received).  Returns (CCHI, SCHI, f) per UTC second as float64 numpy arrays; f = SCHI/SI
+    is the phase-flip parameter of the placement model.  Host routine of the library."""
+    S = np.ascontiguousarray(S_v, dtype=np.float64)
+    D = np.ascontiguousarray(D_v, dtype=np.float64)
+    R = np.ascontiguousarray(R_v, dtype=np.float64)
+    if S.ndim != 2 or S.shape != D.shape or S.shape != R.shape:
+        raise ValueError("S_v, D_v, R_v must be [n_si, n_vehicles] arrays of one shape")
+    n_si, n_v = S.shape
+    n_out = n_si // int(si_per_second) if int(si_per_second) > 0 else 0
+    cchi = np.zeros(max(n_out, 1), np.float64)
+    schi = np.zeros(max(n_out, 1), np.float64)
+    f = np.zeros(max(n_out, 1), np.float64)
+    dp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(load().vc_aaa_intervals(dp(S), dp(D), dp(R), int(n_v), int(n_si), int(si_per_second), float(si_ms),
+                                   float(dcchi_ms), float(dschi_ms), dp(cchi), dp(schi), dp(f)))
+    return cchi[:n_out], schi[:n_out], f[:n_out]
 
 
 def kernel_launches() -> int:
