@@ -131,8 +131,19 @@ static int loop32(Mdp* m, float* buf0, float* buf1, double tol, long long max_sw
         int e = 0;
         frexpf(vm, &e);
         const double tol_eff = std::max(tol, vm > 0 ? 4.0 * ldexp(1.0, e - 24) : 0.0);
-        chunk = predict_sweeps(r, tol_eff, m->gamma);
-        chunk = std::min<long long>(std::max<long long>(chunk, 4), 1024);
+        // sweeps still needed, from the contraction observed over the last sweeps (the
+        // residual ring), else from gamma; most of them are enqueued at once and the rest
+        // in exact small chunks, so few sweeps are launched past the device's stop
+        double rate = m->gamma;
+        const long long k = std::min<long long>(std::min<long long>(chunk, kRing / 2), h.sweeps - 1);
+        if (k >= 4) {
+            float r0;
+            memcpy(&r0, &h.res32[(h.sweeps - 1 - k) % kRing], 4);
+            if (r0 > 0.0f && r > 0.0f && r < r0) rate = pow((double)r / (double)r0, 1.0 / (double)k);
+        }
+        const long long n = predict_sweeps(r, tol_eff, rate);
+        chunk = n > 16 ? n - n / 8 : n;
+        chunk = std::min<long long>(std::max<long long>(chunk, 2), 1024);
         chunk = std::min<long long>(chunk, max_sweeps - h.sweeps + 1);
     }
     *final_idx = h.final_buf;
