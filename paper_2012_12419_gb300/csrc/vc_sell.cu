@@ -31,8 +31,10 @@
 // released, in order).  Consumer warps take (slice, action) blocks of the CTA's tile
 // sequence round-robin, one lane per state: shared-memory reads are lane-consecutive (no
 // bank conflicts) and the V gathers of a warp fall on a few cache lines because the
-// lanes' successors share offsets.  Q values go to a per-tile shared buffer; the warp
-// that completes a tile's last block takes the max over actions and releases the tile.
+// lanes' successors share offsets.  A block's Q values overwrite its own R row in the
+// ring (read once, by the same lane), so no separate Q buffer takes shared memory from the
+// ring; the warp that completes a tile's last block takes the max over actions from the
+// tile's R rows and releases the tile.
 // Sweeps are launched as programmatic dependents of the previous sweep: a CTA that starts
 // while the previous grid drains stages its first tiles (the slab never changes), then
 // waits for that grid (griddepcontrol.wait) before it reads V or the loop's control
@@ -457,8 +459,8 @@ struct SellRingArgs {
     int TS;           // slices per tile (the last tile may hold fewer)
     int64_t ntiles;
     int ring;         // bytes of the tile ring
-    int qfloats;      // floats of one slot's Q buffer (TS * A * 32)
-    int qoff;         // byte offset of the Q buffers
+    int qfloats;      // unused (Q values live in the tiles' R rows)
+    int qoff;         // unused
     int roff;         // byte offset of the ring
 };
 
@@ -478,7 +480,6 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
     int* done_cnt = reinterpret_cast<int*>(empty + kSlots);
     uint32_t* slot_pos = reinterpret_cast<uint32_t*>(done_cnt + kSlots);
     unsigned long long* slot_end = reinterpret_cast<unsigned long long*>(smem + 384);
-    float* qbuf = reinterpret_cast<float*>(smem + t.qoff);
     unsigned char* ring = smem + t.roff;
     __shared__ int s_fail, s_consumed, s_next, s_abort;
     __shared__ long long s_bounds[2][32];
@@ -604,8 +605,7 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                 atomicExch(&s_fail, 1);
                 break;
             }
-            const unsigned char* base = ring + *((volatile uint32_t*)&slot_pos[s]);
-            float* qb = qbuf + s * t.qfloats;
+            unsigned char* base = ring + *((volatile uint32_t*)&slot_pos[s]);
             const int sl = (int)fdiv((uint32_t)b, t.div_A), act = b - sl * A;
             long long roff = 0;
             for (int k = 0; k < sl; ++k)
@@ -619,7 +619,11 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                 if (!VC_IN_BOUNDS(sc.ctl, roff + rb <= tile_bytes)) roff = 0;
             }
 #endif
-            qb[b * kSellC + lane] = block_q<VT>(base + roff, A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl);
+            const float qv = block_q<VT>(base + roff, A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl);
+            // the Q value replaces the block's own R entry in the ring (read above, by this lane
+            // only); the proxy fence orders the write before the tile's next bulk copy
+            reinterpret_cast<float*>(base + roff + 256)[act * kSellC + lane] = qv;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __threadfence_block();
             __syncwarp();
             int l = 0;
@@ -640,7 +644,8 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                         const unsigned char* rec = base + ro;
                         float b1 = -INFINITY, b2 = -INFINITY;
                         int ia = 0;
-                        for (int c = 0; c < A; ++c) top2_step(c, qb[(k * A + c) * kSellC + lane], b1, b2, ia);
+                        const float* qrow = reinterpret_cast<const float*>(rec + 256);
+                        for (int c = 0; c < A; ++c) top2_step(c, qrow[c * kSellC + lane], b1, b2, ia);
                         b1v[k] = b1;
                         b2v[k] = b2;
                         iav[k] = ia;
@@ -677,8 +682,8 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
 }
 
 // Candidate launch shapes of the ring sweep, in preference order: (CTAs per SM, consumer
-// warps per CTA) x slices per tile; the ring takes the shared memory left after the Q
-// buffers and must hold the largest tile.
+// warps per CTA) x slices per tile; the ring takes the shared memory left after the
+// header and must hold the largest tile.
 int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
     (void)st;
     out.clear();
@@ -714,7 +719,7 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             if (threads > fa.maxThreadsPerBlock || (long long)threads * fa.numRegs * ctas > 65536) continue;
             if (nrw > (kSlots - 2) * TS * A) continue;  // claimed blocks stay within kSlots tiles
             const int qoff = kHead;
-            const int qbytes = kSlots * (int)round128(4LL * TS * A * kSellC);
+            const int qbytes = 0;  // Q values live in the tile's R rows
             const int budget = std::min(dyn_max, (smem_sm - 1024 * ctas) / ctas - (int)fa.sharedSizeBytes);
             const int ring = ((budget - qoff - qbytes) / 128) * 128;
             if (ring < max_tile + 128) continue;
@@ -760,9 +765,9 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
         t.TS = m->plan.ts;
         t.ntiles = m->plan.ntiles;
         t.ring = (int)m->plan.cap;
-        t.qfloats = (int)round128(4LL * t.TS * m->A * kSellC) / 4;
+        t.qfloats = 0;
         t.qoff = kHead;
-        t.roff = kHead + kSlots * (int)round128(4LL * t.TS * m->A * kSellC);
+        t.roff = kHead;
         const long long cap = (long long)m->num_sms * m->plan.ctas_per_sm;
         const unsigned grid = (unsigned)(t.ntiles < cap ? t.ntiles : cap);
         const unsigned threads = (unsigned)(m->plan.warps + 1) * 32;
