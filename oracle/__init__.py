@@ -8,8 +8,9 @@ import it; the library itself never does, and nothing here imports the library.
 Two layers:
 
 * ``vc_oracle.c`` (loaded through ctypes): successor enumeration of the model, explicit
-  CSR construction, Jacobi value iteration, single-state backups, policies, policy
-  evaluation, analytic transition derivatives and a bfloat16 rounding routine.
+  CSR construction, Jacobi value iteration (with Eq. 18's backup, and with each action's
+  self-transition solved exactly), single-state backups, policies, policy evaluation,
+  analytic transition derivatives and a bfloat16 rounding routine.
 * numpy helpers below for tiny problems: dense policy evaluation by a linear solve,
   exhaustive policy enumeration, value iteration on dense random MDPs and the
   dense-solve adjoint gradient; and the AAA timer update of Section II (Algorithm 1)
@@ -96,6 +97,10 @@ def lib():
             L.or_policy_eval_iter.restype = ctypes.c_int
             L.or_vi_csr.argtypes = [i64, i32, vp, vp, vp, vp, dbl, dbl, i64, vp, vp, vp]
             L.or_vi_csr.restype = ctypes.c_int
+            L.or_value_iteration_sl.argtypes = [P, dbl, i64, vp, vp, vp, vp]
+            L.or_value_iteration_sl.restype = ctypes.c_int
+            L.or_vi_csr_sl.argtypes = [i64, i32, vp, vp, vp, vp, dbl, dbl, i64, vp, vp, vp]
+            L.or_vi_csr_sl.restype = ctypes.c_int
             L.or_policy_csr.argtypes = [i64, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
             L.or_bf16_rne.argtypes = [dbl]
             L.or_bf16_rne.restype = ctypes.c_uint16
@@ -224,6 +229,29 @@ def value_iteration(p: dict, tol: float = 1e-6, max_sweeps: int = 100000, V0=Non
     return V, int(sweeps[0]), float(res[0])
 
 
+def value_iteration_self_loop(p: dict, tol: float = 1e-6, max_sweeps: int = 100000, V0=None, record=False,
+                              strict=True):
+    """Value iteration whose backup solves each action's self-transition exactly,
+    Qs = (R + gamma sum_{s' != s} P V) / (1 - gamma P(s|s,a)) (Puterman 1994, Sec. 6.3.3;
+    Algorithm 4's in-block iteration for a block of one state, iterated to its limit).
+    Same fixed point V* as Eq. 18.  Returns (V, sweeps, last_change[, changes]); with
+    strict=False a max_sweeps that runs out returns the iterate instead of raising.
+    """
+    S = num_states(p)
+    V = np.zeros(S, np.float64) if V0 is None else np.array(V0, np.float64, copy=True)
+    sweeps = np.zeros(1, np.int64)
+    res = np.zeros(1, np.float64)
+    hist = np.zeros(max_sweeps if record else 0, np.float64)
+    st = lib().or_value_iteration_sl(
+        ctypes.byref(_params(p)), float(tol), int(max_sweeps), _ptr(V), _ptr(sweeps), _ptr(res),
+        _ptr(hist) if record else None)
+    if st != 0 and strict:
+        raise RuntimeError("oracle value iteration did not converge")
+    if record:
+        return V, int(sweeps[0]), float(res[0]), hist[: int(sweeps[0])].copy()
+    return V, int(sweeps[0]), float(res[0])
+
+
 def backup(p: dict, V: np.ndarray, s: int):
     """One Bellman backup of state s from V: (best value, argmax action, Q-gap)."""
     V = np.ascontiguousarray(V, np.float64)
@@ -303,8 +331,9 @@ def solve(p: dict, tol: float = 1e-12):
 # ------------------------------------------------------------- explicit / dense MDPs
 
 
-def vi_csr(S, A, row_ptr, col, val, R, gamma, tol=1e-12, max_sweeps=10**6, V0=None):
-    """Jacobi VI on an explicit CSR MDP (R = -inf marks infeasible rows)."""
+def vi_csr(S, A, row_ptr, col, val, R, gamma, tol=1e-12, max_sweeps=10**6, V0=None, strict=True):
+    """Jacobi VI on an explicit CSR MDP (R = -inf marks infeasible rows); with strict=False
+    a max_sweeps that runs out returns the iterate instead of raising."""
     row_ptr = np.ascontiguousarray(row_ptr, np.int64)
     col = np.ascontiguousarray(col, np.int32)
     val = np.ascontiguousarray(val, np.float64)
@@ -314,7 +343,24 @@ def vi_csr(S, A, row_ptr, col, val, R, gamma, tol=1e-12, max_sweeps=10**6, V0=No
     res = np.zeros(1, np.float64)
     st = lib().or_vi_csr(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(R), float(gamma), float(tol),
                          int(max_sweeps), _ptr(V), _ptr(sweeps), _ptr(res))
-    if st != 0:
+    if st != 0 and strict:
+        raise RuntimeError("oracle CSR value iteration did not converge")
+    return V, int(sweeps[0])
+
+
+def vi_csr_self_loop(S, A, row_ptr, col, val, R, gamma, tol=1e-12, max_sweeps=10**6, V0=None, strict=True):
+    """vi_csr with each row's self-transition solved exactly (entries whose column is the
+    row's own state form P(s|s,a)); returns (V, sweeps)."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    R = np.ascontiguousarray(R, np.float64)
+    V = np.zeros(S, np.float64) if V0 is None else np.array(V0, np.float64, copy=True)
+    sweeps = np.zeros(1, np.int64)
+    res = np.zeros(1, np.float64)
+    st = lib().or_vi_csr_sl(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(R), float(gamma),
+                            float(tol), int(max_sweeps), _ptr(V), _ptr(sweeps), _ptr(res))
+    if st != 0 and strict:
         raise RuntimeError("oracle CSR value iteration did not converge")
     return V, int(sweeps[0])
 

@@ -453,6 +453,73 @@ int or_value_iteration(const or_params* p, double tol, int64_t max_sweeps, doubl
     return status;
 }
 
+/* ----------------------------------- value iteration with self-transitions solved */
+
+/*
+ * Backup of state s with each action's own self-transition solved exactly: for a
+ * feasible action a with P(s|s,a) = p_ss,
+ *     Qs(s,a) = (R(s,a) + gamma * sum_{s' != s} P(s'|s,a) V(s')) / (1 - gamma * p_ss),
+ * and the backup is the largest Qs.  This is the "Jacobi" value iteration of Puterman
+ * (Markov Decision Processes, 1994, Sec. 6.3.3), and the in-block iteration of
+ * Algorithm 4 taken to a block of a single state and iterated to its limit.  For each
+ * action the map W -> R + gamma (p_ss W + rest) is affine with slope gamma p_ss < 1, so
+ * the fixed point of their maximum is the maximum of their fixed points: Eq. 18's V*
+ * is also the fixed point here, and at V* the same actions attain the maximum.
+ */
+static double sl_backup(const or_params* p, const double* V, int64_t s) {
+    double b = -INFINITY;
+    for (int a = 0; a <= p->H; a++) {
+        int64_t cols[OR_MAXSUCC];
+        double probs[OR_MAXSUCC], Rv;
+        int n = or_transitions(p, s, a, cols, probs, &Rv);
+        if (n < 0) continue;
+        double off = 0.0, pss = 0.0;
+        for (int j = 0; j < n; j++) {
+            if (cols[j] == s)
+                pss += probs[j];
+            else
+                off += probs[j] * V[cols[j]];
+        }
+        double qv = (Rv + p->gamma * off) / (1.0 - p->gamma * pss);
+        if (qv > b) b = qv;
+    }
+    return b;
+}
+
+/*
+ * Value iteration with sl_backup in place of Eq. 18's backup: Jacobi sweeps (every state
+ * from the previous iterate) from V, stopping after the first sweep whose change
+ * max_s |V^{k+1}(s) - V^k(s)| is below tol.  Same arguments and return value as
+ * or_value_iteration.
+ */
+int or_value_iteration_sl(const or_params* p, double tol, int64_t max_sweeps, double* V, int64_t* sweeps_out,
+                          double* residual_out, double* residuals) {
+    const int64_t S = or_num_states(p);
+    double* Vn = (double*)malloc(sizeof(double) * S);
+    int64_t k = 0;
+    double res = INFINITY;
+    int status = 1;
+    while (k < max_sweeps) {
+        res = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            Vn[s] = sl_backup(p, V, s);
+            double d = fabs(Vn[s] - V[s]);
+            if (d > res) res = d;
+        }
+        memcpy(V, Vn, sizeof(double) * S);
+        if (residuals) residuals[k] = res;
+        k++;
+        if (res < tol) {
+            status = 0;
+            break;
+        }
+    }
+    free(Vn);
+    *sweeps_out = k;
+    *residual_out = res;
+    return status;
+}
+
 /* Greedy policy of Algorithm 2 read on this MDP: place the head task on the feasible
  * host with the largest service rate (lowest index on ties), else defer. */
 void or_greedy_policy(const or_params* p, int32_t* pi) {
@@ -542,6 +609,51 @@ int or_vi_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, 
                 double acc = 0.0;
                 for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) acc += val[j] * V[col[j]];
                 double qv = R[r] + gamma * acc;
+                if (qv > b) b = qv;
+            }
+            Vn[s] = b;
+            double d = fabs(Vn[s] - V[s]);
+            if (d > res) res = d;
+        }
+        memcpy(V, Vn, sizeof(double) * S);
+        k++;
+        if (res < tol) {
+            status = 0;
+            break;
+        }
+    }
+    free(Vn);
+    *sweeps_out = k;
+    *residual_out = res;
+    return status;
+}
+
+/*
+ * or_vi_csr with each row's self-transition solved exactly (the backup of sl_backup):
+ * entries of row s*A+a whose column is s make up p_ss, the others the sum.
+ */
+int or_vi_csr_sl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const double* val,
+                 const double* R, double gamma, double tol, int64_t max_sweeps, double* V, int64_t* sweeps_out,
+                 double* residual_out) {
+    double* Vn = (double*)malloc(sizeof(double) * S);
+    int64_t k = 0;
+    double res = INFINITY;
+    int status = 1;
+    while (k < max_sweeps) {
+        res = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            double b = -INFINITY;
+            for (int a = 0; a < A; a++) {
+                int64_t r = s * A + a;
+                if (R[r] == -INFINITY) continue;
+                double off = 0.0, pss = 0.0;
+                for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) {
+                    if (col[j] == s)
+                        pss += val[j];
+                    else
+                        off += val[j] * V[col[j]];
+                }
+                double qv = (R[r] + gamma * off) / (1.0 - gamma * pss);
                 if (qv > b) b = qv;
             }
             Vn[s] = b;
