@@ -57,6 +57,9 @@ def parse():
                     help="CSR kernels only: build no sliced (SELL-C-sigma) copy of the stored matrix for the "
                          "autotuner to choose")
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--self-loop", dest="self_loop", action="store_true",
+                    help="FP32 sweeps solve each action's self-transition exactly (VC_ITER_SELF_LOOP; same V*, "
+                         "fewer sweeps); by default the step runs Eq. 18's backup as Algorithm 3 states it")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and the variants")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default CSR schedule (profiling runs: no tuning launches before the timed ones)")
@@ -161,7 +164,7 @@ def run_native(args):
 
     def step():
         V.zero_()  # Algorithm 3, step 1
-        _, V64, pi, st = m.value_iterate(V, tol=args.tol)
+        _, V64, pi, st = m.value_iterate(V, tol=args.tol, self_loop=args.self_loop)
         return st
 
     for _ in range(max(3, args.warmup)):
@@ -213,6 +216,7 @@ def run_native(args):
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "256 MiB buffer written between steps, outside the step events",
             "step": "V=0 -> FP32 sweeps -> argmax -> FP64 policy evaluation -> FP64 Bellman certificate",
+            "sweep": "self-transition solved" if args.self_loop else "Eq. 18 backup",
         },
         "time_to_residual_ms": statistics.median(ms),
         "sweeps_per_step": statistics.median(sweeps),
@@ -237,6 +241,7 @@ def run_native(args):
             if world == 1:
                 out["cpu_baseline"] = cpu_baseline(p, args)
             out["variants"] = variants(args, p, native, torch, dev, stream)
+            out["self_loop"] = self_loop_comparison(args, p, m, V, native, torch, dev, stream)
             if world == 1 and args.workload == "large":
                 out["comparisons"] = comparisons(args, native, torch, dev, stream)
         print(json.dumps(out))
@@ -291,7 +296,7 @@ def run_batched(args):
 
     def step():
         V.zero_()
-        _, _, _, st, _ = b.value_iterate(V, tol=args.tol)
+        _, _, _, st, _ = b.value_iterate(V, tol=args.tol, self_loop=args.self_loop)
         return st
 
     for _ in range(max(3, args.warmup)):
@@ -342,6 +347,7 @@ def run_batched(args):
             "l2": "256 MiB buffer written between steps, outside the step events",
             "step": "V=0 -> one graph launch of FP32 sweeps with per-instance termination -> argmax -> "
                     "FP64 policy evaluation -> FP64 Bellman certificate per instance",
+            "sweep": "self-transition solved" if args.self_loop else "Eq. 18 backup",
         },
         "time_to_residual_ms": statistics.median(ms),
         "certified": all(c == 1 for _, c in gathered),
@@ -366,12 +372,34 @@ def run_batched(args):
         if world == 1:
             out["cpu_baseline"] = cpu_baseline_batched(ps_all)
             out["vs_per_instance"] = batched_vs_per_instance(args, ps, b, native, torch, dev, stream)
+            out["self_loop"] = batched_self_loop(args, b, torch, dev, stream)
     if rank == 0:
         print(json.dumps(out))
     b.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batched_self_loop(args, b, torch, dev, stream):
+    """The batched step with and without VC_ITER_SELF_LOOP (each instance's FP32 loop solves
+    every action's self-transition exactly), device-timed to the same certified residual."""
+    V = torch.zeros(b.total, dtype=torch.float32, device=dev)
+    res = {}
+    for sl in (False, True):
+        def solve():
+            V.zero_()
+            return b.value_iterate(V, tol=args.tol, self_loop=sl)
+
+        solve()
+        t, (_, V64, _, st, _) = _timed(torch, stream, solve, 3)
+        res[sl] = (t, V64.clone(), st)
+    (t0, V0, s0), (t1, V1, s1) = res[False], res[True]
+    return {"eq18_ms": t0, "self_loop_ms": t1, "speedup": t0 / t1,
+            "eq18_sweeps_total": int(sum(x["sweeps"] for x in s0)),
+            "self_loop_sweeps_total": int(sum(x["sweeps"] for x in s1)),
+            "certified": all(x["certified"] == 1 for x in s0 + s1),
+            "max_abs_V64_difference": float((V1 - V0).abs().max())}
 
 
 def batched_e2e(args, ps, nnz, native, torch):
@@ -566,9 +594,9 @@ def comparisons(args, native, torch, dev, stream):
 # kernel source (profiles/k_sell_ring_large_padded.md, k_sell_ring_large_canonical.md);
 # reported only while the sources hash the same, since a changed kernel voids the counters.
 TRAFFIC_SOURCES = ("vc_sell.cu", "vc_internal.cuh", "vc_ptx.cuh")
-TRAFFIC_SOURCE_SHA = "ef6e6c3f67d4a0b9e12a68a6bfb6b7caf6ffede58e5c882f58fdbfd39c82f946"
-TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_494_700_800,
-                 ("large", "csr_f32", False, True): 1_196_749_312}
+TRAFFIC_SOURCE_SHA = "78c9624030b4506bda9d33093f98e42677fd72b1ed5a171745eed85eac978adc"
+TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_494_598_656,
+                 ("large", "csr_f32", False, True): 1_197_186_048}
 
 
 def measured_traffic(args, info):
@@ -655,6 +683,37 @@ def _best_plan(m):
     """The autotuner's chosen line (kernel, tile, stages, CTAs/SM, smem, us per sweep)."""
     rows = m.autotune_report().strip().splitlines()[1:]
     return min(rows, key=lambda r: float(r.split()[-1])) if rows else None
+
+
+def self_loop_comparison(args, p, m, V, native, torch, dev, stream):
+    """The same step with and without VC_ITER_SELF_LOOP (FP32 sweeps that solve each
+    action's self-transition exactly), on the bench's handle and on the implicit form, each
+    device-timed to the same certified residual."""
+    out = {}
+    mi = native.MDP.build(p, fmt="implicit")
+    Vi = torch.zeros(int(mi.info()["S"]), dtype=torch.float32, device=dev)
+    for name, mm, Vb in (("bench_form", m, V), ("implicit", mi, Vi)):
+        res = {}
+        for sl in (False, True):
+            def solve():
+                Vb.zero_()
+                return mm.value_iterate(Vb, tol=args.tol, self_loop=sl)
+
+            solve()
+            t, (_, V64, _, st) = _timed(torch, stream, solve, 3)
+            res[sl] = (t, V64.clone(), st)
+        (t0, V0, s0), (t1, V1, s1) = res[False], res[True]
+        out[name] = {
+            "eq18_ms": t0, "self_loop_ms": t1, "speedup": t0 / t1,
+            "eq18_sweeps": int(s0["sweeps"]), "self_loop_sweeps": int(s1["sweeps"]),
+            "self_loop_ms_fp32_sweeps": s1["ms_fp32"], "self_loop_ms_fp64_refine": s1["ms_fp64"],
+            "self_loop_us_per_sweep": 1e3 * s1["ms_fp32"] / max(int(s1["sweeps"]), 1),
+            "eq18_us_per_sweep": 1e3 * s0["ms_fp32"] / max(int(s0["sweeps"]), 1),
+            "certified": s0["certified"] == 1 and s1["certified"] == 1,
+            "max_abs_V64_difference": float((V1 - V0).abs().max()),
+        }
+    mi.close()
+    return out
 
 
 def variants(args, p, native, torch, dev, stream):

@@ -74,6 +74,15 @@ extern "C" {
                                 max|V64 - V*| <= gamma/(1-gamma) * residual <= tol/2 */
 #define VC_ITER_PLAIN_CORRECTION 4  /* solve the refinement's correction equation by
                                        fixed-point sweeps instead of BiCGSTAB */
+#define VC_ITER_SELF_LOOP 8  /* FP32 sweeps solve each action's self-transition exactly:
+                                Q(s,a) = (R + gamma sum_{s' != s} P V) / (1 - gamma P(s|s,a))
+                                (Puterman 1994, Sec. 6.3.3; Algorithm 4's in-block iteration
+                                for a block of one state, run to its limit).  Same fixed point
+                                V* and the same optimal actions as Eq. 18's backup, contraction
+                                max gamma (1 - p_ss) / (1 - gamma p_ss) <= gamma per sweep, so
+                                fewer sweeps; the sweep change, not Eq. 18's residual, is the
+                                FP32 stopping test, and the FP64 refinement and certificate use
+                                Eq. 18's backup as without the flag.  Every storage form. */
 
 /* Model parameters (host struct; mu and delta are HOST arrays of length H). */
 typedef struct vc_params {
@@ -212,6 +221,8 @@ int vc_set_wait_limit(vc_mdp* m, int64_t polls);
  * V64 = T(V) whose residual max|T V - V| is the certificate (policy improvement repeats
  * if the backup changes pi).  V64_out ([S] double, nullable) receives that backup, pi_out
  * ([S] int32, nullable) its argmax.  Synchronises `stream`.
+ * With VC_ITER_SELF_LOOP the FP32 sweeps use the self-transition-solved backup (see the
+ * flag); the policy taken from the FP32 values and everything after it are unchanged.
  * Errors: VC_ERR_NOT_CONVERGED if max_sweeps ran out (outputs still written),
  * VC_ERR_ARG for tol <= 0 or max_sweeps < 1.
  */
@@ -384,8 +395,9 @@ typedef struct vc_batch_stats {
  * as in vc_build_mdp; implicit form).  Instance i occupies states [off_i, off_i + S_i) of
  * the concatenated arrays, off from vc_batch_offsets.  The schedule (tile size, persistent
  * grid) starts at 4096 states per tile and 8 blocks per SM; vc_batch_autotune picks one by
- * timing.  Two CUDA graphs are captured once per schedule: the FP32 value-iteration loop
- * and the refinement's correction loop, each a device-side WHILE loop.  Algorithm 3 for
+ * timing.  CUDA graphs are captured once per schedule: the FP32 value-iteration loop (with
+ * Eq. 18's backup, and with each action's self-transition solved) and the refinement's
+ * correction loops, each a device-side WHILE loop.  Algorithm 3 for
  * every instance, applied to many cells of a vehicular cloud at once (the paper's BSDI
  * partitions one state space into independent blocks; here the blocks are whole MDPs).
  */
@@ -404,7 +416,8 @@ int vc_batch_offsets(const vc_batch* b, int64_t* offsets);
  * VC_ITER_PLAIN_CORRECTION or if an instance breaks down) + FP64 update and certified by
  * one FP64 Bellman backup (repeated while an instance fails); VC_ITER_ACCURATE certifies
  * each instance's error
- * (residual below tol (1 - gamma_i) / (2 gamma_i)).  V: [total] float in (warm start) / out (FP32
+ * (residual below tol (1 - gamma_i) / (2 gamma_i)).  VC_ITER_SELF_LOOP runs the FP32 loop
+ * with the self-transition-solved backup, as in vc_value_iterate.  V: [total] float in (warm start) / out (FP32
  * iterate); V64_out [total] double and pi_out [total] int32 nullable (pi is local to the
  * instance: 0..H_i); per_inst: HOST array of n stats (nullable).  Synchronises `stream`.
  * VC_ERR_NOT_CONVERGED if an instance is not certified (or, FP32 only, hit max_sweeps).

@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 static void free_mdp(Mdp* m) {
     if (!m) return;
-    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->rate_tab, m->Vb, m->U32, m->U64, m->V64a,
+    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->rate_tab, m->Vb, m->U32, m->U32s, m->U64, m->V64a,
                     m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->kr, m->kr_part, m->kctl, m->ctl,
                     m->sell_rec, m->sell_slab};
     for (void* p : ptrs)
@@ -49,6 +49,7 @@ static int alloc_work(Mdp* m) {
     const size_t S = (size_t)m->S;
     if ((rc = alloc_dev(m, (void**)&m->Vb, 4 * S))) return rc;
     if ((m->fmt & 0xF) == VC_IMPLICIT && (rc = alloc_dev(m, (void**)&m->U32, 4 * S))) return rc;
+    if ((m->fmt & 0xF) == VC_IMPLICIT && (rc = alloc_dev(m, (void**)&m->U32s, 4 * S))) return rc;
     if (m->has_model && (rc = alloc_dev(m, (void**)&m->U64, 8 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->V64a, 8 * S))) return rc;
     if ((rc = alloc_dev(m, (void**)&m->V64b, 8 * S))) return rc;
@@ -644,7 +645,9 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
     VC_CUDA(cudaEventRecord(ev[0], st));
     {
         NvtxRange nv32("fp32 sweeps");
+        const int self_loop = (flags & VC_ITER_SELF_LOOP) ? 1 : 0;
         rc = loop32(m, V, m->Vb, tol, max_sweeps, st, &fin, [&](const float* in, float* o, SweepCtl sc) {
+            sc.self_loop = self_loop;
             return launch_sweep32(m, in, o, nullptr, nullptr, sc, st);
         });
     }

@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "vc_internal.cuh"
@@ -161,10 +162,13 @@ __device__ __forceinline__ const Coef<double>& coef_of<double>(const InstDesc& d
 }
 
 // Pass 1 over all active tiles: U(x) = R(x) + gamma E[V(next) | x] (per instance).
-// done = nullptr processes every instance (extraction / certificate passes).
-template <int MH, typename T>
+// done = nullptr processes every instance (extraction / certificate passes).  SL (FP32
+// loop only): also U2(x) = defer's backup with its self-transition solved.
+template <int MH, typename T, bool SL>
 __global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
-                        const int* __restrict__ done, const T* __restrict__ V, T* __restrict__ U) {
+                        const int* __restrict__ done, const T* __restrict__ V, T* __restrict__ U,
+                        T* __restrict__ U2) {
+    static_assert(!SL || std::is_same<T, float>::value, "self-transition solve in FP32 sweeps only");
     __shared__ InstDesc sd;
     __shared__ int skip;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -180,7 +184,9 @@ __global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __r
                 const int x = tl.start + j;
                 Digits d;
                 decode<MH>(sd.md, x, d);
-                Ui[x] = b_reward<MH>(sd.md, coef_of<T>(sd), d) + coef_of<T>(sd).gamma * b_expect<MH>(sd.md, coef_of<T>(sd), Vi, x, d);
+                const T rx = b_reward<MH>(sd.md, coef_of<T>(sd), d);
+                Ui[x] = rx + coef_of<T>(sd).gamma * b_expect<MH>(sd.md, coef_of<T>(sd), Vi, x, d);
+                if constexpr (SL) U2[sd.off + x] = defer_self_loop<MH>(sd.md, sd.c32, Vi, x, d, rx);
             }
         }
         __syncthreads();
@@ -188,10 +194,12 @@ __global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __r
 }
 
 // Pass 2: V'(s) = max_a U(x_a(s)); per-instance residual and close (loop mode, ctl given),
-// or plain extraction with policy / FP64 certificate residual into res64 (ctl null).
-template <int MH, typename T>
+// or plain extraction with policy / FP64 certificate residual into res64 (ctl null).  SL:
+// defer takes U2(s) (its backup with the self-transition solved).
+template <int MH, typename T, bool SL>
 __global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
-                       BatchCtl c, int loop, int parity, const T* __restrict__ U, const T* __restrict__ V_in,
+                       BatchCtl c, int loop, int parity, const T* __restrict__ U, const T* __restrict__ U2,
+                       const T* __restrict__ V_in,
                        T* __restrict__ V_out, int32_t* __restrict__ pi, unsigned long long* __restrict__ res64) {
     __shared__ InstDesc sd;
     __shared__ int skip;
@@ -226,7 +234,7 @@ __global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __re
                     }
                 }
             }
-            const T u = Ui[s];
+            const T u = SL ? U2[sd.off + s] : Ui[s];
             if (u > best) {
                 best = u;
                 arg = sd.md.H;
@@ -631,7 +639,7 @@ struct Batch {
     std::vector<int> h_tiles_of;
     InstDesc* d_desc = nullptr;
     BatchTile* d_tiles = nullptr;
-    float *Va = nullptr, *Vb = nullptr, *U = nullptr, *E0 = nullptr, *E1 = nullptr, *Rr = nullptr;
+    float *Va = nullptr, *Vb = nullptr, *U = nullptr, *U2 = nullptr, *E0 = nullptr, *E1 = nullptr, *Rr = nullptr;
     double *V64 = nullptr, *V64b = nullptr, *U64 = nullptr;
     int32_t *pi = nullptr, *pi2 = nullptr;
     int *done = nullptr, *sweeps = nullptr, *ticket = nullptr, *tiles_of = nullptr, *final_buf = nullptr,
@@ -652,8 +660,8 @@ struct Batch {
     int *kr_done = nullptr, *kr_iter = nullptr, *tile_first = nullptr;
     unsigned int* kr_ticket = nullptr;
     long long* kr_max_d = nullptr;
-    cudaGraph_t g_vi = nullptr, g_corr = nullptr, g_kry = nullptr;
-    cudaGraphExec_t x_vi = nullptr, x_corr = nullptr, x_kry = nullptr;
+    cudaGraph_t g_vi = nullptr, g_vi_sl = nullptr, g_corr = nullptr, g_kry = nullptr;
+    cudaGraphExec_t x_vi = nullptr, x_vi_sl = nullptr, x_corr = nullptr, x_kry = nullptr;
     std::vector<void*> owned;
     int64_t device_bytes = 0;
     std::string tune_report;
@@ -759,15 +767,16 @@ constexpr int kCorrBodyKernels = 3;
 constexpr int kKryBodyKernels = 6;      // one BiCGSTAB iteration per pass
 constexpr long long kKrylovMaxIter = 1000;
 
-template <int MH>
+template <int MH, bool SL>
 static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
     const BatchCtl c = ctl_of(b);
-    k_bpost<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U);
-    k_bmax<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 0, b->U, b->Va, b->Vb,
-                                                     nullptr, nullptr);
-    k_bpost<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U);
-    k_bmax<MH, float><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 1, b->U, b->Vb, b->Va,
-                                                     nullptr, nullptr);
+    float* U2 = SL ? b->U2 : nullptr;
+    k_bpost<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U, U2);
+    k_bmax<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 0, b->U, U2, b->Va,
+                                                         b->Vb, nullptr, nullptr);
+    k_bpost<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U, U2);
+    k_bmax<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 1, b->U, U2, b->Vb,
+                                                         b->Va, nullptr, nullptr);
     k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
 }
 
@@ -824,7 +833,10 @@ static int make_loop_graph(cudaGraph_t* g, cudaGraphExec_t* x, Body&& body) {
 static int build_graphs(Batch* b) {
     int rc;
     auto vi = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
-        by_mh(b->mh, [&](auto m) { enqueue_vi_body<decltype(m)::value>(b, cs, h); });
+        by_mh(b->mh, [&](auto m) { enqueue_vi_body<decltype(m)::value, false>(b, cs, h); });
+    };
+    auto vi_sl = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        by_mh(b->mh, [&](auto m) { enqueue_vi_body<decltype(m)::value, true>(b, cs, h); });
     };
     auto corr = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
         by_mh(b->mh, [&](auto m) { enqueue_corr_body<decltype(m)::value>(b, cs, h); });
@@ -833,6 +845,7 @@ static int build_graphs(Batch* b) {
         by_mh(b->mh, [&](auto m) { enqueue_kry_body<decltype(m)::value>(b, cs, h); });
     };
     if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, vi))) return rc;
+    if ((rc = make_loop_graph(&b->g_vi_sl, &b->x_vi_sl, vi_sl))) return rc;
     if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, corr))) return rc;
     if ((rc = make_loop_graph(&b->g_kry, &b->x_kry, kry))) return rc;
     return VC_OK;
@@ -842,6 +855,8 @@ static void free_batch(Batch* b) {
     if (!b) return;
     if (b->x_vi) cudaGraphExecDestroy(b->x_vi);
     if (b->g_vi) cudaGraphDestroy(b->g_vi);
+    if (b->x_vi_sl) cudaGraphExecDestroy(b->x_vi_sl);
+    if (b->g_vi_sl) cudaGraphDestroy(b->g_vi_sl);
     if (b->x_corr) cudaGraphExecDestroy(b->x_corr);
     if (b->g_corr) cudaGraphDestroy(b->g_corr);
     if (b->x_kry) cudaGraphExecDestroy(b->x_kry);
@@ -865,21 +880,24 @@ static int reset_loop(Batch* b, double tol, long long max_sweeps, cudaStream_t s
 
 template <int MH>
 static void enqueue_extract(Batch* b, const float* V, int32_t* pi, cudaStream_t st) {
-    k_bpost<MH, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U);
-    k_bmax<MH, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U, V,
-                                                     nullptr, pi, nullptr);
+    k_bpost<MH, float, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U,
+                                                            nullptr);
+    k_bmax<MH, float, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U,
+                                                           nullptr, V, nullptr, pi, nullptr);
 }
 
 template <int MH>
 static void enqueue_cert(Batch* b, cudaStream_t st) {
-    k_bpost<MH, double><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64, b->U64);
-    k_bmax<MH, double><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U64,
-                                                      b->V64, b->V64b, b->pi2, b->res64);
+    k_bpost<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64,
+                                                             b->U64, nullptr);
+    k_bmax<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U64,
+                                                            nullptr, b->V64, b->V64b, b->pi2, b->res64);
 }
 
 template <int MH>
 static void enqueue_resid(Batch* b, cudaStream_t st) {
-    k_bpost<MH, double><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64, b->U64);
+    k_bpost<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64,
+                                                             b->U64, nullptr);
     k_bresid64<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, b->U64, b->V64, b->Rr,
                                                  b->err);
 }
@@ -930,8 +948,8 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t T = (size_t)b->total, N = (size_t)n;
-    void** f4[] = {(void**)&b->Va, (void**)&b->Vb, (void**)&b->U, (void**)&b->E0, (void**)&b->E1, (void**)&b->Rr,
-                   (void**)&b->pi, (void**)&b->pi2};
+    void** f4[] = {(void**)&b->Va, (void**)&b->Vb, (void**)&b->U, (void**)&b->U2, (void**)&b->E0, (void**)&b->E1,
+                   (void**)&b->Rr, (void**)&b->pi, (void**)&b->pi2};
     for (void** pp : f4)
         if (!rc) rc = balloc(b, pp, 4 * T);
     void** f8[] = {(void**)&b->V64, (void**)&b->V64b, (void**)&b->U64};
@@ -1016,7 +1034,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     // ---- FP32 value iteration of every instance: one graph launch
     VC_CUDA(cudaMemcpyAsync(b->Va, V, 4 * T, cudaMemcpyDeviceToDevice, st));
     if ((rc = reset_loop(b, tol, max_sweeps, st))) return rc;
-    VC_CUDA(cudaGraphLaunch(b->x_vi, st));
+    VC_CUDA(cudaGraphLaunch((flags & VC_ITER_SELF_LOOP) ? b->x_vi_sl : b->x_vi, st));
     long long vi_iters = 0, corr_iters = 0;
     VC_CUDA(cudaMemcpyAsync(&vi_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
     count_launches(1);

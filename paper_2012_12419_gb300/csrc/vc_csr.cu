@@ -18,6 +18,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "vc_internal.cuh"
@@ -89,43 +90,78 @@ __device__ __forceinline__ void top2_reduce(float& b1, int& ia, float& b2) {
 // a row of up to kBatch successors costs one memory round trip.
 constexpr int kBatch = 16;
 
-template <typename VT>
-__device__ __forceinline__ float row_dot_smem(const int32_t* cp, const VT* vp, int n, const float* __restrict__ V) {
+// SL: entries whose column is the row's own state `self` add their value to pss and
+// nothing to the sum (fmaf with a zero operand leaves acc unchanged), so the result is
+// the sum over the other successors, still in column order.
+template <typename VT, bool SL>
+__device__ __forceinline__ float row_dot_smem(const int32_t* cp, const VT* vp, int n, const float* __restrict__ V,
+                                              int self, float& pss) {
     float acc = 0.0f;
     for (int j0 = 0; j0 < n; j0 += kBatch) {
         float w[kBatch], g[kBatch];
+        uint32_t own = 0;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (j0 + u < n) {
+                const int c = cp[j0 + u];
                 w[u] = ldv<VT>(vp, j0 + u);
-                g[u] = __ldg(V + cp[j0 + u]);
+                g[u] = __ldg(V + c);
+                if (SL) own |= (c == self ? 1u : 0u) << u;
             }
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (j0 + u < n) acc = fmaf(w[u], g[u], acc);
+        for (int u = 0; u < kBatch; ++u) {
+            if (j0 + u < n) {
+                if (SL) {
+                    const bool o = (own >> u) & 1u;
+                    pss += o ? w[u] : 0.0f;
+                    acc = fmaf(w[u], o ? 0.0f : g[u], acc);
+                } else {
+                    acc = fmaf(w[u], g[u], acc);
+                }
+            }
+        }
     }
     return acc;
 }
 
-template <typename VT>
+template <typename VT, bool SL>
 __device__ __forceinline__ float row_dot_global(const int32_t* __restrict__ col, const VT* __restrict__ val, int64_t lo,
-                                                int n, const float* __restrict__ V) {
+                                                int n, const float* __restrict__ V, int self, float& pss) {
     float acc = 0.0f;
     for (int j0 = 0; j0 < n; j0 += kBatch) {
         float w[kBatch], g[kBatch];
+        uint32_t own = 0;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (j0 + u < n) {
+                const int c = __ldg(col + lo + j0 + u);
                 w[u] = ldg_v<VT>(val, lo + j0 + u);
-                g[u] = __ldg(V + __ldg(col + lo + j0 + u));
+                g[u] = __ldg(V + c);
+                if (SL) own |= (c == self ? 1u : 0u) << u;
             }
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (j0 + u < n) acc = fmaf(w[u], g[u], acc);
+        for (int u = 0; u < kBatch; ++u) {
+            if (j0 + u < n) {
+                if (SL) {
+                    const bool o = (own >> u) & 1u;
+                    pss += o ? w[u] : 0.0f;
+                    acc = fmaf(w[u], o ? 0.0f : g[u], acc);
+                } else {
+                    acc = fmaf(w[u], g[u], acc);
+                }
+            }
+        }
     }
     return acc;
+}
+
+// Q value of a stored row from its sum (and, SL, its self-transition probability).
+template <bool SL>
+__device__ __forceinline__ float row_q(float rr, float gamma, float acc, float pss, const float* sc) {
+    if (SL) return q_self_loop(rr, gamma, sc ? *sc * acc : acc, sc ? *sc * pss : pss);
+    return rr + gamma * (sc ? *sc * acc : acc);
 }
 
 struct CsrArgs {
@@ -145,7 +181,7 @@ struct CsrArgs {
 };
 
 // ------------------------------------------------------------------ pipelined sweep
-template <typename VT, int APAD>
+template <typename VT, int APAD, bool SL>
 __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepCtl sc) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (loop_done(sc)) return;
@@ -257,9 +293,10 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
                             ok = VC_IN_BOUNDS(sc.ctl, cs[j - c0] >= 0 && cs[j - c0] < a.S);
 #endif
                         if (ok) {
-                            const float acc =
-                                row_dot_smem<VT>(cs + (lo - c0), vs + (lo - v0), (int)(hi - lo), a.V_in);
-                            q = rr + a.gamma * (Ss ? Ss[rl] * acc : acc);
+                            float pss = 0.0f;
+                            const float acc = row_dot_smem<VT, SL>(cs + (lo - c0), vs + (lo - v0), (int)(hi - lo),
+                                                                   a.V_in, s0 + sl, pss);
+                            q = row_q<SL>(rr, a.gamma, acc, pss, Ss ? Ss + rl : nullptr);
                         }
                     }
                 }
@@ -297,7 +334,7 @@ __global__ void __launch_bounds__((kNW + 1) * 32, 3) k_csr_tma(CsrArgs a, SweepC
 
 // ------------------------------------------------------------------- direct fallback
 // Same lane-per-row mapping, rows read from global memory; grid-stride over state groups.
-template <typename VT, int APAD>
+template <typename VT, int APAD, bool SL>
 __global__ void __launch_bounds__(kThreads) k_csr_direct(CsrArgs a, SweepCtl sc) {
     if (loop_done(sc)) return;
     const long long sweep = loop_sweep(sc);
@@ -322,8 +359,10 @@ __global__ void __launch_bounds__(kThreads) k_csr_direct(CsrArgs a, SweepCtl sc)
                     ok = VC_IN_BOUNDS(sc.ctl, a.col[j] >= 0 && a.col[j] < a.S);
 #endif
                 if (ok) {
-                    const float acc = row_dot_global<VT>(a.col, val, lo, (int)(hi - lo), a.V_in);
-                    q = rr + a.gamma * (a.scale ? __ldg(a.scale + r) * acc : acc);
+                    float pss = 0.0f;
+                    const float acc = row_dot_global<VT, SL>(a.col, val, lo, (int)(hi - lo), a.V_in, s, pss);
+                    const float scv = a.scale ? __ldg(a.scale + r) : 1.0f;
+                    q = row_q<SL>(rr, a.gamma, acc, pss, a.scale ? &scv : nullptr);
                 }
             }
         }
@@ -345,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) k_csr_direct(CsrArgs a, SweepCtl sc)
 }
 
 // Very wide action sets (A > 32): warp per state, rows in sequence, warp-reduced sums.
-template <typename VT>
+template <typename VT, bool SL>
 __global__ void __launch_bounds__(kThreads) k_csr_wide(CsrArgs a, SweepCtl sc) {
     if (loop_done(sc)) return;
     const long long sweep = loop_sweep(sc);
@@ -360,13 +399,24 @@ __global__ void __launch_bounds__(kThreads) k_csr_wide(CsrArgs a, SweepCtl sc) {
         for (int act = 0; act < a.A; ++act) {
             const int64_t r = (int64_t)s * a.A + act;
             const int64_t lo = __ldg(a.row_ptr + r), hi = __ldg(a.row_ptr + r + 1);
-            float acc = 0.0f;
-            for (int64_t j = lo + lane; j < hi; j += 32) acc = fmaf(ldg_v<VT>(val, j), __ldg(a.V_in + __ldg(a.col + j)), acc);
+            float acc = 0.0f, pss = 0.0f;
+            for (int64_t j = lo + lane; j < hi; j += 32) {
+                const int c = __ldg(a.col + j);
+                const float v = ldg_v<VT>(val, j);
+                if (SL && c == s)
+                    pss += v;
+                else
+                    acc = fmaf(v, __ldg(a.V_in + c), acc);
+            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (SL) pss += __shfl_xor_sync(0xffffffffu, pss, o);
+            }
             const float rr = __ldg(a.R + r);
             if (rr == -INFINITY) continue;
-            const float q = rr + a.gamma * (a.scale ? __ldg(a.scale + r) * acc : acc);
+            const float scv = a.scale ? __ldg(a.scale + r) : 1.0f;
+            const float q = row_q<SL>(rr, a.gamma, acc, pss, a.scale ? &scv : nullptr);
             if (q > best) {
                 second = best;
                 best = q;
@@ -535,18 +585,28 @@ static int pow2_at_least(int a) {
 // Dynamic shared memory limit of a kernel instance, and how many CTAs fit on an SM.
 // `bytes` is the per-block opt-in limit; the kernel's static shared memory comes off it.
 // *dyn_limit receives the dynamic amount actually allowed.
+// Both instantiations (Eq. 18's backup and the self-transition solve) get the same limit,
+// and the occupancy is the smaller of the two, since one plan serves both.
 template <typename VT, int APAD>
 static cudaError_t set_tma_smem(int bytes, int* dyn_limit) {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_csr_tma<VT, APAD>);
+    cudaFuncAttributes fa, fb;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_csr_tma<VT, APAD, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fb, k_csr_tma<VT, APAD, true>);
     if (e != cudaSuccess) return e;
-    *dyn_limit = bytes - (int)fa.sharedSizeBytes;
-    return cudaFuncSetAttribute(k_csr_tma<VT, APAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_limit);
+    *dyn_limit = bytes - (int)std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+    e = cudaFuncSetAttribute(k_csr_tma<VT, APAD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_limit);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_csr_tma<VT, APAD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_limit);
 }
 
 template <typename VT, int APAD>
 static cudaError_t tma_occupancy(int bytes, int* per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_csr_tma<VT, APAD>, (kNW + 1) * 32, bytes);
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_csr_tma<VT, APAD, false>, (kNW + 1) * 32, bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_tma<VT, APAD, true>, (kNW + 1) * 32, bytes);
+    *per_sm = std::min(a, b);
+    return e;
 }
 
 template <typename VT>
@@ -676,35 +736,50 @@ static CsrArgs args_of(const Mdp* m, const float* V_in, float* V_out, int32_t* p
     return a;
 }
 
-template <typename VT>
+template <typename VT, bool SL>
 static void launch_tma(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStream_t st) {
     const long long cap = (long long)m->num_sms * m->plan.ctas_per_sm;
     const int grid = (int)(m->plan.ntiles < cap ? m->plan.ntiles : cap);
     const dim3 blk((kNW + 1) * 32);
     switch (m->plan.apad) {
-        case 1: k_csr_tma<VT, 1><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
-        case 2: k_csr_tma<VT, 2><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
-        case 4: k_csr_tma<VT, 4><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
-        case 8: k_csr_tma<VT, 8><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
-        case 16: k_csr_tma<VT, 16><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
-        default: k_csr_tma<VT, 32><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 1: k_csr_tma<VT, 1, SL><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 2: k_csr_tma<VT, 2, SL><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 4: k_csr_tma<VT, 4, SL><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 8: k_csr_tma<VT, 8, SL><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        case 16: k_csr_tma<VT, 16, SL><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+        default: k_csr_tma<VT, 32, SL><<<grid, blk, m->plan.smem, st>>>(a, sc); break;
+    }
+}
+
+template <typename VT, bool SL>
+static void launch_direct(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStream_t st) {
+    const int g = state_grid(m);
+    if (m->A > 32) {
+        k_csr_wide<VT, SL><<<g, kThreads, 0, st>>>(a, sc);
+        return;
+    }
+    switch (pow2_at_least(m->A)) {
+        case 1: k_csr_direct<VT, 1, SL><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 2: k_csr_direct<VT, 2, SL><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 4: k_csr_direct<VT, 4, SL><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 8: k_csr_direct<VT, 8, SL><<<g, kThreads, 0, st>>>(a, sc); break;
+        case 16: k_csr_direct<VT, 16, SL><<<g, kThreads, 0, st>>>(a, sc); break;
+        default: k_csr_direct<VT, 32, SL><<<g, kThreads, 0, st>>>(a, sc); break;
     }
 }
 
 template <typename VT>
-static void launch_direct(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStream_t st) {
-    const int g = state_grid(m);
-    if (m->A > 32) {
-        k_csr_wide<VT><<<g, kThreads, 0, st>>>(a, sc);
-        return;
-    }
-    switch (pow2_at_least(m->A)) {
-        case 1: k_csr_direct<VT, 1><<<g, kThreads, 0, st>>>(a, sc); break;
-        case 2: k_csr_direct<VT, 2><<<g, kThreads, 0, st>>>(a, sc); break;
-        case 4: k_csr_direct<VT, 4><<<g, kThreads, 0, st>>>(a, sc); break;
-        case 8: k_csr_direct<VT, 8><<<g, kThreads, 0, st>>>(a, sc); break;
-        case 16: k_csr_direct<VT, 16><<<g, kThreads, 0, st>>>(a, sc); break;
-        default: k_csr_direct<VT, 32><<<g, kThreads, 0, st>>>(a, sc); break;
+static void launch_sweep_form(const Mdp* m, const CsrArgs& a, SweepCtl sc, cudaStream_t st) {
+    if (m->plan.tma) {
+        if (sc.self_loop)
+            launch_tma<VT, true>(m, a, sc, st);
+        else
+            launch_tma<VT, false>(m, a, sc, st);
+    } else {
+        if (sc.self_loop)
+            launch_direct<VT, true>(m, a, sc, st);
+        else
+            launch_direct<VT, false>(m, a, sc, st);
     }
 }
 
@@ -713,17 +788,10 @@ int csr_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qga
     const CsrArgs a = args_of(m, V_in, V_out, pi, qgap);
     const bool bf16 = (m->fmt & 0xF) == VC_CSR_BF16;
     count_launches(1);
-    if (m->plan.tma) {
-        if (bf16)
-            launch_tma<uint16_t>(m, a, sc, st);
-        else
-            launch_tma<float>(m, a, sc, st);
-    } else {
-        if (bf16)
-            launch_direct<uint16_t>(m, a, sc, st);
-        else
-            launch_direct<float>(m, a, sc, st);
-    }
+    if (bf16)
+        launch_sweep_form<uint16_t>(m, a, sc, st);
+    else
+        launch_sweep_form<float>(m, a, sc, st);
     VC_CUDA(cudaGetLastError());
     return VC_OK;
 }

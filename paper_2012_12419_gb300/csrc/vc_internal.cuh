@@ -285,7 +285,65 @@ struct SweepCtl {
     int mode;
     int out_index;
     const int32_t* pi_ref;
+    int self_loop;  // FP32 sweeps: solve each action's self-transition (q_self_loop)
 };
+
+// Q value with the row's self-transition solved exactly: the fixed point in W of
+// W = R + gamma (p_ss W + off), i.e. (R + gamma off) / (1 - gamma p_ss), where off is the
+// row sum over the successors other than the state itself and p_ss the probability of
+// staying (Puterman, Markov Decision Processes, 1994, Sec. 6.3.3; Algorithm 4's in-block
+// iteration for a block of one state, run to its limit).  One rounding per operation in a
+// fixed form, shared by every explicit sweep kernel so their results agree bitwise.
+__device__ __forceinline__ float q_self_loop(float rr, float gamma, float off, float pss) {
+    return __fdiv_rn(fmaf(gamma, off, rr), fmaf(-gamma, pss, 1.0f));
+}
+
+// Defer's backup with its self-transition solved (the post-decision state of defer is s
+// itself).  The events that leave x carry probability p_move and the sum sum_move of
+// p_e V(y_e); the rest (uniformisation remainder, an arrival blocked by a full queue, the
+// departure of an empty host) stays at x, so the fixed point of
+// W = R(x) + gamma ((1 - p_move) W + sum_move) is
+// W = (R(x) + gamma sum_move) / ((1 - gamma) + gamma p_move).  Both sums are formed
+// directly (no differences), so W carries a relative rounding error of a few units.
+template <int MH>
+__device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<float>& c, const float* __restrict__ V,
+                                                 int x, const Digits& d, float rx) {
+    float v1[MH], v0[MH];
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        const int o = d.occ[k];
+        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : 0.0f;
+        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : 0.0f;
+    }
+    const float va = (d.q < md.Q) ? V[x + 2] : 0.0f;
+    const float vf = V[d.ph ? x - 1 : x + 1];
+    float sm = 0.0f, pm = 0.0f;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o == 1) {
+                const float p = c.pc[k] + c.pd[k];
+                sm = fmaf(p, v1[k], sm);
+                pm += p;
+            } else if (o > 1) {
+                const float p1 = c.pc[k] * (float)o;
+                sm = fmaf(p1, v1[k], sm);
+                sm = fmaf(c.pd[k], v0[k], sm);
+                pm += p1;
+                pm += c.pd[k];
+            }
+        }
+    }
+    if (d.q < md.Q) {
+        sm = fmaf(c.pa, va, sm);
+        pm += c.pa;
+    }
+    const float pf = d.ph ? c.pf1 : c.pf0;
+    sm = fmaf(pf, vf, sm);
+    pm += pf;
+    return __fdiv_rn(fmaf(c.gamma, sm, rx), fmaf(c.gamma, pm, 1.0f - c.gamma));
+}
 
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -445,6 +503,7 @@ struct Mdp {
     // work buffers (owned)
     float* Vb = nullptr;        // FP32 ping-pong partner
     float* U32 = nullptr;       // FP32 post-decision values (implicit)
+    float* U32s = nullptr;      // FP32 defer values with the self-transition solved (implicit)
     double* U64 = nullptr;      // FP64 post-decision values
     double* V64a = nullptr;     // FP64 pair
     double* V64b = nullptr;

@@ -45,6 +45,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "vc_internal.cuh"
@@ -343,30 +344,48 @@ __device__ __forceinline__ float ld_val<uint16_t>(const uint16_t* p) {
 }
 
 // W consecutive entries of a lane's row: all loads and gathers first, then the fused
-// multiply-adds in column order onto acc.
-template <typename VT, int W>
-__device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, const float* __restrict__ V, float acc) {
+// multiply-adds in column order onto acc.  SL: entries whose column is the lane's own
+// state `self` add their value to pss and nothing to acc (fmaf with a zero operand leaves
+// acc unchanged), so acc is the sum over the other successors, still in column order.
+template <typename VT, int W, bool SL>
+__device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, const float* __restrict__ V, float acc,
+                                           int self, float& pss) {
     float gv[W];
+    uint32_t own = 0;
 #pragma unroll
-    for (int u = 0; u < W; ++u) gv[u] = __ldg(V + cp[u * kSellC]);
+    for (int u = 0; u < W; ++u) {
+        const int c = cp[u * kSellC];
+        gv[u] = __ldg(V + c);
+        if (SL) own |= (c == self ? 1u : 0u) << u;
+    }
     // the values are read from shared memory only once the gathers are in flight, so
     // they hold no registers meanwhile
 #pragma unroll
-    for (int u = 0; u < W; ++u) acc = fmaf(ld_val<VT>(vp + u * kSellC), gv[u], acc);
+    for (int u = 0; u < W; ++u) {
+        const float v = ld_val<VT>(vp + u * kSellC);
+        if (SL) {
+            const bool o = (own >> u) & 1u;
+            pss += o ? v : 0.0f;
+            acc = fmaf(v, o ? 0.0f : gv[u], acc);
+        } else {
+            acc = fmaf(v, gv[u], acc);
+        }
+    }
     return acc;
 }
 
 // Row sum of w entries in column order: rows of up to kSellLast entries in one exactly
 // sized batch (every gather of the row in flight at once), longer rows in batches of 16
 // until the rest fits one batch (no predicated slots).
-template <typename VT>
-__device__ __forceinline__ float row_dot(const int32_t* cp, const VT* vp, int w, const float* __restrict__ V) {
+template <typename VT, bool SL>
+__device__ __forceinline__ float row_dot(const int32_t* cp, const VT* vp, int w, const float* __restrict__ V, int self,
+                                         float& pss) {
     float acc = 0.0f;
     for (; w > kSellLast; w -= kSellBatch, cp += kSellBatch * kSellC, vp += kSellBatch * kSellC)
-        acc = dot_fixed<VT, kSellBatch>(cp, vp, V, acc);
+        acc = dot_fixed<VT, kSellBatch, SL>(cp, vp, V, acc, self, pss);
     switch (w) {
 #define VC_DOT_CASE(n) \
-    case n: return dot_fixed<VT, n>(cp, vp, V, acc);
+    case n: return dot_fixed<VT, n, SL>(cp, vp, V, acc, self, pss);
         VC_DOT_CASE(1) VC_DOT_CASE(2) VC_DOT_CASE(3) VC_DOT_CASE(4) VC_DOT_CASE(5) VC_DOT_CASE(6) VC_DOT_CASE(7)
         VC_DOT_CASE(8) VC_DOT_CASE(9) VC_DOT_CASE(10) VC_DOT_CASE(11) VC_DOT_CASE(12) VC_DOT_CASE(13)
         VC_DOT_CASE(14) VC_DOT_CASE(15) VC_DOT_CASE(16) VC_DOT_CASE(17) VC_DOT_CASE(18) VC_DOT_CASE(19)
@@ -378,8 +397,9 @@ __device__ __forceinline__ float row_dot(const int32_t* cp, const VT* vp, int w,
 static_assert(kSellLast >= kSellBatch, "a remainder must fit one batch");
 
 // Q value of lane `lane` in block `a` of a slice record (shared or global memory):
-// R + gamma (scale) sum_j val_j V[col_j], the sum in column order.
-template <typename VT>
+// R + gamma (scale) sum_j val_j V[col_j], the sum in column order; SL: the same row with
+// its self-transition solved (q_self_loop).
+template <typename VT, bool SL>
 __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a, int lane, float gamma, bool has_scale,
                                          const float* __restrict__ V, int S, Ctl* ctl) {
     const int32_t* hdr = reinterpret_cast<const int32_t*>(rec);
@@ -398,8 +418,11 @@ __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a,
     (void)S;
     (void)ctl;
 #endif
-    const float acc = row_dot<VT>(cp, vp, w, V);
+    float pss = 0.0f;
+    const int self = SL ? reinterpret_cast<const int32_t*>(rec + 128)[lane] : -1;
+    const float acc = row_dot<VT, SL>(cp, vp, w, V, self, pss);
     const float sc = has_scale ? reinterpret_cast<const float*>(rec + L.scale)[a * kSellC + lane] : 1.0f;
+    if (SL) return q_self_loop(rr, gamma, has_scale ? sc * acc : acc, has_scale ? sc * pss : pss);
     return rr + gamma * (has_scale ? sc * acc : acc);
 }
 
@@ -425,7 +448,7 @@ __device__ __forceinline__ void write_state(const SellArgs& a, int s, float b1, 
 }
 
 // Direct: one warp per slice, the record read from global memory.
-template <typename VT>
+template <typename VT, bool SL>
 __global__ void __launch_bounds__(kThreads) k_sell(SellArgs a, SweepCtl sc) {
     if (loop_done(sc)) return;
     const long long sweep = loop_sweep(sc);
@@ -437,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_sell(SellArgs a, SweepCtl sc) {
         float b1 = -INFINITY, b2 = -INFINITY;
         int ia = 0;
         for (int act = 0; act < a.A; ++act)
-            top2_step(act, block_q<VT>(rec, a.A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl), b1, b2, ia);
+            top2_step(act, block_q<VT, SL>(rec, a.A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl), b1, b2, ia);
         write_state(a, reinterpret_cast<const int32_t*>(rec + 128)[lane], b1, b2, ia, res, vabs, sc.ctl);
     }
     if (sc.mode == kModeNone) return;
@@ -466,7 +489,7 @@ struct SellRingArgs {
 
 // MB = 1: up to 800 threads (24 consumer warps), 80 registers; MB = 2: two CTAs of up to
 // 17 warps per SM, 60 registers.
-template <typename VT, int MB>
+template <typename VT, int MB, bool SL>
 __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_sell_ring(SellArgs a, SellRingArgs t,
                                                                                         SweepCtl sc) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -619,7 +642,7 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
                 if (!VC_IN_BOUNDS(sc.ctl, roff + rb <= tile_bytes)) roff = 0;
             }
 #endif
-            const float qv = block_q<VT>(base + roff, A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl);
+            const float qv = block_q<VT, SL>(base + roff, A, act, lane, a.gamma, a.has_scale, a.V_in, a.S, sc.ctl);
             // the Q value replaces the block's own R entry in the ring (read above, by this lane
             // only); the proxy fence orders the write before the tile's next bulk copy
             reinterpret_cast<float*>(base + roff + 256)[act * kSellC + lane] = qv;
@@ -681,9 +704,19 @@ __global__ void __launch_bounds__(MB == 1 ? (kMaxRW + 1) * 32 : 17 * 32, MB) k_s
     finish_block<float>(sc, res, vabs, sweep);
 }
 
+static const void* ring_fn(bool bf16, int mb, bool sl) {
+    if (bf16) {
+        if (mb == 2) return sl ? (const void*)k_sell_ring<uint16_t, 2, true> : (const void*)k_sell_ring<uint16_t, 2, false>;
+        return sl ? (const void*)k_sell_ring<uint16_t, 1, true> : (const void*)k_sell_ring<uint16_t, 1, false>;
+    }
+    if (mb == 2) return sl ? (const void*)k_sell_ring<float, 2, true> : (const void*)k_sell_ring<float, 2, false>;
+    return sl ? (const void*)k_sell_ring<float, 1, true> : (const void*)k_sell_ring<float, 1, false>;
+}
+
 // Candidate launch shapes of the ring sweep, in preference order: (CTAs per SM, consumer
 // warps per CTA) x slices per tile; the ring takes the shared memory left after the
-// header and must hold the largest tile.
+// header and must hold the largest tile.  A shape must fit both instantiations (Eq. 18's
+// backup and the self-transition solve), since one plan serves both.
 int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
     (void)st;
     out.clear();
@@ -709,12 +742,17 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
         }
         for (auto& sh : shapes) {
             const int ctas = sh[0], nrw = sh[1], mb = sh[2];
-            const void* fn = bf16 ? (mb == 2 ? (const void*)k_sell_ring<uint16_t, 2> : (const void*)k_sell_ring<uint16_t, 1>)
-                                  : (mb == 2 ? (const void*)k_sell_ring<float, 2> : (const void*)k_sell_ring<float, 1>);
-            cudaFuncAttributes fa;
+            const void* fn = ring_fn(bf16, mb, false);
+            const void* fn_sl = ring_fn(bf16, mb, true);
+            cudaFuncAttributes fa, fa_sl;
             VC_CUDA(cudaFuncGetAttributes(&fa, fn));
+            VC_CUDA(cudaFuncGetAttributes(&fa_sl, fn_sl));
+            fa.numRegs = std::max(fa.numRegs, fa_sl.numRegs);
+            fa.sharedSizeBytes = std::max(fa.sharedSizeBytes, fa_sl.sharedSizeBytes);
+            fa.maxThreadsPerBlock = std::min(fa.maxThreadsPerBlock, fa_sl.maxThreadsPerBlock);
             const int dyn_max = smem_blk - (int)fa.sharedSizeBytes;
             VC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+            VC_CUDA(cudaFuncSetAttribute(fn_sl, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
             const int threads = (nrw + 1) * 32;
             if (threads > fa.maxThreadsPerBlock || (long long)threads * fa.numRegs * ctas > 65536) continue;
             if (nrw > (kSlots - 2) * TS * A) continue;  // claimed blocks stay within kSlots tiles
@@ -725,7 +763,10 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             if (ring < max_tile + 128) continue;
             const int need = qoff + qbytes + ring;
             int per_sm = 0;
+            int per_sm_sl = 0;
             VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, (size_t)need));
+            VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sl, fn_sl, threads, (size_t)need));
+            per_sm = std::min(per_sm, per_sm_sl);
             if (per_sm < 1) continue;
             CsrPlan P;
             P.sliced = true;
@@ -782,14 +823,8 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (bf16 && m->plan.minb == 2)
-            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<uint16_t, 2>, a, t, sc));
-        else if (bf16)
-            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<uint16_t, 1>, a, t, sc));
-        else if (m->plan.minb == 2)
-            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<float, 2>, a, t, sc));
-        else
-            VC_CUDA(cudaLaunchKernelEx(&cfg, k_sell_ring<float, 1>, a, t, sc));
+        void* args[] = {&a, &t, &sc};
+        VC_CUDA(cudaLaunchKernelExC(&cfg, ring_fn(bf16, m->plan.minb, sc.self_loop != 0), args));
         return VC_OK;
     }
     const int bps = m->plan.ctas_per_sm > 0 ? m->plan.ctas_per_sm : 4;
@@ -797,10 +832,14 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
     const int64_t cap = (int64_t)m->num_sms * bps;
     const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
     count_launches(1);
-    if (bf16)
-        k_sell<uint16_t><<<grid, kThreads, 0, st>>>(a, sc);
+    if (bf16 && sc.self_loop)
+        k_sell<uint16_t, true><<<grid, kThreads, 0, st>>>(a, sc);
+    else if (bf16)
+        k_sell<uint16_t, false><<<grid, kThreads, 0, st>>>(a, sc);
+    else if (sc.self_loop)
+        k_sell<float, true><<<grid, kThreads, 0, st>>>(a, sc);
     else
-        k_sell<float><<<grid, kThreads, 0, st>>>(a, sc);
+        k_sell<float, false><<<grid, kThreads, 0, st>>>(a, sc);
     VC_CUDA(cudaGetLastError());
     return VC_OK;
 }

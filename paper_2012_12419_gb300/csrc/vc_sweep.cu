@@ -97,9 +97,11 @@ __device__ __forceinline__ T post_reward(const Model& md, const Coef<T>& c, cons
 }
 
 // ---------------------------------------------------------------- implicit: pass 1
-template <int MH, typename T>
+// SL (FP32 only): also U2(x) = defer's backup with the self-transition solved.
+template <int MH, typename T, bool SL>
 __global__ void __launch_bounds__(kThreads) k_post(Model md, Coef<T> c, const T* __restrict__ V, T* __restrict__ U,
-                                                   SweepCtl sc) {
+                                                   T* __restrict__ U2, SweepCtl sc) {
+    static_assert(!SL || std::is_same<T, float>::value, "self-transition solve in FP32 sweeps only");
     if (loop_done(sc)) return;
     for (int x = blockIdx.x * kThreads + threadIdx.x; x < md.S; x += gridDim.x * kThreads) {
         Digits d;
@@ -107,13 +109,17 @@ __global__ void __launch_bounds__(kThreads) k_post(Model md, Coef<T> c, const T*
 #ifdef VC_DEBUG_BOUNDS
         if (!successors_in_range<MH>(md, x, d, sc.ctl)) continue;
 #endif
-        U[x] = post_reward<MH>(md, c, d) + c.gamma * expect_next<MH>(md, c, V, x, d);
+        const T rx = post_reward<MH>(md, c, d);
+        U[x] = rx + c.gamma * expect_next<MH>(md, c, V, x, d);
+        if constexpr (SL) U2[x] = defer_self_loop<MH>(md, c, V, x, d, rx);
     }
 }
 
 // ---------------------------------------------------------------- implicit: pass 2
-template <int MH, typename T>
-__global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict__ U, const T* __restrict__ V_in,
+// SL: defer takes U2(s) (its backup with the self-transition solved) instead of U(s).
+template <int MH, typename T, bool SL>
+__global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict__ U, const T* __restrict__ U2,
+                                                  const T* __restrict__ V_in,
                                                   T* __restrict__ V_out, int32_t* __restrict__ pi,
                                                   T* __restrict__ qgap, SweepCtl sc) {
     if (loop_done(sc)) return;
@@ -133,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
                            VC_IN_BOUNDS(sc.ctl, s + md.stride[k] - 2 >= 0 && s + md.stride[k] - 2 < md.S);
             uk[k] = f ? U[s + md.stride[k] - 2] : T(-INFINITY);
         }
-        const T u = U[s];  // defer: the post-decision state is s itself; highest index, so ties keep lower ones
+        const T u = SL ? U2[s] : U[s];  // defer: the post-decision state is s itself; highest index, so ties keep lower ones
 #pragma unroll
         for (int k = 0; k < MH; k++) {
             if (uk[k] > best) {
@@ -292,8 +298,13 @@ int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* 
     count_launches(2);
     by_h(m, [&](auto mh) {
         constexpr int MH = decltype(mh)::value;
-        k_post<MH, float><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, sc1);
-        k_max<MH, float><<<g, kThreads, 0, st>>>(m->md, m->U32, V_in, V_out, pi, qgap, sc);
+        if (sc.self_loop) {
+            k_post<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
+            k_max<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->U32, m->U32s, V_in, V_out, pi, qgap, sc);
+        } else {
+            k_post<MH, float, false><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, nullptr, sc1);
+            k_max<MH, float, false><<<g, kThreads, 0, st>>>(m->md, m->U32, nullptr, V_in, V_out, pi, qgap, sc);
+        }
         return 0;
     });
     VC_CUDA(cudaGetLastError());
@@ -309,8 +320,8 @@ int launch_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, dou
     count_launches(2);
     by_h(m, [&](auto mh) {
         constexpr int MH = decltype(mh)::value;
-        k_post<MH, double><<<g, kThreads, 0, st>>>(m->md, m->c64, V_in, m->U64, none);
-        k_max<MH, double><<<g, kThreads, 0, st>>>(m->md, m->U64, V_in, V_out, pi, qgap, sc);
+        k_post<MH, double, false><<<g, kThreads, 0, st>>>(m->md, m->c64, V_in, m->U64, nullptr, none);
+        k_max<MH, double, false><<<g, kThreads, 0, st>>>(m->md, m->U64, nullptr, V_in, V_out, pi, qgap, sc);
         return 0;
     });
     VC_CUDA(cudaGetLastError());
@@ -325,7 +336,7 @@ int launch_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, Sweep
     count_launches(2);
     by_h(m, [&](auto mh) {
         constexpr int MH = decltype(mh)::value;
-        k_post<MH, double><<<g, kThreads, 0, st>>>(m->md, m->c64, V64, m->U64, none);
+        k_post<MH, double, false><<<g, kThreads, 0, st>>>(m->md, m->c64, V64, m->U64, nullptr, none);
         k_resid64<MH><<<g, kThreads, 0, st>>>(m->md, pi, m->U64, V64, r, sc);
         return 0;
     });

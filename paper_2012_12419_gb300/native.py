@@ -35,6 +35,7 @@ VC_VAL_BF16 = 1
 VC_ITER_FP32_ONLY = 1
 VC_ITER_ACCURATE = 2
 VC_ITER_PLAIN_CORRECTION = 4
+VC_ITER_SELF_LOOP = 8
 
 FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF16}
 
@@ -289,12 +290,13 @@ class MDP:
     # ------------------------------------------------------------------------- solve
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
                       want_v64: bool = True, want_pi: bool = True, stream=None, raise_on_nonconvergence=True,
-                      accurate: bool = False, plain_correction: bool = False):
+                      accurate: bool = False, plain_correction: bool = False, self_loop: bool = False):
         """Algorithm 3 on the device.  Returns (V fp32, V64 fp64 or None, pi int32 or None, stats dict).
 
         accurate=True certifies the error rather than the residual: max|V64 - V*| <= tol / 2.
         plain_correction=True solves the refinement's correction equation by fixed-point
-        sweeps instead of BiCGSTAB."""
+        sweeps instead of BiCGSTAB.  self_loop=True runs the FP32 sweeps with each action's
+        self-transition solved exactly (VC_ITER_SELF_LOOP: same V*, fewer sweeps)."""
         dev = _dev()
         S = self.S
         if V is None:
@@ -303,7 +305,7 @@ class MDP:
         pi = torch.empty(S, dtype=torch.int32, device=dev) if want_pi else None
         st = Stats()
         flags = ((VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
-                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0))
+                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0) | (VC_ITER_SELF_LOOP if self_loop else 0))
         rc = load().vc_value_iterate(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                      flags, ctypes.byref(st), _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
@@ -441,11 +443,12 @@ class Batch:
 
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
                       stream=None, raise_on_nonconvergence=True, accurate: bool = False,
-                      plain_correction: bool = False):
+                      plain_correction: bool = False, self_loop: bool = False):
         """Returns (V fp32 [total], V64 [total] or None, pi [total] or None, list of per-instance dicts, status).
 
         accurate=True certifies every instance's error: max|V64_i - V*_i| <= tol / 2.
-        plain_correction=True solves the correction equations by fixed-point sweeps."""
+        plain_correction=True solves the correction equations by fixed-point sweeps.
+        self_loop=True runs the FP32 loop with each action's self-transition solved."""
         dev = _dev()
         if V is None:
             V = torch.zeros(self.total, dtype=torch.float32, device=dev)
@@ -453,7 +456,7 @@ class Batch:
         pi = torch.empty(self.total, dtype=torch.int32, device=dev)
         st = (BatchStats * self.n)()
         flags = ((VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
-                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0))
+                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0) | (VC_ITER_SELF_LOOP if self_loop else 0))
         rc = load().vc_value_iterate_batch(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                            flags, st, _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
