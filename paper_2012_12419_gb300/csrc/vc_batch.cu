@@ -185,8 +185,14 @@ __global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __r
                 Digits d;
                 decode<MH>(sd.md, x, d);
                 const T rx = b_reward<MH>(sd.md, coef_of<T>(sd), d);
-                Ui[x] = rx + coef_of<T>(sd).gamma * b_expect<MH>(sd.md, coef_of<T>(sd), Vi, x, d);
-                if constexpr (SL) U2[sd.off + x] = defer_self_loop<MH>(sd.md, sd.c32, Vi, x, d, rx);
+                if constexpr (SL) {
+                    float u, w;
+                    post_and_defer<MH>(sd.md, sd.c32, Vi, x, d, rx, u, w);
+                    Ui[x] = u;
+                    U2[sd.off + x] = w;
+                } else {
+                    Ui[x] = rx + coef_of<T>(sd).gamma * b_expect<MH>(sd.md, coef_of<T>(sd), Vi, x, d);
+                }
             }
         }
         __syncthreads();

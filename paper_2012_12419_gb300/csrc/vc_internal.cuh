@@ -298,16 +298,20 @@ __device__ __forceinline__ float q_self_loop(float rr, float gamma, float off, f
     return __fdiv_rn(fmaf(gamma, off, rr), fmaf(-gamma, pss, 1.0f));
 }
 
-// Defer's backup with its self-transition solved (the post-decision state of defer is s
-// itself).  The events that leave x carry probability p_move and the sum sum_move of
-// p_e V(y_e); the rest (uniformisation remainder, an arrival blocked by a full queue, the
-// departure of an empty host) stays at x, so the fixed point of
+// Pass 1 of an implicit sweep at post-decision state x with defer's self-transition solved,
+// from one set of gathers: U = R(x) + gamma E[V(next) | x] in the difference form of the
+// plain pass (E = V(x) + sum_e p_e (V(y_e) - V(x)), the self-loop probability never
+// formed), and W = defer's backup with its self-transition solved (the post-decision state
+// of defer is s itself).  The events that leave x carry probability p_move and the sum
+// sum_move of p_e V(y_e); the rest (uniformisation remainder, an arrival blocked by a full
+// queue, the departure of an empty host) stays at x, so the fixed point of
 // W = R(x) + gamma ((1 - p_move) W + sum_move) is
-// W = (R(x) + gamma sum_move) / ((1 - gamma) + gamma p_move).  Both sums are formed
+// W = (R(x) + gamma sum_move) / ((1 - gamma) + gamma p_move).  Both sums of W are formed
 // directly (no differences), so W carries a relative rounding error of a few units.
 template <int MH>
-__device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<float>& c, const float* __restrict__ V,
-                                                 int x, const Digits& d, float rx) {
+__device__ __forceinline__ void post_and_defer(const Model& md, const Coef<float>& c, const float* __restrict__ V,
+                                               int x, const Digits& d, float rx, float& U, float& W) {
+    const float vx = V[x];
     float v1[MH], v0[MH];
 #pragma unroll
     for (int k = 0; k < MH; k++) {
@@ -317,17 +321,19 @@ __device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<flo
     }
     const float va = (d.q < md.Q) ? V[x + 2] : 0.0f;
     const float vf = V[d.ph ? x - 1 : x + 1];
-    float sm = 0.0f, pm = 0.0f;
+    float acc = 0.0f, sm = 0.0f, pm = 0.0f;
 #pragma unroll
     for (int k = 0; k < MH; k++) {
         if (k < md.H) {
             const int o = d.occ[k];
             if (o == 1) {
                 const float p = c.pc[k] + c.pd[k];
+                acc += p * (v1[k] - vx);
                 sm = fmaf(p, v1[k], sm);
                 pm += p;
             } else if (o > 1) {
                 const float p1 = c.pc[k] * (float)o;
+                acc += p1 * (v1[k] - vx) + c.pd[k] * (v0[k] - vx);
                 sm = fmaf(p1, v1[k], sm);
                 sm = fmaf(c.pd[k], v0[k], sm);
                 pm += p1;
@@ -336,13 +342,16 @@ __device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<flo
         }
     }
     if (d.q < md.Q) {
+        acc += c.pa * (va - vx);
         sm = fmaf(c.pa, va, sm);
         pm += c.pa;
     }
     const float pf = d.ph ? c.pf1 : c.pf0;
+    acc += pf * (vf - vx);
     sm = fmaf(pf, vf, sm);
     pm += pf;
-    return __fdiv_rn(fmaf(c.gamma, sm, rx), fmaf(c.gamma, pm, 1.0f - c.gamma));
+    U = rx + c.gamma * (vx + acc);
+    W = __fdiv_rn(fmaf(c.gamma, sm, rx), fmaf(c.gamma, pm, 1.0f - c.gamma));
 }
 
 __device__ __forceinline__ float warp_max(float v) {

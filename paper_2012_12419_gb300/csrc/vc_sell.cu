@@ -355,21 +355,23 @@ __device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, cons
 #pragma unroll
     for (int u = 0; u < W; ++u) {
         const int c = cp[u * kSellC];
-        gv[u] = __ldg(V + c);
-        if (SL) own |= (c == self ? 1u : 0u) << u;
+        if (SL) {
+            // an own-state entry is not gathered: it enters through pss
+            const bool o = c == self;
+            own |= (o ? 1u : 0u) << u;
+            gv[u] = o ? 0.0f : __ldg(V + c);
+        } else {
+            gv[u] = __ldg(V + c);
+        }
     }
     // the values are read from shared memory only once the gathers are in flight, so
     // they hold no registers meanwhile
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-        const float v = ld_val<VT>(vp + u * kSellC);
-        if (SL) {
-            const bool o = (own >> u) & 1u;
-            pss += o ? v : 0.0f;
-            acc = fmaf(v, o ? 0.0f : gv[u], acc);
-        } else {
-            acc = fmaf(v, gv[u], acc);
-        }
+    for (int u = 0; u < W; ++u) acc = fmaf(ld_val<VT>(vp + u * kSellC), gv[u], acc);
+    if (SL) {
+        // the own-state entries' values in column order (one non-zero at most in a
+        // generated row; padding entries add zeros)
+        for (; own; own &= own - 1) pss += ld_val<VT>(vp + (__ffs(own) - 1) * kSellC);
     }
     return acc;
 }

@@ -96,6 +96,50 @@ __device__ __forceinline__ T post_reward(const Model& md, const Coef<T>& c, cons
     return c.w_occ * T(occ_sum) + c.w_q * T(d.q) + loss;
 }
 
+// Defer's backup with its self-transition solved, W of post_and_defer, computed on its
+// own: in the single-instance pass 1 this form, next to the plain expect_next, timed
+// faster (93 against 108 us per sweep of the 2.5 M-state instance) than the fused one,
+// which the batched pass uses.
+template <int MH>
+__device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<float>& c, const float* __restrict__ V,
+                                                 int x, const Digits& d, float rx) {
+    float v1[MH], v0[MH];
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        const int o = d.occ[k];
+        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : 0.0f;
+        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : 0.0f;
+    }
+    const float va = (d.q < md.Q) ? V[x + 2] : 0.0f;
+    const float vf = V[d.ph ? x - 1 : x + 1];
+    float sm = 0.0f, pm = 0.0f;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o == 1) {
+                const float p = c.pc[k] + c.pd[k];
+                sm = fmaf(p, v1[k], sm);
+                pm += p;
+            } else if (o > 1) {
+                const float p1 = c.pc[k] * (float)o;
+                sm = fmaf(p1, v1[k], sm);
+                sm = fmaf(c.pd[k], v0[k], sm);
+                pm += p1;
+                pm += c.pd[k];
+            }
+        }
+    }
+    if (d.q < md.Q) {
+        sm = fmaf(c.pa, va, sm);
+        pm += c.pa;
+    }
+    const float pf = d.ph ? c.pf1 : c.pf0;
+    sm = fmaf(pf, vf, sm);
+    pm += pf;
+    return __fdiv_rn(fmaf(c.gamma, sm, rx), fmaf(c.gamma, pm, 1.0f - c.gamma));
+}
+
 // ---------------------------------------------------------------- implicit: pass 1
 // SL (FP32 only): also U2(x) = defer's backup with the self-transition solved.
 template <int MH, typename T, bool SL>
