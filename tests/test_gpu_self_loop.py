@@ -182,3 +182,41 @@ def test_batched_self_loop_against_the_oracle():
         if p["gamma"] == 0.99:
             assert stats[i]["sweeps"] < res[False][2][i]["sweeps"]
     b.close()
+
+
+def test_edge_cases_one_state_and_no_self_transitions():
+    """A one-state MDP (every row a self-transition) reaches max_a R_a / (1 - gamma) in one
+    sweep; rows without self-transitions give Eq. 18's sweep bit for bit."""
+    native = native_or_skip()
+    import torch
+
+    dev = "cuda"
+    g = 0.95
+    Rr = np.array([0.3, 1.7, -2.0], np.float32)
+    m = native.MDP.from_csr(1, 3, torch.tensor([0, 1, 2, 3], dtype=torch.int64, device=dev),
+                            torch.zeros(3, dtype=torch.int32, device=dev), torch.ones(3, device=dev),
+                            torch.tensor(Rr, device=dev), g)
+    W = _sl_sweep(m, torch.zeros(1, device=dev)).cpu().numpy()
+    assert W[0] == np.float32(np.float32(1.7) / (np.float32(1.0) - np.float32(g)))
+    m.close()
+    # no self-transitions: a ring of states, each row moving to the next states only
+    S, A = 300, 3
+    rng = np.random.default_rng(9)
+    rp, col, val, R = [0], [], [], []
+    for s in range(S):
+        for a in range(A):
+            c = sorted({(s + 1 + int(k)) % S for k in rng.integers(0, 5, size=3)})
+            w = rng.random(len(c)) + 0.1
+            col += c
+            val += (w / w.sum()).tolist()
+            rp.append(len(col))
+            R.append(rng.uniform(-1, 1))
+    args = (torch.tensor(rp, dtype=torch.int64, device=dev), torch.tensor(col, dtype=torch.int32, device=dev),
+            torch.tensor(val, dtype=torch.float32, device=dev), torch.tensor(R, dtype=torch.float32, device=dev))
+    m = native.MDP.from_csr(S, A, *args, 0.9)
+    V0 = _seeded_V(S, 8, 5.0)
+    Vo = torch.empty_like(V0)
+    m.bellman32(V0, Vo)
+    torch.cuda.synchronize()
+    assert torch.equal(_sl_sweep(m, V0), Vo)
+    m.close()
