@@ -36,3 +36,17 @@ def test_library_targets_sm103a_only():
         return  # cuobjdump unavailable: nothing to check
     archs = set(re.findall(r"sm_(\d+a?)", out.stdout))
     assert archs == {"103a"}, archs
+
+
+def test_binding_constants_equal_the_header():
+    """Every integer #define of the header that the binding also names has the same value
+    (status codes, storage forms, value types, iteration flags)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = {k: int(v) for k, v in re.findall(r"^#define\s+(VC_\w+)\s+(-?\d+)\s*$", src, flags=re.M)}
+    shared = [k for k in defs if hasattr(native, k)]
+    assert {"VC_OK", "VC_ITER_FP32_ONLY", "VC_ITER_SELF_LOOP", "VC_SLICED"} <= set(shared)
+    for k in shared:
+        assert getattr(native, k) == defs[k], k
+    # the iteration flags are distinct bits
+    flags = [defs[k] for k in defs if k.startswith("VC_ITER_")]
+    assert all(f > 0 and f & (f - 1) == 0 for f in flags) and len(set(flags)) == len(flags)
