@@ -9,7 +9,8 @@ Two layers:
 
 * ``vc_oracle.c`` (loaded through ctypes): successor enumeration of the model, explicit
   CSR construction, Jacobi value iteration (with Eq. 18's backup, and with each action's
-  self-transition solved exactly), single-state backups, policies, policy evaluation,
+  self-transition solved exactly, also inside Algorithm 4's blocks of consecutive states),
+  single-state backups, policies, policy evaluation,
   analytic transition derivatives and a bfloat16 rounding routine.
 * numpy helpers below for tiny problems: dense policy evaluation by a linear solve,
   exhaustive policy enumeration, value iteration on dense random MDPs and the
@@ -101,6 +102,8 @@ def lib():
             L.or_value_iteration_sl.restype = ctypes.c_int
             L.or_vi_csr_sl.argtypes = [i64, i32, vp, vp, vp, vp, dbl, dbl, i64, vp, vp, vp]
             L.or_vi_csr_sl.restype = ctypes.c_int
+            L.or_block_vi_csr_sl.argtypes = [i64, i32, vp, vp, vp, vp, dbl, i64, i32, dbl, i64, vp, vp, vp]
+            L.or_block_vi_csr_sl.restype = ctypes.c_int
             L.or_policy_csr.argtypes = [i64, i32, vp, vp, vp, vp, dbl, vp, vp, vp]
             L.or_bf16_rne.argtypes = [dbl]
             L.or_bf16_rne.restype = ctypes.c_uint16
@@ -362,6 +365,27 @@ def vi_csr_self_loop(S, A, row_ptr, col, val, R, gamma, tol=1e-12, max_sweeps=10
                             float(tol), int(max_sweeps), _ptr(V), _ptr(sweeps), _ptr(res))
     if st != 0 and strict:
         raise RuntimeError("oracle CSR value iteration did not converge")
+    return V, int(sweeps[0])
+
+
+def block_vi_csr_self_loop(S, A, row_ptr, col, val, R, gamma, tile, passes, tol=1e-12, max_sweeps=10**6, V0=None,
+                           strict=True):
+    """Algorithm 4's in-block iteration over consecutive blocks of `tile` states, `passes`
+    local passes of the self-transition-solved backup per global sweep (successors in the
+    state's block from the previous local pass, others from the previous global iterate).
+    Returns (V, global sweeps)."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    R = np.ascontiguousarray(R, np.float64)
+    V = np.zeros(S, np.float64) if V0 is None else np.array(V0, np.float64, copy=True)
+    sweeps = np.zeros(1, np.int64)
+    res = np.zeros(1, np.float64)
+    st = lib().or_block_vi_csr_sl(int(S), int(A), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(R), float(gamma),
+                                  int(tile), int(passes), float(tol), int(max_sweeps), _ptr(V), _ptr(sweeps),
+                                  _ptr(res))
+    if st != 0 and strict:
+        raise RuntimeError("oracle block value iteration did not converge")
     return V, int(sweeps[0])
 
 

@@ -673,6 +673,73 @@ int or_vi_csr_sl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* co
     return status;
 }
 
+/*
+ * Block iteration (Algorithm 4's in-block "episodes") on an explicit CSR MDP, with each
+ * action's self-transition solved as in or_vi_csr_sl.  States are cut into consecutive
+ * blocks of `tile` states.  In one global sweep every block runs `passes` local Jacobi
+ * passes of the self-transition-solved backup: a successor inside the state's own block
+ * takes the block's values from the previous local pass (the previous iterate in the first
+ * pass), a successor outside it the previous global iterate.  passes = 1 is or_vi_csr_sl's
+ * sweep; tile = 1 leaves only the state itself in its block, which the backup already
+ * solves; one block of all S states with p passes is p sweeps of or_vi_csr_sl.  Stops
+ * after the first global sweep whose change max_s |V^{k+1}(s) - V^k(s)| is below tol.
+ */
+int or_block_vi_csr_sl(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const double* val,
+                       const double* R, double gamma, int64_t tile, int32_t passes, double tol, int64_t max_sweeps,
+                       double* V, int64_t* sweeps_out, double* residual_out) {
+    double* Vold = (double*)malloc(sizeof(double) * S);
+    double* W = (double*)malloc(sizeof(double) * S);
+    double* Wn = (double*)malloc(sizeof(double) * S);
+    int64_t k = 0;
+    double res = INFINITY;
+    int status = 1;
+    if (tile < 1) tile = 1;
+    if (passes < 1) passes = 1;
+    while (k < max_sweeps) {
+        memcpy(Vold, V, sizeof(double) * S);
+        memcpy(W, V, sizeof(double) * S);
+        for (int32_t pass = 0; pass < passes; pass++) {
+            for (int64_t s = 0; s < S; s++) {
+                const int64_t blk = s / tile;
+                double b = -INFINITY;
+                for (int a = 0; a < A; a++) {
+                    int64_t r = s * A + a;
+                    if (R[r] == -INFINITY) continue;
+                    double off = 0.0, pss = 0.0;
+                    for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) {
+                        const int64_t c = col[j];
+                        if (c == s)
+                            pss += val[j];
+                        else
+                            off += val[j] * (c / tile == blk ? W[c] : Vold[c]);
+                    }
+                    double qv = (R[r] + gamma * off) / (1.0 - gamma * pss);
+                    if (qv > b) b = qv;
+                }
+                Wn[s] = b;
+            }
+            memcpy(W, Wn, sizeof(double) * S);
+        }
+        res = 0.0;
+        for (int64_t s = 0; s < S; s++) {
+            double d = fabs(W[s] - Vold[s]);
+            if (d > res) res = d;
+        }
+        memcpy(V, W, sizeof(double) * S);
+        k++;
+        if (res < tol) {
+            status = 0;
+            break;
+        }
+    }
+    free(Vold);
+    free(W);
+    free(Wn);
+    *sweeps_out = k;
+    *residual_out = res;
+    return status;
+}
+
 void or_policy_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t* col, const double* val,
                    const double* R, double gamma, const double* V, int32_t* pi, double* qgap) {
     for (int64_t s = 0; s < S; s++) {

@@ -130,3 +130,56 @@ def test_model_form_reaches_the_pinned_optimum_in_fewer_sweeps():
         assert np.array_equal(Va, Vb)
     _, n_plain, _ = oracle.value_iteration(p, tol=1e-12)
     assert n < n_plain
+
+
+def _random_csr_with_self_loops(S, A, seed):
+    rng = np.random.default_rng(seed)
+    P = rng.random((A, S, S)) * (rng.random((A, S, S)) < 0.2)
+    for a in range(A):
+        P[a] += np.diag(rng.random(S))
+        P[a, np.arange(S), (np.arange(S) + 1) % S] += 0.05
+        P[a] /= P[a].sum(1, keepdims=True)
+    R = rng.normal(size=(S, A))
+    R[rng.random((S, A)) < 0.2] = -np.inf
+    R[:, 0] = rng.normal(size=S)
+    return P, R
+
+
+def test_block_iteration_reduces_to_the_self_transition_sweeps():
+    """passes = 1, or blocks of one state, give the sweeps of vi_csr_self_loop bit for bit;
+    one block of every state with p passes is p of those sweeps."""
+    S, A, g = 50, 3, 0.93
+    P, R = _random_csr_with_self_loops(S, A, 4)
+    rp, col, val, Rr = _dense_to_csr(P, R)
+    V0 = np.random.default_rng(1).normal(size=S)
+    kw = dict(tol=1e-300, V0=V0, strict=False)
+    for k in (1, 4):
+        ref, _ = oracle.vi_csr_self_loop(S, A, rp, col, val, Rr, g, max_sweeps=k, **kw)
+        a, _ = oracle.block_vi_csr_self_loop(S, A, rp, col, val, Rr, g, 16, 1, max_sweeps=k, **kw)
+        b, _ = oracle.block_vi_csr_self_loop(S, A, rp, col, val, Rr, g, 1, 3, max_sweeps=k, **kw)
+        assert np.array_equal(a, ref) and np.array_equal(b, ref)
+    for p in (2, 5):
+        ref, _ = oracle.vi_csr_self_loop(S, A, rp, col, val, Rr, g, max_sweeps=p, **kw)
+        c, _ = oracle.block_vi_csr_self_loop(S, A, rp, col, val, Rr, g, S, p, max_sweeps=1, **kw)
+        assert np.array_equal(c, ref)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_block_iteration_reaches_the_brute_force_optimum(seed):
+    S, A, g = 6, 3, 0.9
+    P, R = _random_dense(S, A, seed, self_weight=1.0)
+    Vbf = oracle.brute_force_optimum(P, R, g)
+    rp, col, val, Rr = _dense_to_csr(P, R)
+    V, _ = oracle.block_vi_csr_self_loop(S, A, rp, col, val, Rr, g, 3, 4, tol=1e-14)
+    assert np.max(np.abs(V - Vbf)) <= 1e-11 * np.max(np.abs(Vbf))
+
+
+def test_block_iteration_on_the_model_needs_fewer_global_sweeps():
+    p = inputs.make_params(3, 3, 4, 0.95, seed=0)
+    S, A = oracle.num_states(p), oracle.num_actions(p)
+    rp, col, val, Rr = oracle.build_csr(p)
+    Vstar = oracle.solve(p, tol=1e-13)[0]
+    _, n1 = oracle.vi_csr_self_loop(S, A, rp, col, val, Rr, p["gamma"], tol=1e-10)
+    V, n4 = oracle.block_vi_csr_self_loop(S, A, rp, col, val, Rr, p["gamma"], 32, 4, tol=1e-10)
+    assert n4 < n1
+    assert np.max(np.abs(V - Vstar)) <= 1e-7
