@@ -366,7 +366,8 @@ def run_batched(args):
         out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                            "traffic": None, "peak_source": f"{src} hbm_gbs",
                            "kernel": "k_bpost+k_bmax (one graph pass = one sweep of every instance)",
-                           "bytes_per_launch": nbytes, "launch_us": tune_sweep_ms * 1e3}
+                           "bytes_per_launch": nbytes, "launch_us": tune_sweep_ms * 1e3,
+                           "ncu_sol": batched_sol()}
     if rank == 0 and not args.no_extras:
         out["e2e"] = batched_e2e(args, ps, nnz, native, torch)
         if world == 1:
@@ -599,17 +600,35 @@ TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_494_589_696,
                  ("large", "csr_f32", False, True): 1_196_799_488}
 
 
-def measured_traffic(args, info):
+# ncu speed-of-light figures of the batched loop's pass-1 kernel on the 512-instance batch
+# (profiles/k_bpost_batched_pass1.md), attached to the batched roofline while the sources
+# hash as captured: that sweep is bound by gather latency at half occupancy, not by a
+# memory roof, and these say how far each unit is from its own peak.
+BATCH_SOL_SOURCES = ("vc_batch.cu", "vc_internal.cuh")
+BATCH_SOL_SHA = "59b8815b5b88ffffad5427db8f580ac8a2b8a2760184aeb3b5ca7b536de4db46"
+BATCH_SOL = {"kernel": "k_bpost<5, float, false>", "dram_pct": 7.9, "l2_pct": 10.5, "sm_pct": 55.2,
+             "warps_active_pct": 46.9, "registers_per_thread": 63, "top_stall": "long scoreboard (V gathers)"}
+
+
+def _sources_sha(names):
     import hashlib
 
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2012_12419_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(args, info):
     key = (args.workload, args.form, args.padded, bool(info["csr_sliced"]))
     if key not in TRAFFIC_BYTES or not info["csr_pipelined"]:
         return None
-    h = hashlib.sha256()
-    for name in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, "paper_2012_12419_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
-    return TRAFFIC_BYTES[key] if h.hexdigest() == TRAFFIC_SOURCE_SHA else None
+    return TRAFFIC_BYTES[key] if _sources_sha(TRAFFIC_SOURCES) == TRAFFIC_SOURCE_SHA else None
+
+
+def batched_sol():
+    return dict(BATCH_SOL) if _sources_sha(BATCH_SOL_SOURCES) == BATCH_SOL_SHA else None
 
 
 def roofline(m, info, args, V, dev, stream):
