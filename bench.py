@@ -418,7 +418,7 @@ def batched_e2e(args, ps, nnz, native, torch):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b = native.Batch(ps)
-        _, V64, pi, st, _ = b.value_iterate(tol=args.tol)
+        _, V64, pi, st, _ = b.value_iterate(tol=args.tol, self_loop=args.self_loop)
         hv.copy_(V64, non_blocking=True)
         hp.copy_(pi, non_blocking=True)
         torch.cuda.synchronize()
@@ -681,7 +681,7 @@ def e2e(args, p, native, torch, nnz):
         m = native.MDP.build(p, fmt=args.form, padded=args.padded, sliced=args.sliced)
         torch.cuda.synchronize()
         tb = time.perf_counter()
-        V, V64, pi, st = m.value_iterate(tol=args.tol)
+        V, V64, pi, st = m.value_iterate(tol=args.tol, self_loop=args.self_loop)
         hv.copy_(V64, non_blocking=True)
         hp.copy_(pi, non_blocking=True)
         torch.cuda.synchronize()
