@@ -11,6 +11,9 @@ against V*.
   than Eq. 18's backup on the same handle.
 * A user CSR whose rows contain self-transitions: the iterate after k sweeps equals the
   oracle's CSR form of the iteration within the bound, and the solve is certified.
+* The batch's self-transition loop graph against every instance's oracle sweep and optimum.
+* Edge cases: a one-state MDP reaches max_a R_a / (1 - gamma) in one FP32 sweep exactly;
+  rows without self-transitions give Eq. 18's sweep bit for bit.
 
 FP32 bound of one sweep (derived from the arithmetic): the numerator R + gamma off takes at
 most n + 2 roundings (n stored entries, FP32 probabilities within one rounding of the FP64
