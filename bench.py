@@ -209,15 +209,8 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {
-            "workload": WORKLOAD_DESC[args.workload],
-            "form": args.form + ("+padded" if args.padded else "") + ("+sliced" if args.sliced else ""),
-            "tol": args.tol, "nnz_logical_per_sweep": nnz, "nnz_stored_per_sweep": int(info["nnz_stored"]),
-            "parallelism": "replicas" if world > 1 else "single",
-            "l2": "256 MiB buffer written between steps, outside the step events",
-            "step": "V=0 -> FP32 sweeps -> argmax -> FP64 policy evaluation -> FP64 Bellman certificate",
-            "sweep": "self-transition solved" if args.self_loop else "Eq. 18 backup",
-        },
+        "config": step_config(args, nnz, world),
+        "layout": layout_of(args, info),
         "time_to_residual_ms": statistics.median(ms),
         "sweeps_per_step": statistics.median(sweeps),
         "fp32_correction_products_per_step": statistics.median([s["eval_sweeps"] for s in stats]),
@@ -244,11 +237,52 @@ def run_native(args):
             out["self_loop"] = self_loop_comparison(args, p, m, V, native, torch, dev, stream)
             if world == 1 and args.workload == "large":
                 out["comparisons"] = comparisons(args, native, torch, dev, stream)
+                out["batched"] = batched_record(args, native, torch, dev, stream)
         print(json.dumps(out))
     m.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def step_config(args, nnz_logical, world):
+    """The workload and step definition, identical in both arms (the reference arm times the
+    oracle on the same workload, so nothing here names an implementation's storage)."""
+    return {
+        "workload": WORKLOAD_DESC[args.workload],
+        "form": args.form + ("+padded" if args.padded else "") + ("+sliced" if args.sliced else ""),
+        "tol": args.tol, "nnz_logical_per_sweep": int(nnz_logical),
+        "parallelism": "replicas" if world > 1 else "single",
+        "l2": "256 MiB buffer written between steps, outside the step events",
+        "step": "V=0 -> FP32 sweeps -> argmax -> FP64 policy evaluation -> FP64 Bellman certificate",
+        "sweep": "self-transition solved" if args.self_loop else "Eq. 18 backup",
+    }
+
+
+def layout_of(args, info):
+    """What the timed sweep streams: the stored matrix and, when the sweep runs on it, the
+    sliced copy (which drops infeasible rows and pads each 32-state block to its longest row)."""
+    sliced = bool(info["csr_sliced"])
+    nnz_stored = int(info["nnz_stored"])
+    d = {"nnz_stored_matrix": nnz_stored, "nnz_streamed_per_sweep": int(info["nnz_sliced"]) if sliced else nnz_stored,
+         "stored_bytes_per_sweep": int(info["sweep_bytes"])}
+    if args.form == "implicit":
+        d["streamed"] = "nothing per transition: successors generated in registers from the state code"
+    elif sliced:
+        d["streamed"] = (f"sliced copy of the {'padded' if args.padded else 'canonical'} CSR ({nnz_stored:,} "
+                         f"entries): infeasible rows dropped, each 32-state block padded to its longest row, "
+                         f"{int(info['nnz_sliced']):,} entries")
+    else:
+        d["streamed"] = f"{'padded' if args.padded else 'canonical'} CSR, {nnz_stored:,} entries"
+    return d
+
+
+def algorithmic_sweep_bytes(S, A, nnz_logical, bf16):
+    """Algorithmic HBM bytes of one explicit Bellman sweep of the logical (canonical) work:
+    each non-zero successor's value and column, each (state, action) row's offset and
+    reward (and BF16 row scale), V read and written once."""
+    v = 2 if bf16 else 4
+    return nnz_logical * (v + 4) + S * A * (8 + 4 + (4 if bf16 else 0)) + 8 * S
 
 
 # --------------------------------------------------------------------------- batched arm
@@ -380,6 +414,55 @@ def run_batched(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batched_record(args, native, torch, dev, stream, steps: int = 5):
+    """The 512-instance batched workload inside the default run: one graph-captured solve of
+    every instance to its certified residual, timed as the batched arm times it (L2 flushed
+    between steps, events on the stream), with the per-instance plain-FP32 comparison and
+    the self-transition variant."""
+    from paper_2012_12419_gb300 import inputs
+
+    ps = inputs.batch_params(512, seed=2)
+    nnz = [_implicit_nnz(native, p) for p in ps]
+    b = native.Batch(ps)
+    tune_ms = b.autotune(sweeps=20)
+    binfo = b.info()
+    V = torch.zeros(b.total, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        V.zero_()
+        return b.value_iterate(V, tol=args.tol)[3]
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    units = float(sum(n * x["sweeps"] for st in stats for n, x in zip(nnz, st)))
+    last = stats[-1]
+    out = {
+        "workload": WORKLOAD_DESC["batched"], "value": units / (sum(ms) / 1e3), "unit": UNIT, "steps": steps,
+        "ms_per_step": sum(ms) / steps, "time_to_residual_ms": statistics.median(ms),
+        "states": int(binfo["total_states"]), "certified": all(x["certified"] == 1 for x in last),
+        "sweeps_max": max(x["sweeps"] for x in last), "sweeps_median": statistics.median([x["sweeps"] for x in last]),
+        "residual64": max(x["residual64"] for x in last),
+        "schedule": {k: int(binfo[k]) for k in ("tile_states", "blocks_per_sm", "grid", "tiles")},
+        "autotuned_sweep_ms": tune_ms / 20,
+    }
+    out["vs_per_instance"] = batched_vs_per_instance(args, ps, b, native, torch, dev, stream)
+    out["self_loop"] = batched_self_loop(args, b, torch, dev, stream)
+    b.close()
+    return out
 
 
 def batched_self_loop(args, b, torch, dev, stream):
@@ -591,19 +674,19 @@ def comparisons(args, native, torch, dev, stream):
     return out
 
 
-# DRAM bytes (read + write) of one sweep-kernel launch from an ncu capture of this exact
-# kernel source (profiles/k_sell_ring_large_padded.md, k_sell_ring_large_canonical.md);
-# reported only while the sources hash the same, since a changed kernel voids the counters.
+# DRAM bytes (read + write) per launch of the headline sweep kernels, from one ncu capture
+# of this exact kernel source each (large workload, padded and canonical CSR with the sliced
+# copy); reported only while the sources hash the same, since a changed kernel voids them.
 TRAFFIC_SOURCES = ("vc_sell.cu", "vc_internal.cuh", "vc_ptx.cuh")
 TRAFFIC_SOURCE_SHA = "42bb77e358a1625af889be07cce81f50d1f2cee76c39c61bfea13f8ae3bf9b2b"
 TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_494_589_696,
                  ("large", "csr_f32", False, True): 1_196_799_488}
 
 
-# ncu speed-of-light figures of the batched loop's pass-1 kernel on the 512-instance batch
-# (profiles/k_bpost_batched_pass1.md), attached to the batched roofline while the sources
-# hash as captured: that sweep is bound by gather latency at half occupancy, not by a
-# memory roof, and these say how far each unit is from its own peak.
+# ncu speed-of-light figures of the batched loop's pass-1 kernel on the 512-instance batch,
+# attached to the batched roofline while the sources hash as captured: that sweep is bound
+# by gather latency at half occupancy, not by a memory roof, and these say how far each
+# unit is from its own peak.
 BATCH_SOL_SOURCES = ("vc_batch.cu", "vc_internal.cuh")
 BATCH_SOL_SHA = "59b8815b5b88ffffad5427db8f580ac8a2b8a2760184aeb3b5ca7b536de4db46"
 BATCH_SOL = {"kernel": "k_bpost<5, float, false>", "dram_pct": 7.9, "l2_pct": 10.5, "sm_pct": 55.2,
@@ -620,11 +703,15 @@ def _sources_sha(names):
     return h.hexdigest()
 
 
-def measured_traffic(args, info):
+def captured_traffic(args, info):
+    """(bytes per launch, provenance) of the timed kernel from its ncu capture, or (None, why)."""
     key = (args.workload, args.form, args.padded, bool(info["csr_sliced"]))
     if key not in TRAFFIC_BYTES or not info["csr_pipelined"]:
-        return None
-    return TRAFFIC_BYTES[key] if _sources_sha(TRAFFIC_SOURCES) == TRAFFIC_SOURCE_SHA else None
+        return None, "no capture of this configuration"
+    sha = _sources_sha(TRAFFIC_SOURCES)
+    if sha != TRAFFIC_SOURCE_SHA:
+        return None, "kernel sources changed since the capture"
+    return TRAFFIC_BYTES[key], f"ncu dram__bytes_read.sum + dram__bytes_write.sum, sources sha256 {sha[:16]}"
 
 
 def batched_sol():
@@ -632,7 +719,11 @@ def batched_sol():
 
 
 def roofline(m, info, args, V, dev, stream):
-    """Average launch time of the FP32 sweep kernel, timed with events on its stream."""
+    """Average launch time of the FP32 sweep kernel, timed with events on its stream.
+
+    frac = algorithmic bytes of the logical work (every non-zero successor once, the
+    canonical count) / launch time / measured HBM copy bandwidth; stored_frac = the bytes
+    the timed layout actually stores per sweep over the same time."""
     import torch
 
     hbm, src = peaks()
@@ -652,14 +743,26 @@ def roofline(m, info, args, V, dev, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     avg_s = e0.elapsed_time(e1) / 1e3 / n
-    traffic = measured_traffic(args, info)
-    achieved = info["sweep_bytes"] / avg_s / 1e9
     implicit = args.form == "implicit"
+    S, Aa = int(info["S"]), int(info["A"])
+    if implicit:
+        alg = 8 * S  # V read and written; no matrix
+    else:
+        alg = algorithmic_sweep_bytes(S, Aa, int(info["nnz_logical"]), args.form == "csr_bf16")
+    traffic, provenance = captured_traffic(args, info)
+    achieved = alg / avg_s / 1e9
+    stored = info["sweep_bytes"] / avg_s / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_post+k_max" if implicit else (
+            "traffic": traffic, "traffic_source": provenance, "peak_source": f"{src} hbm_gbs",
+            "kernel": "k_post+k_max" if implicit else (
                 ("k_sell_ring" if info["csr_pipelined"] else "k_sell") if info["csr_sliced"]
                 else ("k_csr_tma" if info["csr_pipelined"] else "k_csr_direct")),
-            "bytes_per_launch": int(info["sweep_bytes"]), "launch_us": avg_s * 1e6,
+            "bytes_per_launch": int(alg),
+            "bytes_definition": "8 S (V in and out)" if implicit else
+            "logical nnz x (value + 4 B column) + S A x (8 B offset + 4 B reward [+ 4 B BF16 scale]) + 8 S",
+            "launch_us": avg_s * 1e6,
+            "stored_bytes_per_launch": int(info["sweep_bytes"]), "stored_achieved": stored,
+            "stored_frac": stored / hbm,
             "plan": {k: int(info[k]) for k in ("csr_pipelined", "csr_tile_states", "csr_stages", "csr_ctas_per_sm",
                                                 "csr_smem_bytes")}}
 
@@ -883,8 +986,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "strong" if args.workload == "batched" else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD_DESC[args.workload],
-                   "form": f"oracle enumeration (FP64, {cores} host threads)", "tol": args.tol},
+        "config": (step_config(args, oracle.csr_nnz(p), int(os.environ.get("WORLD_SIZE", "1")))
+                   if args.workload != "batched" else {"workload": WORKLOAD_DESC[args.workload], "tol": args.tol}),
+        "reference_form": f"FP64 oracle: successor enumeration and Jacobi backups on {cores} host threads",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: Jacobi backups of every {stride}th state of the "
                                    + ("512 instances" if args.workload == "batched" else "instance")

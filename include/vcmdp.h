@@ -154,8 +154,10 @@ int64_t vc_kernel_launches(void);
 int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out);
 
 /*
- * Build an instance from an arbitrary explicit MDP in CSR form (device pointers, copied
- * into the handle): row r = s*A + a spans [row_ptr[r], row_ptr[r+1]) of col/val; R[r]
+ * Build an instance from an arbitrary explicit MDP in CSR form: the transition law
+ * P(s'|s,a) and expected reward r(s,a) of the Bellman equation (Section V-G, Eq. 18) given
+ * as data instead of generated from Eq. 10-16, so any finite MDP runs through the same
+ * sweeps (device pointers, copied into the handle): row r = s*A + a spans [row_ptr[r], row_ptr[r+1]) of col/val; R[r]
  * is its expected reward, -INFINITY marking an infeasible action.  val_dtype is
  * VC_VAL_F32 (float) or VC_VAL_BF16 (uint16 bf16 bit patterns); row_scale (nullable,
  * [S*A] float) multiplies a row's sum (BF16 only; NULL = 1/sum of the stored values).
@@ -250,15 +252,19 @@ int vc_bellman32(vc_mdp* m, const float* V, float* V_out, int32_t* pi, float* qg
  * synchronisation an allocation can cause, or code running while another library captures
  * the stream.  The paper has no counterpart; it is an interface convenience.
  *   V: [S] float in; V_out: [S] float out (a different buffer); pi: [S] int32 argmax
- *   (nullable); residual: ONE float on the device (nullable) receiving max|V_out - V|.
+ *   (nullable); residual: ONE float on the device (nullable) receiving max|V_out - V|
+ *   (+INFINITY if any difference is NaN).
  * Results equal vc_bellman32 on a VC_IMPLICIT handle of the same model.
  * Scratch: the post-decision values live in a static device array of 1,048,576 floats
- * (4 MiB) plus a residual word, present on every GPU that loads the library until the
- * process exits; S above 1,048,576 returns VC_ERR_ARG.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that device current:
+ * (4 MiB) plus a residual word and a 1.3 KB control block, present on every GPU that
+ * loads the library until the process exits; S above 1,048,576 returns VC_ERR_ARG.  The
+ * first call on each device looks up the arrays' device addresses (cudaGetSymbolAddress)
+ * with that device current:
  * make that first call before any stream capture.  All calls on a device share the
  * array, so calls that overlap on the GPU (different streams, or different host threads)
  * race and must be ordered by the caller.  The residual word is cleared on every call.
+ * In the bounds-checking build (libvcmdp_debug.so) the call also synchronises `stream`
+ * and returns VC_ERR_CUDA if a device bounds check failed.
  */
 int vc_bellman32_noalloc(const vc_params* p, const float* V, float* V_out, int32_t* pi, float* residual,
                          void* stream);
@@ -348,7 +354,10 @@ typedef struct vc_grad_stats {
 } vc_grad_stats;
 
 /*
- * Adjoint gradient of J = rho . V_pi for a handle built from model parameters:
+ * Adjoint gradient of J = rho . V_pi for a handle built from model parameters.  The paper
+ * differentiates nothing; this is Eq. 18 with the action fixed to pi (the policy-evaluation
+ * equation V = R_pi + gamma P_pi V of Section V-G) differentiated in the model parameters
+ * of Eq. 12-16 (rates and reward weights), by the adjoint method:
  *     dJ/dtheta_i = lam . (dR_pi/dtheta_i + gamma (dP_pi/dtheta_i) V),
  *     (I - gamma P_pi)^T lam = rho,
  * theta = (lambda, mu_1..mu_H, delta_1..delta_H, f, w_occ, w_loss, w_q), 2H+5 entries.
@@ -366,6 +375,15 @@ typedef struct vc_grad_stats {
  */
 int vc_value_grad(vc_mdp* m, const double* V, const int32_t* pi, const double* rho, double* dJ_dtheta,
                   double* lambda_out, double tol, int64_t max_sweeps, vc_grad_stats* stats, void* stream);
+
+/*
+ * The objective of vc_value_grad, J = rho . V = sum_s rho[s] V[s], in FP64 on the device
+ * (the initial-distribution-weighted value whose gradient vc_value_grad returns; the paper
+ * has no objective of this form).  V, rho: [S] double device arrays; J: ONE double on the
+ * device, written on `stream` (enqueued only).  One block sums in a fixed order, so the
+ * result is reproducible bit for bit.  VC_ERR_ARG for NULL pointers or S < 1.
+ */
+int vc_objective(const double* V, const double* rho, int64_t S, double* J, void* stream);
 
 /* ------------------------------------------------------------------ batched solves */
 

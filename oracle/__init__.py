@@ -539,6 +539,38 @@ def sweep_states(p: dict, V: np.ndarray, Vn: np.ndarray, s0: int, s1: int, step:
     return int(L.or_sweep_states(ctypes.byref(_params(p)), _ptr(V), _ptr(Vn), int(s0), int(s1), int(step)))
 
 
+def backup_range(p: dict, V: np.ndarray, s0: int, s1: int, Vn: np.ndarray, pi: np.ndarray, gap: np.ndarray):
+    """Backups of states s0 .. s1-1 of V into Vn, pi, gap (each indexed like V), by the
+    single-state backup; the C routine runs outside the Python lock."""
+    L = lib()
+    L.or_backup_range.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_backup_range.restype = None
+    for a, t in ((V, np.float64), (Vn, np.float64), (pi, np.int32), (gap, np.float64)):
+        if a.dtype != t or not a.flags.c_contiguous:
+            raise ValueError("backup_range wants contiguous float64 V, Vn, gap and int32 pi")
+    L.or_backup_range(ctypes.byref(_params(p)), _ptr(V), int(s0), int(s1), _ptr(Vn), _ptr(pi), _ptr(gap))
+
+
+def backup_all(p: dict, V, threads: int | None = None):
+    """Bellman backup, argmax and Q-gap of every state of V, on contiguous state ranges
+    split over host threads (Jacobi: each state reads only V, so the result does not
+    depend on the split).  Returns (Vn, pi, gap)."""
+    V = np.ascontiguousarray(V, np.float64)
+    S = len(V)
+    Vn = np.empty(S, np.float64)
+    pi = np.empty(S, np.int32)
+    gap = np.empty(S, np.float64)
+    n = max(1, min(threads or os.cpu_count() or 1, S))
+    cuts = [S * i // n for i in range(n + 1)]
+    ts = [threading.Thread(target=backup_range, args=(p, V, cuts[i], cuts[i + 1], Vn, pi, gap)) for i in range(n)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return Vn, pi, gap
+
+
 def grad_contract(p: dict, V, pi, lam) -> np.ndarray:
     """sum_s lam[s] (dR/dtheta + gamma dP/dtheta V) over the policy's rows, in C (any size)."""
     L = lib()

@@ -550,6 +550,24 @@ void or_policy(const or_params* p, const double* V, int32_t* pi, double* qgap) {
 }
 
 /*
+ * Backups of the states s0 .. s1-1 from V (Algorithm 3, steps 2 and 4 for a range of
+ * states): Vn[s] (nullable) the best Q value, pi[s] (nullable) its lowest-index argmax,
+ * gap[s] (nullable) the Q-gap, each state by or_backup.  Arrays are indexed like V, so
+ * disjoint ranges can run on separate host threads.
+ */
+void or_backup_range(const or_params* p, const double* V, int64_t s0, int64_t s1, double* Vn, int32_t* pi,
+                     double* gap) {
+    for (int64_t s = s0; s < s1; s++) {
+        double b, g;
+        int32_t a;
+        or_backup(p, V, s, &b, &a, &g);
+        if (Vn) Vn[s] = b;
+        if (pi) pi[s] = a;
+        if (gap) gap[s] = g;
+    }
+}
+
+/*
  * Policy evaluation by Jacobi iteration: V <- R_pi + gamma P_pi V until the sweep change
  * is below tol.  Returns 0 on convergence, 1 if max_sweeps ran out, 2 if pi is not
  * feasible somewhere.

@@ -2,11 +2,15 @@
 
 ``VCValueFn.apply(theta, base, rho)`` returns J = rho . V*(theta) for the vehicular-cloud
 placement MDP with parameters theta = (lambda, mu_1..mu_H, delta_1..delta_H, f, w_occ,
-w_loss, w_q) on top of the fixed sizes and discount in ``base``; its backward calls
-``vc_value_grad`` (adjoint solve on the device).  Forward and backward both run in the
-CUDA library; this module only packs parameters.  The derivative is that of V_pi at the
-optimal policy, i.e. of V* wherever the optimal action is unique (V* is piecewise smooth
-in theta, with kinks where the optimal policy changes).
+w_loss, w_q) on top of the fixed sizes and discount in ``base``.  The forward pass solves
+the instance (``vc_value_iterate``) and takes J from the library (``vc_objective``); when
+theta requires a gradient it also runs the adjoint solve (``vc_value_grad``) right away,
+so the instance's handle and its device memory are released before forward returns and
+the graph keeps only the 2H+5 derivatives, which backward scales by the incoming
+gradient.  Every step runs in the CUDA library; this module only packs parameters.
+The derivative is that of V_pi at the optimal policy, i.e. of V* wherever the optimal
+action is unique (V* is piecewise smooth in theta, with kinks where the optimal policy
+changes).
 """
 from __future__ import annotations
 
@@ -46,17 +50,20 @@ class VCValueFn(torch.autograd.Function):
     def forward(ctx, theta, base, rho, fmt="implicit", tol=1e-6, grad_tol=1e-11):
         p = params_with(base, theta.detach().cpu().tolist())
         m = native.MDP.build(p, fmt=fmt)
-        _, V64, pi, st = m.value_iterate(tol=tol)
-        rho_d = rho.detach().to(device=V64.device, dtype=torch.float64).contiguous()
-        J = torch.dot(rho_d, V64)
-        ctx.m, ctx.V64, ctx.pi, ctx.rho = m, V64, pi, rho_d
-        ctx.grad_tol = grad_tol
+        try:
+            _, V64, pi, _ = m.value_iterate(tol=tol)
+            rho_d = rho.detach().to(device=V64.device, dtype=torch.float64).contiguous()
+            J = native.objective(V64, rho_d)[0]
+            dJ = None
+            if ctx.needs_input_grad[0]:
+                dJ, _, _ = m.value_grad(V64, pi, rho_d, tol=grad_tol)
+        finally:
+            m.close()
+        ctx.dJ = dJ
         ctx.theta_device, ctx.theta_dtype = theta.device, theta.dtype
         return J.to(device=theta.device, dtype=theta.dtype)
 
     @staticmethod
     def backward(ctx, gJ):
-        dJ, _, _ = ctx.m.value_grad(ctx.V64, ctx.pi, ctx.rho, tol=ctx.grad_tol)
-        g = gJ.to(torch.float64) * dJ.to(gJ.device)
-        ctx.m.close()
+        g = gJ.to(torch.float64) * ctx.dJ.to(gJ.device)
         return g.to(device=ctx.theta_device, dtype=ctx.theta_dtype), None, None, None, None, None

@@ -195,6 +195,24 @@ __global__ void k_grad_final(const double* __restrict__ partial, int nblocks, in
     out[i] = v;
 }
 
+
+// J = rho . V in FP64 by one block: each thread sums its strided states in index order,
+// then the block halves the partials in a fixed tree, so the result is reproducible bit
+// for bit (one block suffices: the objective is read once per solve).
+__global__ void __launch_bounds__(1024) k_objective(const double* __restrict__ V, const double* __restrict__ rho,
+                                                   long long S, double* __restrict__ J) {
+    __shared__ double part[1024];
+    double acc = 0.0;
+    for (long long s = threadIdx.x; s < S; s += 1024) acc = fma(rho[s], V[s], acc);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = part[0];
+}
+
 // ------------------------------------------------------------------------ launchers
 int launch_adj_count(Mdp* m, const int32_t* pi, int32_t* cnt, int* err, cudaStream_t st) {
     count_launches(1);
@@ -246,4 +264,19 @@ int launch_grad_contract(Mdp* m, const int32_t* pi, const double* V, const doubl
     return VC_OK;
 }
 
+int launch_objective(const double* V, const double* rho, long long S, double* J, cudaStream_t st) {
+    count_launches(1);
+    k_objective<<<1, 1024, 0, st>>>(V, rho, S, J);
+    VC_CUDA(cudaGetLastError());
+    return VC_OK;
+}
+
 }  // namespace vc
+
+// The objective of the gradient entry point, exported on its own: J = rho . V.
+extern "C" int vc_objective(const double* V, const double* rho, int64_t S, double* J, void* stream) {
+    vc::set_error("");
+    if (!V || !rho || !J) return vc::fail(VC_ERR_ARG, "vc_objective: NULL argument");
+    if (S < 1) return vc::fail(VC_ERR_ARG, "vc_objective: S < 1");
+    return vc::launch_objective(V, rho, (long long)S, J, (cudaStream_t)stream);
+}

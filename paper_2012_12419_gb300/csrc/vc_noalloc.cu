@@ -4,9 +4,10 @@
 // another allocator (a framework's caching pool), code that must not risk the implicit
 // device synchronisation an allocation can cause (latency-bound control loops), and code
 // that runs while another library captures the stream.  For them this file keeps the
-// sweep's scratch -- the post-decision value array U and a residual word -- in
-// file-scope __device__ arrays of fixed size, loaded with the library on every GPU that
-// loads it and held until the process exits.  The caller still passes V and V_out.
+// sweep's scratch -- the post-decision value array U, a residual word and a control block
+// whose error word the bounds-checking build reports through -- in file-scope __device__
+// arrays of fixed size, loaded with the library on every GPU that loads it and held until
+// the process exits.  The caller still passes V and V_out.
 #include <math.h>
 
 #include <mutex>
@@ -19,6 +20,7 @@ constexpr int kNoAllocMaxStates = 1 << 20;  // 1,048,576 states: 4 MiB of float 
 
 static __device__ __align__(256) float g_noalloc_U[kNoAllocMaxStates];
 static __device__ __align__(256) unsigned int g_noalloc_res[64];
+static __device__ __align__(256) Ctl g_noalloc_ctl;
 
 // Device addresses of the static arrays, looked up once per device.  In host code the
 // array names are host-side stand-ins, never device addresses: only these pointers are
@@ -27,6 +29,7 @@ struct NoAllocScratch {
     bool ready = false;
     float* U = nullptr;
     unsigned int* res = nullptr;
+    Ctl* ctl = nullptr;
 };
 
 constexpr int kMaxDevices = 64;
@@ -45,6 +48,8 @@ static int noalloc_scratch(NoAllocScratch* out) {
         s.U = (float*)p;
         VC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_res));
         s.res = (unsigned int*)p;
+        VC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_ctl));
+        s.ctl = (Ctl*)p;
         s.ready = true;
     }
     *out = s;
@@ -52,12 +57,16 @@ static int noalloc_scratch(NoAllocScratch* out) {
 }
 
 // max |V_out - V| over all states into *cell (non-negative float bits, order independent).
+// A NaN difference counts as +infinity: fmaxf would drop it, and a sweep that produced a
+// NaN must not report a finite residual.
 __global__ void __launch_bounds__(kThreads) k_noalloc_residual(const float* __restrict__ V,
                                                                const float* __restrict__ V_out, int S,
                                                                unsigned int* cell) {
     float r = 0.0f;
-    for (int s = blockIdx.x * kThreads + threadIdx.x; s < S; s += gridDim.x * kThreads)
-        r = fmaxf(r, fabsf(V_out[s] - V[s]));
+    for (int s = blockIdx.x * kThreads + threadIdx.x; s < S; s += gridDim.x * kThreads) {
+        const float d = fabsf(V_out[s] - V[s]);
+        r = (d != d) ? INFINITY : fmaxf(r, d);
+    }
     r = block_max<float, kThreads>(r);
     if (threadIdx.x == 0) atomicMax(cell, __float_as_uint(r));
 }
@@ -89,7 +98,14 @@ extern "C" int vc_bellman32_noalloc(const vc_params* p, const float* V, float* V
     VC_CUDA(cudaDeviceGetAttribute(&m.num_sms, cudaDevAttrMultiProcessorCount, dev));
     m.U32 = sc.U;
     cudaStream_t st = (cudaStream_t)stream;
+#ifdef VC_DEBUG_BOUNDS
+    // bounds-checking build: the sweep raises its flags in the static control block, which
+    // is cleared here and read back after the sweep (this build synchronises the stream)
+    VC_CUDA(cudaMemsetAsync(&sc.ctl->error, 0, sizeof(int), st));
+    SweepCtl none{sc.ctl, kModeNone, 0, nullptr};
+#else
     SweepCtl none{nullptr, kModeNone, 0, nullptr};
+#endif
     if ((rc = launch_sweep32(&m, V, V_out, pi, nullptr, none, st))) return rc;
     if (residual) {
         VC_CUDA(cudaMemsetAsync(sc.res, 0, sizeof(unsigned int), st));
@@ -98,5 +114,11 @@ extern "C" int vc_bellman32_noalloc(const vc_params* p, const float* V, float* V
         k_noalloc_copy_residual<<<1, 1, 0, st>>>(sc.res, residual);
         VC_CUDA(cudaGetLastError());
     }
+#ifdef VC_DEBUG_BOUNDS
+    int err = 0;
+    VC_CUDA(cudaMemcpyAsync(&err, &sc.ctl->error, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    if (err & kErrBounds) return fail(VC_ERR_CUDA, "a device bounds check failed (bounds-checking build)");
+#endif
     return VC_OK;
 }

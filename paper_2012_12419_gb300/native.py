@@ -44,7 +44,7 @@ EXPORTS = [
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
     "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
-    "vc_set_wait_limit", "vc_aaa_intervals",
+    "vc_set_wait_limit", "vc_aaa_intervals", "vc_objective",
 ]
 
 
@@ -162,6 +162,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_greedy_policy.argtypes = [vp, vp, vp]
         L.vc_set_wait_limit.argtypes = [vp, i64]
         L.vc_aaa_intervals.argtypes = [vp, vp, vp, i32, i32, i32, dbl, dbl, dbl, vp, vp, vp]
+        L.vc_objective.argtypes = [vp, vp, i64, vp, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -496,6 +497,16 @@ def bellman32_noalloc(params: dict, V, V_out, pi=None, residual=None, stream=Non
                                        _stream(stream)))
     del keep
     return V_out
+
+
+def objective(V, rho, stream=None):
+    """J = rho . V in FP64 on the device (float64 CUDA tensors of one length); returns a
+    one-element float64 CUDA tensor."""
+    if V.dtype != torch.float64 or rho.dtype != torch.float64 or V.numel() != rho.numel():
+        raise ValueError("V and rho must be float64 tensors of one length")
+    J = torch.empty(1, dtype=torch.float64, device=V.device)
+    _check(load().vc_objective(_ptr(V), _ptr(rho), int(V.numel()), _ptr(J), _stream(stream)))
+    return J
 
 
 def aaa_intervals(S_v, D_v, R_v, si_per_second: int = 10, si_ms: float = 100.0, dcchi_ms: float = 50.0,

@@ -51,8 +51,7 @@ def test_oracle_no_traffic_and_saturation():
     assert c == [50.0] and s == [50.0] and f == [0.5]
 
 
-@pytest.mark.parametrize("n_vehicles,seed", [(5, 1), (40, 2), (200, 3)])
-def test_intervals_sum_to_the_si_and_library_equals_oracle(n_vehicles, seed):
+def _library_equals_oracle(n_vehicles, seed):
     S, D, R = inputs.aaa_trace(n_vehicles, 6, seed)
     c, s, f = oracle.aaa_intervals(S.tolist(), D.tolist(), R.tolist())
     assert len(c) == 6
@@ -62,6 +61,22 @@ def test_intervals_sum_to_the_si_and_library_equals_oracle(n_vehicles, seed):
     native = _lib()
     lc, ls, lf = native.aaa_intervals(S, D, R)
     assert np.array_equal(lc, np.array(c)) and np.array_equal(ls, np.array(s)) and np.array_equal(lf, np.array(f))
+
+
+@pytest.mark.parametrize("n_vehicles,seed", [(5, 1), (40, 2), (200, 3)])
+def test_intervals_sum_to_the_si_and_library_equals_oracle(n_vehicles, seed):
+    _library_equals_oracle(n_vehicles, seed)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n_vehicles,seed", [(5, 1), (40, 2), (200, 3), (1000, 4)])
+def test_library_equals_oracle_in_the_gpu_build(n_vehicles, seed):
+    """The same comparison in the GPU test run, against the library built on that machine
+    (the routine is host code, so the GPU build is the one a user of the GPU path loads)."""
+    from gpu_common import native_or_skip
+
+    native_or_skip()
+    _library_equals_oracle(n_vehicles, seed)
 
 
 def test_library_argument_errors():

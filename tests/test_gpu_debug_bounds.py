@@ -51,6 +51,18 @@ for sliced in (False, True):
     _, V64, pi, st = m.value_iterate(tol=1e-8)
     assert st["certified"] == 1, st
     m.close()
+# the no-allocation sweep reports its checks through its static control block
+for p in (inputs.workload("tiny"), inputs.make_params(4, 4, 6, 0.95, seed=7)):
+    m = native.MDP.build(p, fmt="implicit")
+    V = torch.rand(m.S, device="cuda") * 50
+    ref = torch.empty_like(V)
+    m.bellman32(V, ref)
+    out = torch.empty_like(V)
+    res = torch.zeros(1, device="cuda")
+    native.bellman32_noalloc(p, V, out, None, res)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref) and res.item() == (out - V).abs().max().item()
+    m.close()
 print("debug bounds ok")
 """.replace("ROOT", repr(ROOT))
 

@@ -138,6 +138,45 @@ def test_autograd_function_returns_the_adjoint_gradient():
     assert np.max(np.abs(g - g_ref)) < 1e-5 * np.max(np.abs(g_ref))
 
 
+def test_objective_entry_point_and_no_grad_forward():
+    """vc_objective: rho . V in FP64 on the device equals the host dot product to rounding
+    and the J that vc_value_grad reports; with S not a multiple of the block and S = 1.
+    A forward pass without a gradient runs no adjoint solve and returns the same J."""
+    native = native_or_skip()
+    import torch
+
+    from paper_2012_12419_gb300.autograd import VCValueFn, theta_of
+
+    g = np.random.default_rng(4)
+    for S in (1, 1023, 1025, 343_750):
+        V = g.normal(30, 10, S)
+        rho = g.random(S)
+        J = native.objective(torch.tensor(V, device="cuda"), torch.tensor(rho, device="cuda"))
+        J2 = native.objective(torch.tensor(V, device="cuda"), torch.tensor(rho, device="cuda"))
+        assert float(J) == pytest.approx(float(np.dot(rho, V)), rel=1e-13)
+        assert torch.equal(J, J2)
+    with pytest.raises(ValueError):
+        native.objective(torch.zeros(3, device="cuda"), torch.zeros(3, device="cuda"))
+    p = inputs.workload("tiny")
+    m = native.MDP.build(p, fmt="implicit")
+    _, V64, pi, _ = m.value_iterate(tol=1e-6)
+    rho = torch.tensor(rho_empty_hosts(p), dtype=torch.float64, device="cuda")
+    _, _, gs = m.value_grad(V64, pi, rho)
+    assert float(native.objective(V64, rho)) == pytest.approx(gs["J"], rel=1e-13)
+    m.close()
+    theta = torch.tensor(theta_of(p), dtype=torch.float64)
+    base = {k: p[k] for k in ("H", "C", "Q", "gamma")}
+    n0 = native.kernel_launches()
+    with torch.no_grad():
+        J0 = VCValueFn.apply(theta, base, rho.cpu())
+    n1 = native.kernel_launches()
+    thg = theta.clone().requires_grad_(True)
+    J1 = VCValueFn.apply(thg, base, rho.cpu())
+    n2 = native.kernel_launches()
+    assert float(J0) == float(J1.detach())
+    assert n2 - n1 > n1 - n0  # the adjoint solve ran only when theta required a gradient
+
+
 def test_gradient_rejects_explicit_handles_and_bad_policies():
     native = native_or_skip()
     import torch

@@ -5,8 +5,9 @@ another allocator's pool, latency-bound loops that must not risk an allocation's
 synchronisation, code running under another library's stream capture): it keeps its
 scratch in a static device array instead.  Through the C ABI, two calls in a row with
 different inputs must reproduce vc_bellman32 on a VC_IMPLICIT handle of the same model
-bitwise (same kernels, same arithmetic), return max|V_out - V| as the residual, and reject
-models larger than the static scratch.  This file is collected last so that a run stopping
+bitwise (same kernels, same arithmetic), return max|V_out - V| as the residual (+infinity
+when a difference is NaN), accept NULL for the optional outputs, and reject models larger
+than the static scratch.  This file is collected last so that a run stopping
 at the first failure has already run every other test.
 """
 import ctypes
@@ -23,8 +24,8 @@ pytestmark = pytest.mark.gpu
 def _call(native, p, V, V_out, pi, res):
     L = native.load()
     cp, keep = native._params(p)
-    rc = L.vc_bellman32_noalloc(ctypes.byref(cp), ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(V_out.data_ptr()),
-                                ctypes.c_void_p(pi.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None)
+    rc = L.vc_bellman32_noalloc(ctypes.byref(cp), ptr(V), ptr(V_out), ptr(pi), ptr(res),
                                 ctypes.c_void_p(native.torch.cuda.current_stream().cuda_stream))
     del keep
     return rc
@@ -52,6 +53,36 @@ def test_noalloc_sweep_matches_handle_sweep_twice(name):
         assert torch.equal(V_out, ref)
         assert torch.equal(pi, ref_pi)
         assert res.item() == (V_out - V).abs().max().item()
+    m.close()
+
+
+def test_noalloc_optional_outputs_and_nan_residual():
+    """pi and residual are optional; a NaN in the input makes the residual +infinity
+    rather than a finite number (a NaN difference never drops out of the maximum)."""
+    native = native_or_skip()
+    import torch
+
+    p = inputs.workload("tiny")
+    m = native.MDP.build(p, fmt="implicit")
+    S = m.S
+    V = torch.rand(S, device="cuda", generator=torch.Generator(device="cuda").manual_seed(9)) * 40
+    ref = torch.empty_like(V)
+    m.bellman32(V, ref)
+    out = torch.full_like(V, float("nan"))
+    assert _call(native, p, V, out, None, None) == native.VC_OK
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    Vn = V.clone()
+    Vn[17] = float("nan")
+    res = torch.zeros(1, device="cuda")
+    assert _call(native, p, Vn, out, None, res) == native.VC_OK
+    torch.cuda.synchronize()
+    assert res.item() == float("inf")
+    # the residual word is cleared on every call: a clean input gives a finite value again
+    pi = torch.empty(S, dtype=torch.int32, device="cuda")
+    assert _call(native, p, V, out, pi, res) == native.VC_OK
+    torch.cuda.synchronize()
+    assert res.item() == (out - V).abs().max().item()
     m.close()
 
 
