@@ -238,6 +238,7 @@ def run_native(args):
             if world == 1 and args.workload == "large":
                 out["comparisons"] = comparisons(args, native, torch, dev, stream)
                 out["batched"] = batched_record(args, native, torch, dev, stream)
+                out["binary_model"] = binary_record(args, native, torch, dev, stream)
         print(json.dumps(out))
     m.close()
     if world > 1:
@@ -414,6 +415,53 @@ def run_batched(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def binary_record(args, native, torch, dev, stream):
+    """The paper's binary-action model (A = {-1, 1}: paid traditional cloud or the
+    requested vehicular cloud; 6 clouds of 6 VMs, requests of 1-3 VMs, 2,235,331 states) as
+    an explicit CSR built on the device, solved to the certified residual in each storage
+    form, device-timed like the headline step, with the sweep's roofline."""
+    from paper_2012_12419_gb300 import inputs
+
+    p = inputs.binary_workload("binary")
+    hbm, src = peaks()
+    out = {"workload": "binary-action model: H=6 clouds x C=6 VMs, requests of 1..3 VMs, S=2,235,331, A=2, "
+                       "gamma=0.95"}
+    for form, sliced in (("csr_f32", True), ("csr_f32", False), ("csr_bf16", True)):
+        t0 = time.perf_counter()
+        m = native.MDP.build_binary(p, fmt=form, sliced=sliced)
+        torch.cuda.synchronize()
+        build_ms = (time.perf_counter() - t0) * 1e3
+        m.autotune(reps=5)
+        info = m.info()
+        V = torch.zeros(info["S"], dtype=torch.float32, device=dev)
+        res = {}
+        for sl in (False, True):
+            def solve():
+                V.zero_()
+                return m.value_iterate(V, tol=args.tol, self_loop=sl)
+
+            solve()
+            t, (_, _, _, st) = _timed(torch, stream, solve, 3)
+            res[sl] = (t, st)
+        best = _best_plan(m)
+        sweep_us = float(best.split()[-1]) if best else None
+        alg = algorithmic_sweep_bytes(int(info["S"]), 2, int(info["nnz_logical"]), form == "csr_bf16")
+        t, st = res[False]
+        out[form + ("+sliced" if sliced else "")] = {
+            "time_to_residual_ms": t, "sweeps": int(st["sweeps"]), "certified": st["certified"] == 1,
+            "updates_per_s": info["nnz_logical"] * st["sweeps"] / (t / 1e3),
+            "ms_fp32_sweeps": st["ms_fp32"], "ms_fp64_refine": st["ms_fp64"], "build_ms": build_ms,
+            "sweep_us": sweep_us, "alg_bytes_per_sweep": alg,
+            "sweep_frac": (alg / (sweep_us * 1e-6) / 1e9 / hbm) if sweep_us else None,
+            "stored_frac": (info["sweep_bytes"] / (sweep_us * 1e-6) / 1e9 / hbm) if sweep_us else None,
+            "peak_source": f"{src} hbm_gbs",
+            "self_loop_ms": res[True][0], "self_loop_sweeps": int(res[True][1]["sweeps"]),
+            "self_loop_certified": res[True][1]["certified"] == 1,
+            "nnz_logical": int(info["nnz_logical"]), "nnz_sliced": int(info["nnz_sliced"]), "tuned": best}
+        m.close()
+    return out
 
 
 def batched_record(args, native, torch, dev, stream, steps: int = 5):
@@ -714,6 +762,40 @@ def captured_traffic(args, info):
     return TRAFFIC_BYTES[key], f"ncu dram__bytes_read.sum + dram__bytes_write.sum, sources sha256 {sha[:16]}"
 
 
+# ncu speed-of-light figures of the implicit sweep's two kernels on the large workload,
+# attached to that variant while the kernel source hashes as captured: the sweep is bound
+# by gather latency and issue, not by a memory roof (its HBM fraction is low by design).
+IMPLICIT_SOL_SOURCES = ("vc_sweep.cu",)
+IMPLICIT_SOL_SHA = "db4f4870c06ef9c3fad75d988e2fe6139b9aabbbd83bb168a67a3a840f4687ef"
+IMPLICIT_SOL = {"kernels": "k_post<7, float, 0> / k_max<7, float, 0>", "sm_issue_pct": [58.2, 50.0],
+                "l1tex_pct": [17.3, 13.5], "l2_pct": [10.5, 8.4], "dram_pct": [3.8, 7.5],
+                "warps_active_pct": [56.5, 73.8], "bound": "gather latency and instruction issue"}
+
+
+def implicit_sol():
+    return dict(IMPLICIT_SOL) if _sources_sha(IMPLICIT_SOL_SOURCES) == IMPLICIT_SOL_SHA else None
+
+
+def _sweep_us(m, torch, dev, stream, n: int = 40):
+    """Average time of one FP32 sweep (every kernel of it), events on the stream."""
+    S = int(m.info()["S"])
+    A = torch.rand(S, dtype=torch.float32, device=dev) * 50
+    B = torch.empty_like(A)
+    for _ in range(5):
+        m.bellman32(A, B, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n):
+        if i % 2 == 0:
+            m.bellman32(A, B, stream=stream)
+        else:
+            m.bellman32(B, A, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / n
+
+
 def batched_sol():
     return dict(BATCH_SOL) if _sources_sha(BATCH_SOL_SOURCES) == BATCH_SOL_SHA else None
 
@@ -834,7 +916,38 @@ def self_loop_comparison(args, p, m, V, native, torch, dev, stream):
             "certified": s0["certified"] == 1 and s1["certified"] == 1,
             "max_abs_V64_difference": float((V1 - V0).abs().max()),
         }
+    out["implicit"]["block"] = block_comparison(args, mi, Vi, torch, stream, res[True][0])
     mi.close()
+    return out
+
+
+def block_comparison(args, mi, Vi, torch, stream, t_self_loop):
+    """Algorithm 4's in-block iteration (VC_ITER_BLOCK: blocks of the states of h inner
+    hosts, p local passes per global sweep, self-transitions solved) on the implicit form,
+    several shapes, each device-timed to the same certified residual."""
+    out = {"shapes": []}
+    best = None
+    for h, passes in ((1, 4), (2, 2), (2, 4), (2, 8)):
+        try:
+            mi.set_block_iteration(h, passes)
+        except Exception:
+            continue
+
+        def solve():
+            Vi.zero_()
+            return mi.value_iterate(Vi, tol=args.tol, block=True)
+
+        solve()
+        t, (_, _, _, st) = _timed(torch, stream, solve, 3)
+        row = {"inner_hosts": h, "block_states": mi.block_iteration_info()["block_states"], "passes": passes,
+               "ms": t, "sweeps": int(st["sweeps"]), "ms_fp32_sweeps": st["ms_fp32"], "ms_fp64_refine": st["ms_fp64"],
+               "us_per_sweep": 1e3 * st["ms_fp32"] / max(int(st["sweeps"]), 1), "certified": st["certified"] == 1}
+        out["shapes"].append(row)
+        if best is None or t < best["ms"]:
+            best = row
+    mi.set_block_iteration(-1, 4)
+    out["best"] = best
+    out["speedup_vs_self_loop"] = t_self_loop / best["ms"] if best else None
     return out
 
 
@@ -868,11 +981,16 @@ def variants(args, p, native, torch, dev, stream):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / reps
         best = _best_plan(m) if form != "implicit" else None
-        sweep_us = float(best.split()[-1]) if best else None
+        sweep_us = float(best.split()[-1]) if best else _sweep_us(m, torch, dev, stream)
+        hbm = peaks()[0]
+        alg = (8 * int(info["S"]) if form == "implicit" else
+               algorithmic_sweep_bytes(int(info["S"]), int(info["A"]), int(info["nnz_logical"]), form == "csr_bf16"))
         out[form + ("+padded" if padded else "") + ("+sliced" if sliced else "")] = {
             "time_to_residual_ms": t, "updates_per_s": info["nnz_logical"] * sweeps / reps / (t / 1e3),
             "sweep_us": sweep_us,
-            "sweep_hbm_frac": (info["sweep_bytes"] / (sweep_us * 1e-6) / 1e9 / peaks()[0]) if sweep_us else None,
+            "sweep_alg_frac": alg / (sweep_us * 1e-6) / 1e9 / hbm,
+            "sweep_stored_frac": info["sweep_bytes"] / (sweep_us * 1e-6) / 1e9 / hbm,
+            "ncu_sol": implicit_sol() if form == "implicit" else None,
             "ms_fp32_sweeps": st["ms_fp32"], "ms_fp64_refine": st["ms_fp64"],
             "sweeps": sweeps // reps, "nnz_stored": int(info["nnz_stored"]),
             "nnz_sliced": int(info["nnz_sliced"]), "sweep_bytes": int(info["sweep_bytes"]),

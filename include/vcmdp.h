@@ -84,6 +84,17 @@ extern "C" {
                                 FP32 stopping test, and the FP64 refinement and certificate use
                                 Eq. 18's backup as without the flag.  Every storage form. */
 
+#define VC_ITER_BLOCK 16     /* implicit handles: FP32 sweeps run Algorithm 4's in-block iteration
+                                (Section V-H) with the self-transition solve of VC_ITER_SELF_LOOP:
+                                states are cut into blocks of B = 2(Q+1)(C+1)^h consecutive codes
+                                (every queue length, phase and occupancy of the h inner hosts), and
+                                in one global sweep each block runs `passes` local Jacobi passes in
+                                which successors inside the block take the block's latest local
+                                values and all others the previous global iterate
+                                (vc_set_block_iteration).  Same fixed point V*; the stopping test
+                                is the global sweep change; refinement and certificate unchanged.
+                                VC_ERR_ARG for explicit handles. */
+
 /* Model parameters (host struct; mu and delta are HOST arrays of length H). */
 typedef struct vc_params {
     int32_t H, C, Q;      /* hosts, VM slots per host, queue capacity */
@@ -170,6 +181,52 @@ int vc_build_mdp_csr(int64_t S, int32_t A, const int64_t* row_ptr, const int32_t
                      int val_dtype, const float* row_scale, const float* R, double gamma, void* stream,
                      vc_mdp** out);
 
+/*
+ * Parameters of the paper's binary-action model (host struct; mu and delta are HOST arrays
+ * of length H).  Section V-B..V-E: the state (n_1..n_TT, M, e) of Eq. 10 is read as the
+ * busy VMs u_k of each of H vehicular clouds plus the pending request e; the actions are
+ * A = {-1, 1} of Eq. 11; the reward is r = k - g of Eqs. 14-16.
+ */
+typedef struct vc_binary_params {
+    int32_t H;            /* vehicular clouds (1..16) */
+    int32_t C;            /* VMs per cloud */
+    int32_t J;            /* largest request in VMs (1..8); sizes 1..J equally likely */
+    int32_t reserved;
+    double lambda;        /* request arrival rate */
+    double gamma;         /* discount factor in (0, 1) */
+    double beta_vc;       /* reward per VM placed on a vehicular cloud (Eq. 15) */
+    double beta_tc;       /* cost per VM hosted in the paid traditional cloud (Eq. 16) */
+    double gamma_vc;      /* penalty per idle VM of the requested cloud (Eq. 16) */
+    const double* mu;     /* host, [H] completion rate of each busy VM */
+    const double* delta;  /* host, [H] departure rate of each cloud */
+} vc_binary_params;
+
+/*
+ * Build an explicit instance of the paper's binary-action model (Section V-B..V-E; the
+ * transition law the paper leaves open is read as one uniformised event per step):
+ *   state  s = e + E * sum_k u_k (C+1)^k, E = 1 + H J, S = E (C+1)^H; u_k in 0..C busy
+ *          VMs of cloud k; e = 0 no request, e = 1 + i J + (n-1) a task of n VMs for cloud i
+ *   action 0 ("-1"): the task goes to the paid traditional cloud, reward
+ *          -beta_tc n - gamma_vc (C - u_i); with no request the no-op, reward 0
+ *   action 1 ("+1"): the task is placed on cloud i, feasible iff a request is pending and
+ *          u_i + n <= C, reward beta_vc n - gamma_vc (C - u_i - n)
+ *   then from the post-decision state (request consumed) one event, rates over
+ *          Lam = lambda + C sum(mu) + sum(delta) + 1: completion of a busy VM of cloud k
+ *          (mu_k u_k, u_k - 1), departure of cloud k (delta_k, u_k = 0), a request of n VMs
+ *          at cloud i (lambda / (H J) for each (i, n)), self-loop the rest.
+ * Rows hold the merged non-zero successors sorted by column (at most 2H + 1 + HJ).  fmt is
+ * VC_CSR_F32 or VC_CSR_BF16 (BF16 values rounded to nearest even from the FP64
+ * probability, per-row FP32 scale 1/sum bf16(p)), optionally | VC_SLICED | VC_DIRECT.  The
+ * handle keeps the exact FP64 probabilities and rewards beside the stored ones, so the
+ * FP64 refinement and certificate of vc_value_iterate solve the exact model; the FP32
+ * sweeps, products and autotuner run on the stored values.  It has no rate gradients
+ * (vc_value_grad) and no greedy rule (vc_greedy_policy): both return VC_ERR_ARG.
+ * Errors: VC_ERR_ARG for H outside 1..16, J outside 1..8, C < 1, S >= 2^31, lambda or a mu
+ * not > 0, a delta < 0, gamma outside (0, 1), non-finite weights, other formats;
+ * VC_ERR_OOM.
+ */
+int vc_build_binary_mdp(const vc_binary_params* p, int fmt, void* stream, vc_mdp** out);
+
 /* Sizes of a handle (host struct out). */
 int vc_mdp_info(const vc_mdp* m, vc_info* out);
 
@@ -244,6 +301,19 @@ int vc_extract_policy(vc_mdp* m, const float* V, int32_t* pi, float* qgap, void*
  * fixed number of Jacobi sweeps; kernels are only enqueued on `stream`.
  */
 int vc_bellman32(vc_mdp* m, const float* V, float* V_out, int32_t* pi, float* qgap, void* stream);
+
+/*
+ * Shape of the in-block iteration of an implicit handle (VC_ITER_BLOCK; Algorithm 4's
+ * "episodes" inside a block, Section V-H): inner_hosts = h gives blocks of
+ * B = 2(Q+1)(C+1)^h states (at most 1024; -1 = the largest such h, the default), passes the
+ * local passes per global sweep (1..64, default 4; 1 is the plain self-transition sweep).
+ * Applies to later solves.  VC_ERR_ARG for explicit handles, passes outside 1..64 or a block
+ * of more than 1024 states.
+ */
+int vc_set_block_iteration(vc_mdp* m, int32_t inner_hosts, int32_t passes);
+
+/* The current shape (host outputs, each nullable): inner hosts, states per block, passes. */
+int vc_block_iteration_info(const vc_mdp* m, int32_t* inner_hosts, int32_t* block_states, int32_t* passes);
 
 /*
  * One FP32 Bellman sweep of the model in *p (implicit form) that allocates no device
@@ -435,13 +505,26 @@ int vc_batch_offsets(const vc_batch* b, int64_t* offsets);
  * one FP64 Bellman backup (repeated while an instance fails); VC_ITER_ACCURATE certifies
  * each instance's error
  * (residual below tol (1 - gamma_i) / (2 gamma_i)).  VC_ITER_SELF_LOOP runs the FP32 loop
- * with the self-transition-solved backup, as in vc_value_iterate.  V: [total] float in (warm start) / out (FP32
+ * with the self-transition-solved backup, as in vc_value_iterate; VC_ITER_BLOCK adds
+ * Algorithm 4's in-block passes to it (vc_batch_set_block_iteration), each instance in its
+ * own blocks.  V: [total] float in (warm start) / out (FP32
  * iterate); V64_out [total] double and pi_out [total] int32 nullable (pi is local to the
  * instance: 0..H_i); per_inst: HOST array of n stats (nullable).  Synchronises `stream`.
  * VC_ERR_NOT_CONVERGED if an instance is not certified (or, FP32 only, hit max_sweeps).
  */
 int vc_value_iterate_batch(vc_batch* b, float* V, double* V64_out, int32_t* pi_out, double tol, int64_t max_sweeps,
                            int flags, vc_batch_stats* per_inst, void* stream);
+
+/*
+ * Shape of the batched in-block iteration (VC_ITER_BLOCK; Algorithm 4's "episodes", Section
+ * V-H): each instance i is cut into blocks of 2(Q_i+1)(C_i+1)^h_i states with the largest
+ * h_i that fits `threads` (32..1024, default 512), packed into tiles of whole blocks of at
+ * most `threads` states, one thread per state; `passes` (1..64, default 4) local passes per
+ * global sweep.  Rebuilds the tile table and recaptures the loop graphs on `stream`
+ * (synchronised).  VC_ERR_ARG for out-of-range values or an instance whose smallest block
+ * 2(Q_i+1) exceeds `threads` (the previous shape is kept).
+ */
+int vc_batch_set_block_iteration(vc_batch* b, int32_t threads, int32_t passes, void* stream);
 
 /*
  * Autotuner of the batched schedule: times the FP32 loop graph for `sweeps` sweeps of every

@@ -648,3 +648,128 @@ def aaa_intervals(S_v, D_v, R_v, si_per_second: int = 10, si_ms: float = 100.0, 
             s_v2v = 0.0
             d_v2v = 0.0
     return out_c, out_s, out_f
+
+
+# ------------------------------------------------- the paper's binary-action model (NEXT)
+
+
+class _BinParams(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int32),
+        ("C", ctypes.c_int32),
+        ("J", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
+        ("lam", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("beta_vc", ctypes.c_double),
+        ("beta_tc", ctypes.c_double),
+        ("gamma_vc", ctypes.c_double),
+        ("mu", ctypes.c_double * MAXH),
+        ("delta", ctypes.c_double * MAXH),
+    ]
+
+
+def _bin_params(p: dict) -> _BinParams:
+    H, J = int(p["H"]), int(p["J"])
+    if not 1 <= H <= MAXH or not 1 <= J <= 8:
+        raise ValueError("H must be in 1..16 and J in 1..8")
+    c = _BinParams()
+    c.H, c.C, c.J = H, int(p["C"]), J
+    c.lam, c.gamma = float(p["lam"]), float(p["gamma"])
+    c.beta_vc, c.beta_tc, c.gamma_vc = float(p["beta_vc"]), float(p["beta_tc"]), float(p["gamma_vc"])
+    for k in range(H):
+        c.mu[k] = float(p["mu"][k])
+        c.delta[k] = float(p["delta"][k])
+    return c
+
+
+def _bin_lib():
+    L = lib()
+    if not hasattr(L, "_bin_ready"):
+        P = ctypes.POINTER(_BinParams)
+        vp = ctypes.c_void_p
+        L.or_bin_num_states.argtypes = [P]
+        L.or_bin_num_states.restype = ctypes.c_int64
+        L.or_bin_uniformisation.argtypes = [P]
+        L.or_bin_uniformisation.restype = ctypes.c_double
+        L.or_bin_transitions.argtypes = [P, ctypes.c_int64, ctypes.c_int, vp, vp, vp]
+        L.or_bin_transitions.restype = ctypes.c_int
+        L.or_bin_build_csr.argtypes = [P, vp, vp, vp, vp]
+        L.or_bin_build_csr.restype = ctypes.c_int64
+        L._bin_ready = True
+    return L
+
+
+def bin_num_states(p: dict) -> int:
+    return int(_bin_lib().or_bin_num_states(ctypes.byref(_bin_params(p))))
+
+
+def bin_uniformisation(p: dict) -> float:
+    return float(_bin_lib().or_bin_uniformisation(ctypes.byref(_bin_params(p))))
+
+
+def bin_transitions(p: dict, s: int, a: int):
+    """Merged, sorted successor row of (s, a) of the binary-action model: (cols, probs, R),
+    or None if a is infeasible in s (a = 0 is the paper's -1, a = 1 its +1)."""
+    cols = np.zeros(162, np.int64)
+    probs = np.zeros(162, np.float64)
+    R = np.zeros(1, np.float64)
+    n = _bin_lib().or_bin_transitions(ctypes.byref(_bin_params(p)), int(s), int(a), _ptr(cols), _ptr(probs), _ptr(R))
+    if n < 0:
+        return None
+    return cols[:n].copy(), probs[:n].copy(), float(R[0])
+
+
+def bin_build_csr(p: dict):
+    """Explicit CSR of the binary-action model: (row_ptr int64[2S+1], col int32, val float64,
+    R float64[2S] with -inf on infeasible rows); row r = 2 s + a."""
+    cp = _bin_params(p)
+    L = _bin_lib()
+    S = bin_num_states(p)
+    nnz = L.or_bin_build_csr(ctypes.byref(cp), None, None, None, None)
+    row_ptr = np.zeros(2 * S + 1, np.int64)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz, np.float64)
+    R = np.zeros(2 * S, np.float64)
+    L.or_bin_build_csr(ctypes.byref(cp), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(R))
+    return row_ptr, col, val, R
+
+
+def bin_solve(p: dict, tol: float = 1e-12, val=None):
+    """Optimum of the binary-action model: value iteration on its CSR (val replaces the
+    exact FP64 probabilities, e.g. their FP32 rounding), then the argmax policy.
+    Returns (V, pi, gap, sweeps)."""
+    S = bin_num_states(p)
+    rp, col, v, R = bin_build_csr(p)
+    if val is not None:
+        v = np.asarray(val, np.float64)
+    V, n = vi_csr(S, 2, rp, col, v, R, p["gamma"], tol=tol)
+    pi, gap = policy_csr(S, 2, rp, col, v, R, p["gamma"], V)
+    return V, pi, gap, n
+
+
+def bin_backup_all(p: dict, V, threads: int | None = None):
+    """Bellman backup, argmax and Q-gap of every state of the binary-action model from V,
+    on contiguous state ranges over host threads.  Returns (Vn, pi, gap)."""
+    L = _bin_lib()
+    L.or_bin_backup_range.argtypes = [ctypes.POINTER(_BinParams), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_bin_backup_range.restype = None
+    V = np.ascontiguousarray(V, np.float64)
+    S = len(V)
+    Vn = np.empty(S, np.float64)
+    pi = np.empty(S, np.int32)
+    gap = np.empty(S, np.float64)
+    cp = _bin_params(p)
+    n = max(1, min(threads or os.cpu_count() or 1, S))
+    cuts = [S * i // n for i in range(n + 1)]
+
+    def run(i):
+        L.or_bin_backup_range(ctypes.byref(cp), _ptr(V), cuts[i], cuts[i + 1], _ptr(Vn), _ptr(pi), _ptr(gap))
+
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(n)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return Vn, pi, gap

@@ -910,3 +910,191 @@ int or_adjoint_apply(const or_params* p, const int32_t* pi, const double* lam, d
     }
     return 0;
 }
+
+/* =====================================================================================
+ * The paper's binary-action model (Section V-B..V-E: state Eq. 10, actions A = {-1, 1}
+ * of Eq. 11, reward r = k - g of Eqs. 14-16), with the transition law the paper leaves
+ * open read as one uniformised event per step (the readings are in the design notes):
+ *   state  s = e + E * sum_k u_k (C+1)^k,  E = 1 + H*J
+ *          u_k in 0..C busy VMs of vehicular cloud k (Eq. 10's n_k), e the pending request:
+ *          e = 0 none, e = 1 + i*J + (n-1) a task of n VMs (1 <= n <= J) asking VC i
+ *   action index 0 = "-1": the task goes to the paid traditional cloud (TCC), always
+ *          feasible; with no request it is the no-op (reward 0)
+ *          index 1 = "+1": the task is placed on VC i, feasible iff a request is pending
+ *          and u_i + n <= C
+ *   reward index 1: beta_vc n - gamma_vc (C - u_i - n)       (k - g, free VMs after)
+ *          index 0: -beta_tc n - gamma_vc (C - u_i)          (paid VMs, VC i stays idle)
+ *   post-decision state: u (+ n on VC i for index 1), e = 0; then one event, rates over
+ *          Lam = lambda + C sum(mu) + sum(delta) + 1:
+ *          completion of one busy VM of VC k   mu_k u_k -> u_k - 1
+ *          departure of VC k                   delta_k  -> u_k = 0 (self if u_k = 0)
+ *          a request of n VMs at VC i          lambda / (H J) for each (i, n) -> e
+ *          self-loop                           the rest
+ * ===================================================================================== */
+
+typedef struct {
+    int32_t H, C, J, pad_;
+    double lambda, gamma, beta_vc, beta_tc, gamma_vc;
+    double mu[OR_MAXH];
+    double delta[OR_MAXH];
+} or_bin_params;
+
+#define OR_BIN_MAXSUCC (2 * OR_MAXH + 2 + OR_MAXH * 8)
+
+int64_t or_bin_num_states(const or_bin_params* p) {
+    int64_t n = 1 + (int64_t)p->H * p->J;
+    for (int k = 0; k < p->H; k++) n *= (p->C + 1);
+    return n;
+}
+
+static void bin_decode(const or_bin_params* p, int64_t s, int* u, int* e) {
+    const int64_t E = 1 + (int64_t)p->H * p->J;
+    *e = (int)(s % E);
+    int64_t rest = s / E;
+    for (int k = 0; k < p->H; k++) {
+        u[k] = (int)(rest % (p->C + 1));
+        rest /= (p->C + 1);
+    }
+}
+
+static int64_t bin_encode(const or_bin_params* p, const int* u, int e) {
+    int64_t code = 0;
+    for (int k = p->H - 1; k >= 0; k--) code = code * (p->C + 1) + u[k];
+    return e + (1 + (int64_t)p->H * p->J) * code;
+}
+
+double or_bin_uniformisation(const or_bin_params* p) {
+    double mu = 0.0, de = 0.0;
+    for (int k = 0; k < p->H; k++) {
+        mu += p->mu[k];
+        de += p->delta[k];
+    }
+    return p->lambda + p->C * mu + de + 1.0;
+}
+
+/* Row of (s, a): merged successors sorted by target, zeros dropped, and the reward.
+ * Returns the number of successors, or -1 if a is not feasible in s. */
+int or_bin_transitions(const or_bin_params* p, int64_t s, int a, int64_t* cols, double* probs, double* R) {
+    int u[OR_MAXH] = {0}, e = 0;
+    bin_decode(p, s, u, &e);
+    const int H = p->H, C = p->C, J = p->J;
+    int vc = -1, n = 0;
+    if (e > 0) {
+        vc = (e - 1) / J;
+        n = (e - 1) % J + 1;
+    }
+    if (a == 1) {
+        if (e == 0 || u[vc] + n > C) return -1;
+        u[vc] += n;
+        *R = p->beta_vc * n - p->gamma_vc * (C - u[vc]);
+    } else if (a == 0) {
+        *R = (e == 0) ? 0.0 : -p->beta_tc * n - p->gamma_vc * (C - u[vc]);
+    } else {
+        return -1;
+    }
+    const int64_t x = bin_encode(p, u, 0);
+    const double Lam = or_bin_uniformisation(p);
+
+    int64_t ec[OR_BIN_MAXSUCC];
+    double ep[OR_BIN_MAXSUCC];
+    int ne = 0;
+    double total = 0.0;
+    for (int k = 0; k < H; k++) {
+        if (u[k] > 0) {
+            int u2[OR_MAXH];
+            memcpy(u2, u, sizeof(int) * H);
+            u2[k] -= 1;
+            ec[ne] = bin_encode(p, u2, 0);
+            ep[ne] = p->mu[k] * u[k] / Lam;
+            total += ep[ne];
+            ne++;
+        }
+        {
+            int u2[OR_MAXH];
+            memcpy(u2, u, sizeof(int) * H);
+            u2[k] = 0;
+            ec[ne] = bin_encode(p, u2, 0);
+            ep[ne] = p->delta[k] / Lam;
+            total += ep[ne];
+            ne++;
+        }
+    }
+    for (int i = 0; i < H; i++) {
+        for (int m = 1; m <= J; m++) {
+            ec[ne] = bin_encode(p, u, 1 + i * J + (m - 1));
+            ep[ne] = p->lambda / (H * J) / Lam;
+            total += ep[ne];
+            ne++;
+        }
+    }
+    ec[ne] = x;
+    ep[ne] = 1.0 - total;
+    ne++;
+
+    int cnt = 0;
+    for (int i = 0; i < ne; i++) add_succ(cols, probs, &cnt, ec[i], ep[i]);
+    int m = 0;
+    for (int i = 0; i < cnt; i++) {
+        if (probs[i] != 0.0) {
+            cols[m] = cols[i];
+            probs[m] = probs[i];
+            m++;
+        }
+    }
+    sort_succ(cols, probs, m);
+    return m;
+}
+
+/* CSR of the binary model (row r = 2 s + a); with NULL outputs returns the count only. */
+int64_t or_bin_build_csr(const or_bin_params* p, int64_t* row_ptr, int32_t* col, double* val, double* R) {
+    const int64_t S = or_bin_num_states(p);
+    int64_t nnz = 0;
+    int64_t cols[OR_BIN_MAXSUCC];
+    double probs[OR_BIN_MAXSUCC];
+    if (row_ptr) row_ptr[0] = 0;
+    for (int64_t s = 0; s < S; s++) {
+        for (int a = 0; a < 2; a++) {
+            double Rv = 0.0;
+            const int n = or_bin_transitions(p, s, a, cols, probs, &Rv);
+            const int64_t r = 2 * s + a;
+            if (R) R[r] = (n < 0) ? -INFINITY : Rv;
+            for (int j = 0; j < n; j++) {
+                if (col) col[nnz + j] = (int32_t)cols[j];
+                if (val) val[nnz + j] = probs[j];
+            }
+            if (n > 0) nnz += n;
+            if (row_ptr) row_ptr[r + 1] = nnz;
+        }
+    }
+    return nnz;
+}
+
+/* Backups of the states s0 .. s1-1 of the binary-action model from V: Vn[s] the best Q
+ * value, pi[s] its lowest-index argmax, gap[s] the Q-gap (+inf with one feasible action). */
+void or_bin_backup_range(const or_bin_params* p, const double* V, int64_t s0, int64_t s1, double* Vn, int32_t* pi,
+                         double* gap) {
+    int64_t cols[OR_BIN_MAXSUCC];
+    double probs[OR_BIN_MAXSUCC];
+    for (int64_t s = s0; s < s1; s++) {
+        double b = -INFINITY, second = -INFINITY;
+        int ba = -1;
+        for (int a = 0; a < 2; a++) {
+            double Rv;
+            const int n = or_bin_transitions(p, s, a, cols, probs, &Rv);
+            if (n < 0) continue;
+            double acc = 0.0;
+            for (int j = 0; j < n; j++) acc += probs[j] * V[cols[j]];
+            const double qv = Rv + p->gamma * acc;
+            if (qv > b) {
+                second = b;
+                b = qv;
+                ba = a;
+            } else if (qv > second) {
+                second = qv;
+            }
+        }
+        Vn[s] = b;
+        pi[s] = ba;
+        gap[s] = (second == -INFINITY) ? INFINITY : b - second;
+    }
+}

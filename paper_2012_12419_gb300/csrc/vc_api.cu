@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 static void free_mdp(Mdp* m) {
     if (!m) return;
-    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->rate_tab, m->Vb, m->U32, m->U32s, m->U64, m->V64a,
+    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->val64, m->R64, m->rate_tab, m->Vb, m->U32, m->U32s, m->U64, m->V64a,
                     m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->kr, m->kr_part, m->kctl, m->ctl,
                     m->sell_rec, m->sell_slab};
     for (void* p : ptrs)
@@ -252,6 +252,31 @@ int vc_build_mdp(const vc_params* p, int fmt, void* stream, vc_mdp** out) {
     if (!rc) rc = upload_rate_table(m, st);
     if (!rc && base != VC_IMPLICIT) rc = build_csr_from_model(m, st);
     if (!rc && base == VC_IMPLICIT) rc = count_model_rows(m, st);  // logical nnz, nothing stored
+    if (!rc) rc = alloc_work(m);
+    if (!rc && (fmt & VC_SLICED)) rc = use_sliced(m, st);
+    if (rc) {
+        free_mdp(m);
+        return rc;
+    }
+    *out = (vc_mdp*)m;
+    return VC_OK;
+}
+
+int vc_build_binary_mdp(const vc_binary_params* p, int fmt, void* stream, vc_mdp** out) {
+    NvtxRange nv("vc_build_binary_mdp");
+    g_err.clear();
+    if (!out) return fail(VC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(VC_ERR_ARG, "params is NULL");
+    const int base = fmt & 0xF;
+    if (base != VC_CSR_F32 && base != VC_CSR_BF16) return fail(VC_ERR_ARG, "the binary model needs a CSR format");
+    if ((fmt & ~(0xF | VC_DIRECT | VC_SLICED)) != 0) return fail(VC_ERR_ARG, "unknown or unsupported format flag");
+    Mdp* m = new Mdp();
+    m->fmt = fmt;
+    m->has_model = false;
+    m->num_sms = device_sms();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = build_csr_binary(m, p, st);
     if (!rc) rc = alloc_work(m);
     if (!rc && (fmt & VC_SLICED)) rc = use_sliced(m, st);
     if (rc) {
@@ -552,6 +577,40 @@ int vc_extract_policy(vc_mdp* mh, const float* V, int32_t* pi, float* qgap, void
     return launch_sweep32(m, V, nullptr, pi, qgap, sc, (cudaStream_t)stream);
 }
 
+int vc_set_block_iteration(vc_mdp* mh, int32_t inner_hosts, int32_t passes) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    Mdp* m = (Mdp*)mh;
+    if ((m->fmt & 0xF) != VC_IMPLICIT) return fail(VC_ERR_ARG, "the in-block iteration needs a VC_IMPLICIT handle");
+    if (passes < 1 || passes > 64) return fail(VC_ERR_ARG, "passes must be in 1..64");
+    if (inner_hosts < -1 || inner_hosts > m->md.H) return fail(VC_ERR_ARG, "inner_hosts must be in -1..H");
+    const int old_h = m->blk_h;
+    m->blk_h = inner_hosts;
+    int h = 0, B = 0;
+    const int rc = block_shape(m, &h, &B);
+    if (rc) {
+        m->blk_h = old_h;
+        return rc;
+    }
+    m->blk_passes = passes;
+    m->blk_grid = 0;
+    return VC_OK;
+}
+
+int vc_block_iteration_info(const vc_mdp* mh, int32_t* inner_hosts, int32_t* block_states, int32_t* passes) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    const Mdp* m = (const Mdp*)mh;
+    if ((m->fmt & 0xF) != VC_IMPLICIT) return fail(VC_ERR_ARG, "the in-block iteration needs a VC_IMPLICIT handle");
+    int h = 0, B = 0;
+    const int rc = block_shape(m, &h, &B);
+    if (rc) return rc;
+    if (inner_hosts) *inner_hosts = h;
+    if (block_states) *block_states = B;
+    if (passes) *passes = m->blk_passes;
+    return VC_OK;
+}
+
 int vc_bellman32(vc_mdp* mh, const float* V, float* V_out, int32_t* pi, float* qgap, void* stream) {
     g_err.clear();
     if (!mh || !V) return fail(VC_ERR_ARG, "NULL argument");
@@ -645,9 +704,15 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
     VC_CUDA(cudaEventRecord(ev[0], st));
     {
         NvtxRange nv32("fp32 sweeps");
-        const int self_loop = (flags & VC_ITER_SELF_LOOP) ? 1 : 0;
+        const int block = (flags & VC_ITER_BLOCK) ? 1 : 0;
+        const int self_loop = ((flags & VC_ITER_SELF_LOOP) || block) ? 1 : 0;
+        if (block && (m->fmt & 0xF) != VC_IMPLICIT) {
+            rc = fail(VC_ERR_ARG, "VC_ITER_BLOCK needs a VC_IMPLICIT handle");
+            goto out;
+        }
         rc = loop32(m, V, m->Vb, tol, max_sweeps, st, &fin, [&](const float* in, float* o, SweepCtl sc) {
             sc.self_loop = self_loop;
+            sc.block = block;
             return launch_sweep32(m, in, o, nullptr, nullptr, sc, st);
         });
     }

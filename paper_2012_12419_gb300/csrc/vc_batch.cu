@@ -32,7 +32,7 @@ struct InstDesc {
     Coef<double> c64;
     long long off;  // first state in the concatenated arrays
     int S;
-    int pad_;
+    int blk_h;      // inner hosts of the in-block iteration's blocks (2(Q+1)(C+1)^blk_h states)
 };
 
 struct BatchTile {
@@ -260,6 +260,38 @@ __global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __re
                     atomicMax(&res64[tl.inst], dbits((double)res));
             }
         }
+        __syncthreads();
+    }
+}
+
+// Algorithm 4's in-block iteration for every active instance (VC_ITER_BLOCK): the block
+// tile table cuts each instance into tiles of whole blocks of 2(Q_i+1)(C_i+1)^h_i states
+// (block_tile), one thread per state; each tile closes its share of the instance's sweep.
+template <int MH>
+__global__ void __launch_bounds__(1024) k_bblock(const InstDesc* __restrict__ descs,
+                                                 const BatchTile* __restrict__ tiles, int ntiles, BatchCtl c,
+                                                 int parity, int passes, const float* __restrict__ U,
+                                                 const float* __restrict__ U2, const float* __restrict__ V_in,
+                                                 float* __restrict__ V_out) {
+    extern __shared__ float bb_sm[];
+    __shared__ InstDesc sd;
+    __shared__ int skip;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x == 0) skip = *((volatile int*)&c.done[tl.inst]) != 0;
+        __syncthreads();
+        if (skip) {
+            __syncthreads();
+            continue;
+        }
+        load_desc(descs, tl.inst, sd);
+        __syncthreads();
+        float res = 0.0f, vabs = 0.0f;
+        block_tile<MH>(sd.md, sd.c32, sd.blk_h, tl.start, tl.count, passes, V_in + sd.off, U + sd.off, U2 + sd.off,
+                       V_out + sd.off, bb_sm, nullptr, res, vabs);
+        res = block_max_dyn(res);
+        vabs = block_max_dyn(vabs);
+        if (threadIdx.x == 0) close_instance(c, tl.inst, res, vabs, parity, parity ^ 1);
         __syncthreads();
     }
 }
@@ -666,8 +698,16 @@ struct Batch {
     int *kr_done = nullptr, *kr_iter = nullptr, *tile_first = nullptr;
     unsigned int* kr_ticket = nullptr;
     long long* kr_max_d = nullptr;
-    cudaGraph_t g_vi = nullptr, g_vi_sl = nullptr, g_corr = nullptr, g_kry = nullptr;
-    cudaGraphExec_t x_vi = nullptr, x_vi_sl = nullptr, x_corr = nullptr, x_kry = nullptr;
+    // in-block iteration (VC_ITER_BLOCK): tiles of whole blocks of at most blk_threads states
+    int blk_threads = 512;
+    int blk_passes = 4;
+    int blk_grid = 0;
+    int nbtiles = 0;
+    std::vector<int> h_btiles_of;
+    BatchTile* d_btiles = nullptr;
+    int* btiles_of = nullptr;
+    cudaGraph_t g_vi = nullptr, g_vi_sl = nullptr, g_corr = nullptr, g_kry = nullptr, g_vi_blk = nullptr;
+    cudaGraphExec_t x_vi = nullptr, x_vi_sl = nullptr, x_corr = nullptr, x_kry = nullptr, x_vi_blk = nullptr;
     std::vector<void*> owned;
     int64_t device_bytes = 0;
     std::string tune_report;
@@ -766,6 +806,45 @@ static int build_tiles(Batch* b, cudaStream_t st) {
     return VC_OK;
 }
 
+// Block tile table of the in-block iteration: per instance the largest h with a block of
+// B = 2(Q+1)(C+1)^h <= blk_threads states, tiles of floor(blk_threads / B) whole blocks
+// (the last one shorter), tiles of an instance contiguous.
+static int build_block_tiles(Batch* b, cudaStream_t st) {
+    std::vector<BatchTile> tiles;
+    b->h_btiles_of.assign(b->n, 0);
+    for (int i = 0; i < b->n; i++) {
+        InstDesc& d = b->h_desc[i];
+        int h = 0;
+        long long B = 2LL * (d.md.Q + 1);
+        while (h < d.md.H && B * (d.md.C + 1) <= b->blk_threads) {
+            B *= (d.md.C + 1);
+            h++;
+        }
+        if (B > b->blk_threads) return fail(VC_ERR_ARG, "an instance's smallest block exceeds the block threads");
+        d.blk_h = h;
+        const int T = (int)(B * (b->blk_threads / B));
+        for (int s0 = 0; s0 < d.S; s0 += T) {
+            BatchTile t;
+            t.inst = i;
+            t.start = s0;
+            t.count = std::min(T, d.S - s0);
+            t.pad_ = 0;
+            tiles.push_back(t);
+            b->h_btiles_of[i]++;
+        }
+    }
+    b->nbtiles = (int)tiles.size();
+    if (b->d_btiles) cudaFree(b->d_btiles);
+    b->d_btiles = nullptr;
+    VC_CUDA(cudaMalloc((void**)&b->d_btiles, sizeof(BatchTile) * tiles.size()));
+    VC_CUDA(cudaMemcpyAsync(b->d_btiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(b->btiles_of, b->h_btiles_of.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaMemcpyAsync(b->d_desc, b->h_desc.data(), sizeof(InstDesc) * b->n, cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    b->blk_grid = 0;
+    return VC_OK;
+}
+
 // Kernels in one pass of each loop body (two sweeps per pass); the launch counter adds
 // passes x this after every graph launch, since the graph runs them without a host call.
 constexpr int kViBodyKernels = 5;
@@ -783,6 +862,29 @@ static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandl
     k_bpost<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U, U2);
     k_bmax<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 1, b->U, U2, b->Vb,
                                                          b->Va, nullptr, nullptr);
+    k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
+}
+
+template <int MH>
+static void enqueue_vi_blk_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
+    BatchCtl c = ctl_of(b);
+    c.tiles_of = b->btiles_of;  // the block tiles close each instance's sweep
+    const int threads = (b->blk_threads + 31) / 32 * 32;
+    const size_t smem = 3 * sizeof(float) * (size_t)threads;
+    if (b->blk_grid <= 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bblock<MH>, threads, smem) != cudaSuccess)
+            per_sm = 1;
+        b->blk_grid = std::max(1, std::min(b->nbtiles, std::max(1, per_sm) * b->num_sms));
+    }
+    k_bpost<MH, float, true><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U,
+                                                           b->U2);
+    k_bblock<MH><<<b->blk_grid, threads, smem, cs>>>(b->d_desc, b->d_btiles, b->nbtiles, c, 0, b->blk_passes, b->U,
+                                                    b->U2, b->Va, b->Vb);
+    k_bpost<MH, float, true><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U,
+                                                           b->U2);
+    k_bblock<MH><<<b->blk_grid, threads, smem, cs>>>(b->d_desc, b->d_btiles, b->nbtiles, c, 1, b->blk_passes, b->U,
+                                                    b->U2, b->Vb, b->Va);
     k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
 }
 
@@ -852,6 +954,10 @@ static int build_graphs(Batch* b) {
     };
     if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, vi))) return rc;
     if ((rc = make_loop_graph(&b->g_vi_sl, &b->x_vi_sl, vi_sl))) return rc;
+    auto vi_blk = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        by_mh(b->mh, [&](auto m) { enqueue_vi_blk_body<decltype(m)::value>(b, cs, h); });
+    };
+    if ((rc = make_loop_graph(&b->g_vi_blk, &b->x_vi_blk, vi_blk))) return rc;
     if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, corr))) return rc;
     if ((rc = make_loop_graph(&b->g_kry, &b->x_kry, kry))) return rc;
     return VC_OK;
@@ -867,6 +973,9 @@ static void free_batch(Batch* b) {
     if (b->g_corr) cudaGraphDestroy(b->g_corr);
     if (b->x_kry) cudaGraphExecDestroy(b->x_kry);
     if (b->g_kry) cudaGraphDestroy(b->g_kry);
+    if (b->x_vi_blk) cudaGraphExecDestroy(b->x_vi_blk);
+    if (b->g_vi_blk) cudaGraphDestroy(b->g_vi_blk);
+    if (b->d_btiles) cudaFree(b->d_btiles);
     for (void* p : b->owned) cudaFree(p);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->kr_part) cudaFree(b->kr_part);
@@ -962,7 +1071,7 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
     for (void** pp : f8)
         if (!rc) rc = balloc(b, pp, 8 * T);
     void** fi[] = {(void**)&b->done, (void**)&b->sweeps, (void**)&b->ticket, (void**)&b->tiles_of,
-                   (void**)&b->final_buf, (void**)&b->since_best, (void**)&b->best_res};
+                   (void**)&b->final_buf, (void**)&b->since_best, (void**)&b->best_res, (void**)&b->btiles_of};
     for (void** pp : fi)
         if (!rc) rc = balloc(b, pp, 4 * N);
     if (!rc) rc = balloc(b, (void**)&b->res32, 8 * N);
@@ -995,6 +1104,7 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(descriptors)");
     }
     if (!rc) rc = build_tiles(b, st);
+    if (!rc) rc = build_block_tiles(b, st);
     if (!rc) rc = build_graphs(b);
     if (rc) {
         free_batch(b);
@@ -1040,7 +1150,8 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     // ---- FP32 value iteration of every instance: one graph launch
     VC_CUDA(cudaMemcpyAsync(b->Va, V, 4 * T, cudaMemcpyDeviceToDevice, st));
     if ((rc = reset_loop(b, tol, max_sweeps, st))) return rc;
-    VC_CUDA(cudaGraphLaunch((flags & VC_ITER_SELF_LOOP) ? b->x_vi_sl : b->x_vi, st));
+    VC_CUDA(cudaGraphLaunch((flags & VC_ITER_BLOCK) ? b->x_vi_blk : (flags & VC_ITER_SELF_LOOP) ? b->x_vi_sl : b->x_vi,
+                            st));
     long long vi_iters = 0, corr_iters = 0;
     VC_CUDA(cudaMemcpyAsync(&vi_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
     count_launches(1);
@@ -1167,6 +1278,28 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     }
     if (!all_cert) return fail(VC_ERR_NOT_CONVERGED, "an instance was not certified");
     return VC_OK;
+}
+
+int vc_batch_set_block_iteration(vc_batch* bh, int32_t threads, int32_t passes, void* stream) {
+    set_error("");
+    if (!bh) return fail(VC_ERR_ARG, "NULL handle");
+    if (threads < 32 || threads > 1024) return fail(VC_ERR_ARG, "threads must be in 32..1024");
+    if (passes < 1 || passes > 64) return fail(VC_ERR_ARG, "passes must be in 1..64");
+    Batch* b = (Batch*)bh;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int old_t = b->blk_threads, old_p = b->blk_passes;
+    b->blk_threads = threads;
+    b->blk_passes = passes;
+    int rc = build_block_tiles(b, st);
+    if (rc) {
+        const std::string why = vc_last_error();
+        b->blk_threads = old_t;
+        b->blk_passes = old_p;
+        build_block_tiles(b, st);
+        build_graphs(b);
+        return fail(rc, why);
+    }
+    return build_graphs(b);
 }
 
 // Times the FP32 loop graph for every (tile size, blocks per SM) schedule on this batch

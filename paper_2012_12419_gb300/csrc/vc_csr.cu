@@ -450,10 +450,24 @@ __device__ __forceinline__ double row_dot64(const int64_t* __restrict__ row_ptr,
     return acc;
 }
 
+// The same row with the exact FP64 probabilities a handle keeps beside its stored ones
+// (handles built from a model's FP64 rows; val64 = nullptr: the stored values).
+template <typename VT>
+__device__ __forceinline__ double row_dot64x(const CsrArgs& a, const VT* __restrict__ val,
+                                             const double* __restrict__ val64, int64_t r,
+                                             const double* __restrict__ V) {
+    if (!val64) return row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V);
+    double acc = 0.0;
+    for (int64_t j = a.row_ptr[r]; j < a.row_ptr[r + 1]; j++) acc += val64[j] * V[a.col[j]];
+    return acc;
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) k_csr_bellman64(CsrArgs a, double gamma, const double* __restrict__ V_in,
                                                             double* __restrict__ V_out, int32_t* __restrict__ pi,
-                                                            double* __restrict__ qgap, SweepCtl sc) {
+                                                            double* __restrict__ qgap, SweepCtl sc,
+                                                            const double* __restrict__ val64,
+                                                            const double* __restrict__ R64) {
     const VT* val = reinterpret_cast<const VT*>(a.val);
     double res = 0.0;
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(kThreads) k_csr_bellman64(CsrArgs a, double ga
             const int64_t r = (int64_t)s * a.A + act;
             const float rr = a.R[r];
             if (rr == -INFINITY) continue;
-            const double qv = (double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V_in);
+            const double qv = (R64 ? R64[r] : (double)rr) + gamma * row_dot64x<VT>(a, val, val64, r, V_in);
             if (qv > best) {
                 second = best;
                 best = qv;
@@ -486,7 +500,8 @@ __global__ void __launch_bounds__(kThreads) k_csr_bellman64(CsrArgs a, double ga
 template <typename VT>
 __global__ void __launch_bounds__(kThreads) k_csr_resid64(CsrArgs a, double gamma, const int32_t* __restrict__ pi,
                                                           const double* __restrict__ V, float* __restrict__ r_out,
-                                                          SweepCtl sc) {
+                                                          SweepCtl sc, const double* __restrict__ val64,
+                                                          const double* __restrict__ R64) {
     const VT* val = reinterpret_cast<const VT*>(a.val);
     double mx = 0.0;
     for (int s = blockIdx.x * kThreads + threadIdx.x; s < a.S; s += gridDim.x * kThreads) {
@@ -498,7 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_csr_resid64(CsrArgs a, double gamm
             r_out[s] = 0.0f;
             continue;
         }
-        const double rd = (double)rr + gamma * row_dot64<VT>(a.row_ptr, a.col, val, a.scale, r, V) - V[s];
+        const double rd = (R64 ? R64[r] : (double)rr) + gamma * row_dot64x<VT>(a, val, val64, r, V) - V[s];
         r_out[s] = (float)rd;
         mx = fmax(mx, fabs(rd));
     }
@@ -801,9 +816,11 @@ int csr_bellman64(Mdp* m, const double* V_in, double* V_out, int32_t* pi, double
     const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
     count_launches(1);
     if ((m->fmt & 0xF) == VC_CSR_BF16)
-        k_csr_bellman64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc);
+        k_csr_bellman64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc,
+                                                                       m->val64, m->R64);
     else
-        k_csr_bellman64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc);
+        k_csr_bellman64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, V_in, V_out, pi, qgap, sc, m->val64,
+                                                                    m->R64);
     VC_CUDA(cudaGetLastError());
     return VC_OK;
 }
@@ -812,9 +829,9 @@ int csr_resid64(Mdp* m, const int32_t* pi, const double* V64, float* r, SweepCtl
     const CsrArgs a = args_of(m, nullptr, nullptr, nullptr, nullptr);
     count_launches(1);
     if ((m->fmt & 0xF) == VC_CSR_BF16)
-        k_csr_resid64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc);
+        k_csr_resid64<uint16_t><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc, m->val64, m->R64);
     else
-        k_csr_resid64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc);
+        k_csr_resid64<float><<<state_grid(m), kThreads, 0, st>>>(a, m->gamma, pi, V64, r, sc, m->val64, m->R64);
     VC_CUDA(cudaGetLastError());
     return VC_OK;
 }

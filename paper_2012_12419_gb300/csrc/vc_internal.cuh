@@ -286,6 +286,7 @@ struct SweepCtl {
     int out_index;
     const int32_t* pi_ref;
     int self_loop;  // FP32 sweeps: solve each action's self-transition (q_self_loop)
+    int block;      // FP32 sweeps of an implicit handle: Algorithm 4's in-block passes (k_block)
 };
 
 // Q value with the row's self-transition solved exactly: the fixed point in W of
@@ -402,6 +403,127 @@ __device__ __forceinline__ float block_max_dyn(float v) {
     return r;
 }
 
+// Algorithm 4's in-block "episodes" (Section V-H) over one tile of whole blocks, with each
+// action's self-transition solved.  A block is the 2(Q+1)(C+1)^h consecutive states that
+// share the occupancies of hosts h..H-1: every queue length, phase and occupancy of the h
+// inner hosts.  The events of the inner hosts, the arrivals and the phase flips of a state
+// stay in its block, everything else leaves it, so a tile of whole blocks needs no block
+// index at all.  Given the pass-1 values of the previous iterate V (U(x) = R(x) + gamma
+// E[V(next) | x] and defer's self-transition-solved W(x), from k_post<SL> or k_bpost<SL>),
+// the tile runs `passes` local Jacobi passes in shared memory in which a successor inside
+// the state's block takes the block's previous local values Vl and every other successor
+// V.  Each pass corrects the pass-1 values by the in-block terms only:
+//   U_l(x) = U(x) + gamma ((1 - p_move(x)) (Vl(x) - V(x)) + D(x)),
+//   W_l(x) = W(x) + gamma D(x) / ((1 - gamma) + gamma p_move(x)),
+//   D(x) = sum over the in-block events e of x of p_e (Vl(y_e) - V(y_e));
+// a placement on an outer host a leaves the block, and of its post-decision state's events
+// only the completion on host a (merged with the departure when host a was empty) comes
+// back, to s - 2.  The first pass therefore reproduces the plain self-transition sweep bit
+// for bit; p passes over blocks of B states are the block iteration of the oracle's CSR
+// routine with tile B (the sums differ only in rounding).  One thread per state (blockDim
+// >= count); smem holds 3 x blockDim floats; res / vabs accumulate max|V' - V| and |V'|.
+template <int MH>
+__device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c, int h, int start, int count,
+                                           int passes, const float* __restrict__ Vin, const float* __restrict__ U,
+                                           const float* __restrict__ W, float* __restrict__ V_out, float* smem,
+                                           Ctl* ctl, float& res, float& vabs) {
+    float* Vg = smem;                    // previous iterate on the tile
+    float* Vl = smem + blockDim.x;       // local values of the previous pass
+    float* Ul = smem + 2 * blockDim.x;   // corrected pass-1 values of the current pass
+    const int i = threadIdx.x;
+    const bool act = i < count;
+    const int s = start + i;
+    Digits d;
+    float ug = 0.0f, wg = 0.0f, vg = 0.0f, pm = 0.0f, den = 1.0f;
+    float uo[MH], pin[MH];
+    if (act) {
+        decode<MH>(md, s, d);
+        vg = Vin[s];
+        ug = U[s];
+        wg = W[s];
+        Vg[i] = vg;
+        Vl[i] = vg;
+        // probability that an event leaves s read as a post-decision state (pass-1 order)
+#pragma unroll
+        for (int k = 0; k < MH; k++) {
+            if (k < md.H) {
+                const int o = d.occ[k];
+                if (o == 1) {
+                    pm += c.pc[k] + c.pd[k];
+                } else if (o > 1) {
+                    pm += c.pc[k] * (float)o;
+                    pm += c.pd[k];
+                }
+            }
+        }
+        if (d.q < md.Q) pm += c.pa;
+        pm += d.ph ? c.pf1 : c.pf0;
+        den = fmaf(c.gamma, pm, 1.0f - c.gamma);
+        // placements on outer hosts: the pass-1 value of their post-decision state and the
+        // probability of its one event back into the block
+#pragma unroll
+        for (int k = 0; k < MH; k++) {
+            const bool f = k >= h && d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1) &&
+                           VC_IN_BOUNDS(ctl, s + md.stride[k] - 2 < md.S);
+            uo[k] = f ? U[s + md.stride[k] - 2] : -INFINITY;
+            pin[k] = k < md.H ? c.pc[k] * (float)(d.occ[k] + 1) + (d.occ[k] == 0 ? c.pd[k] : 0.0f) : 0.0f;
+        }
+    }
+    __syncthreads();
+    float vnew = vg;
+    for (int pass = 0; pass < passes; pass++) {
+        float wl = wg;
+        if (act) {
+            float D = 0.0f;
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                if (k < h) {
+                    const int o = d.occ[k];
+                    const int j1 = i - md.stride[k];
+                    if (o == 1) {
+                        D = fmaf(c.pc[k] + c.pd[k], Vl[j1] - Vg[j1], D);
+                    } else if (o > 1) {
+                        const int j0 = i - o * md.stride[k];
+                        D = fmaf(c.pc[k] * (float)o, Vl[j1] - Vg[j1], D);
+                        D = fmaf(c.pd[k], Vl[j0] - Vg[j0], D);
+                    }
+                }
+            }
+            if (d.q < md.Q) D = fmaf(c.pa, Vl[i + 2] - Vg[i + 2], D);
+            const int jf = d.ph ? i - 1 : i + 1;
+            D = fmaf(d.ph ? c.pf1 : c.pf0, Vl[jf] - Vg[jf], D);
+            Ul[i] = ug + c.gamma * fmaf(1.0f - pm, Vl[i] - Vg[i], D);
+            wl = wg + __fdiv_rn(c.gamma * D, den);
+        }
+        __syncthreads();
+        if (act) {
+            float best = -INFINITY;
+            const float back = (d.q >= 1) ? Vl[i - 2] - Vg[i - 2] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                float u = -INFINITY;
+                if (k < h) {
+                    if (d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1))
+                        u = Ul[i + md.stride[k] - 2];
+                } else if (uo[k] != -INFINITY) {
+                    u = uo[k] + c.gamma * pin[k] * back;
+                }
+                if (u > best) best = u;
+            }
+            if (wl > best) best = wl;  // defer last: ties keep the lower action
+            vnew = best;
+        }
+        __syncthreads();
+        if (act) Vl[i] = vnew;
+        __syncthreads();
+    }
+    if (act) {
+        V_out[s] = vnew;
+        res = fmaxf(res, fabsf(vnew - vg));
+        vabs = fmaxf(vabs, fabsf(vnew));
+    }
+}
+
 __device__ __forceinline__ unsigned int fbits(float x) { return __float_as_uint(x); }
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
@@ -499,6 +621,8 @@ struct Mdp {
     void* val = nullptr;        // float or uint16 (bf16)
     float* scale = nullptr;     // BF16 per-row scale
     float* R = nullptr;         // [S*A], -inf = infeasible
+    double* val64 = nullptr;    // exact FP64 probabilities beside val (handles built from a model's
+    double* R64 = nullptr;      // FP64 rows without a register generator); the FP64 steps use them
     double* rate_tab = nullptr; // rates.occ_tab (device, owned)
     CsrPlan plan;
     std::string tune_report;    // candidates and times of the last autotune
@@ -530,6 +654,11 @@ struct Mdp {
     int64_t device_bytes = 0;
     int num_sms = 0;
     long long spin_polls = -1;  // bounded-wait cap for the pipelined sweeps (-1 = the default)
+    // in-block iteration of the implicit form (VC_ITER_BLOCK): blocks of the states of
+    // blk_h inner hosts' occupancies (B = 2(Q+1)(C+1)^blk_h), blk_passes local passes
+    int blk_h = -1;             // -1: the largest h with B <= 1024
+    int blk_passes = 4;
+    int blk_grid = 0;           // resident blocks of k_block (0: not yet queried)
 };
 
 // Process-wide count of kernels this library has enqueued.
@@ -553,6 +682,8 @@ int count_model_rows(Mdp* m, cudaStream_t st);
 int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
                    const float* row_scale, const float* R, cudaStream_t st);
 int plan_csr(Mdp* m, cudaStream_t st);
+// CSR of the binary-action model (vc_binary.cu), with its exact FP64 values and rewards.
+int build_csr_binary(Mdp* m, const vc_binary_params* p, cudaStream_t st);
 // Sliced layout (vc_sell.cu): build from the stored CSR, sweep, sweep bytes.
 int build_sliced(Mdp* m, cudaStream_t st);
 int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out);
@@ -562,6 +693,9 @@ int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us);
 
 // Grid of the persistent state-parallel kernels.
 int state_grid(const Mdp* m);
+
+// Inner hosts and block size of the in-block iteration of an implicit handle.
+int block_shape(const Mdp* m, int* h_out, int* B_out);
 
 // One FP32 Bellman backup V_in -> V_out (implicit or CSR), optional policy / gap.
 int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc,

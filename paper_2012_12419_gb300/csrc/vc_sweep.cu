@@ -17,6 +17,7 @@
 // (MH) so the per-host loops issue no dead iterations up to 8 hosts.
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "vc_internal.cuh"
@@ -214,6 +215,29 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
     finish_block<T>(sc, res, vabs, sweep);
 }
 
+// ------------------------------------------------------- implicit: in-block iteration
+// (block_tile, the local passes over one tile of blocks, lives in vc_internal.cuh: the
+// batched loop runs the same routine per instance.)
+template <int MH>
+__global__ void __launch_bounds__(1024) k_block(Model md, Coef<float> c, int h, int T, int passes,
+                                                const float* __restrict__ Vin, const float* __restrict__ U,
+                                                const float* __restrict__ W, float* __restrict__ V_out,
+                                                SweepCtl sc) {
+    extern __shared__ float blk_sm[];
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    const int ntiles = (md.S + T - 1) / T;
+    float res = 0.0f, vabs = 0.0f;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int start = t * T;
+        block_tile<MH>(md, c, h, start, min(T, md.S - start), passes, Vin, U, W, V_out, blk_sm, sc.ctl, res, vabs);
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max_dyn(res);
+    vabs = block_max_dyn(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
 // ------------------------------------------------ implicit: mixed-precision refinement
 // Policy residual in FP64, r(s) = U64(x_pi(s)) - V64(s) with U64 = R + gamma E[V64(next) | x]
 // from the FP64 pass-1 kernel over every post-decision state (coalesced: thread x gathers
@@ -333,9 +357,60 @@ static int by_h(const Mdp* m, F&& f) {
     }
 }
 
+// Inner hosts and states of the blocks of the in-block iteration: h as set on the handle,
+// else the largest h whose block of 2(Q+1)(C+1)^h states fits 1024 threads.
+int block_shape(const Mdp* m, int* h_out, int* B_out) {
+    int h = m->blk_h;
+    if (h < 0) {
+        h = 0;
+        long long B = 2LL * (m->md.Q + 1);
+        while (h < m->md.H && B * (m->md.C + 1) <= 1024) {
+            B *= (m->md.C + 1);
+            h++;
+        }
+    }
+    long long B = 2LL * (m->md.Q + 1);
+    for (int k = 0; k < h; k++) B *= (m->md.C + 1);
+    if (h > m->md.H || B > 1024) return fail(VC_ERR_ARG, "a block of the in-block iteration exceeds 1024 states");
+    *h_out = h;
+    *B_out = (int)B;
+    return VC_OK;
+}
+
+static int launch_block(Mdp* m, const float* V_in, float* V_out, SweepCtl sc, cudaStream_t st) {
+    int h = 0, B = 0, rc;
+    if ((rc = block_shape(m, &h, &B))) return rc;
+    // tiles of whole blocks, about 512 states (one block if it is larger)
+    const int T = B * std::max(1, 512 / B);
+    const int threads = (T + 31) / 32 * 32;
+    const size_t smem = 3 * sizeof(float) * (size_t)threads;
+    const int g = state_grid(m);
+    SweepCtl sc1 = sc;
+    if (sc1.mode != kModeLoop32) sc1.mode = kModeNone;
+    count_launches(2);
+    return by_h(m, [&](auto mh) {
+        constexpr int MH = decltype(mh)::value;
+        if (m->blk_grid <= 0) {
+            int per_sm = 0;
+            VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_block<MH>, threads, smem));
+            m->blk_grid = std::max(1, per_sm) * (m->num_sms > 0 ? m->num_sms : 148);
+        }
+        const int ntiles = (m->S + T - 1) / T;
+        k_post<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
+        k_block<MH><<<std::min(ntiles, m->blk_grid), threads, smem, st>>>(m->md, m->c32, h, T, m->blk_passes, V_in,
+                                                                           m->U32, m->U32s, V_out, sc);
+        VC_CUDA(cudaGetLastError());
+        return (int)VC_OK;
+    });
+}
+
 int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc,
                    cudaStream_t st) {
     if (!implicit_sweeps(m)) return csr_sweep32(m, V_in, V_out, pi, qgap, sc, st);
+    if (sc.block) {
+        if (pi || qgap) return fail(VC_ERR_ARG, "the in-block iteration returns values only");
+        return launch_block(m, V_in, V_out, sc, st);
+    }
     const int g = state_grid(m);
     SweepCtl sc1 = sc;
     if (sc1.mode != kModeLoop32) sc1.mode = kModeNone;

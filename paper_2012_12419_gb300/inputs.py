@@ -12,7 +12,10 @@ Instance recipe (the paper, Section V, leaves the instance unspecified):
     delta_1..delta_H ~ U[0.01, 0.1], f ~ U[0.3, 0.7]; reward weights
     (w_occ, w_loss, w_q) = (1, -5, -0.1);
   * the batched workload first draws H in {2..5}, C in {2..6}, Q in {3..12} and
-    gamma in {0.9, 0.95, 0.99} per instance, then the rates.
+    gamma in {0.9, 0.95, 0.99} per instance, then the rates;
+  * the binary-action model (the paper's A = {-1, 1}): H clouds of C VMs, requests of
+    1..J VMs, mu_1..mu_H ~ U[0.2, 1], lambda ~ U[0.5, 2], delta_1..delta_H ~ U[0.01, 0.1],
+    reward constants (beta_vc, beta_tc, gamma_vc) = (1, 1.2, 1).
 Uniform doubles are the top 53 bits of SplitMix64 outputs; the seed of a named
 workload is its index in the list below.
 """
@@ -31,6 +34,18 @@ WORKLOADS = {
     "precision_sub": dict(seed=3, H=5, C=4, Q=15, gamma=0.95),  # S = 100,000,   A = 6
     "grad": dict(seed=4, H=6, C=4, Q=10, gamma=0.95),         # S = 343,750,    A = 7
 }
+
+# The paper's binary-action model (A = {-1, 1}): H vehicular clouds of C VMs each, requests
+# of 1..J VMs; S = (1 + H J) (C+1)^H, A = 2.
+BINARY_WORKLOADS = {
+    "binary": dict(seed=5, H=6, C=6, J=3, gamma=0.95),        # S = 2,235,331,  A = 2
+    "binary_tiny": dict(seed=6, H=2, C=3, J=2, gamma=0.95),   # S = 80,         A = 2
+    "binary_mid": dict(seed=7, H=4, C=4, J=2, gamma=0.95),    # S = 5,625,      A = 2
+}
+
+# Reward constants of the paper's numerical section: VM reward per VC, VM cost per paid
+# traditional-cloud VM, penalty per idle VC VM.
+BINARY_WEIGHTS = dict(beta_vc=1.0, beta_tc=1.2, gamma_vc=1.0)
 
 WEIGHTS = dict(w_occ=1.0, w_loss=-5.0, w_q=-0.1)
 
@@ -84,6 +99,29 @@ def workload(name: str) -> dict:
     if name == "batched":
         raise ValueError("use batch_params() for the batched workload")
     return make_params(w["H"], w["C"], w["Q"], w["gamma"], w["seed"])
+
+
+def binary_params(H: int, C: int, J: int, gamma: float, seed: int) -> dict:
+    """One instance of the binary-action model: per VC k a completion rate mu_k ~ U[0.2, 1]
+    per busy VM, then the request rate lambda ~ U[0.5, 2], then departure rates
+    delta_k ~ U[0.01, 0.1] (the placement model's draws without f), and the paper's reward
+    constants."""
+    rng = SplitMix64(seed)
+    mu = [rng.uniform(0.2, 1.0) for _ in range(H)]
+    lam = rng.uniform(0.5, 2.0)
+    delta = [rng.uniform(0.01, 0.1) for _ in range(H)]
+    p = dict(H=H, C=C, J=J, gamma=gamma, mu=mu, lam=lam, delta=delta)
+    p.update(BINARY_WEIGHTS)
+    return p
+
+
+def binary_workload(name: str) -> dict:
+    w = BINARY_WORKLOADS[name]
+    return binary_params(w["H"], w["C"], w["J"], w["gamma"], w["seed"])
+
+
+def binary_num_states(H: int, C: int, J: int) -> int:
+    return (1 + H * J) * (C + 1) ** H
 
 
 def batch_params(n: int = 512, seed: int = 2) -> list:

@@ -36,6 +36,7 @@ VC_ITER_FP32_ONLY = 1
 VC_ITER_ACCURATE = 2
 VC_ITER_PLAIN_CORRECTION = 4
 VC_ITER_SELF_LOOP = 8
+VC_ITER_BLOCK = 16
 
 FORMATS = {"implicit": VC_IMPLICIT, "csr_f32": VC_CSR_F32, "csr_bf16": VC_CSR_BF16}
 
@@ -44,7 +45,8 @@ EXPORTS = [
     "vc_bellman64", "vc_evaluate_policy", "vc_destroy", "vc_mdp_export_csr", "vc_bellman32", "vc_kernel_launches", "vc_autotune", "vc_autotune_report", "vc_bellman32_noalloc",
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
     "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
-    "vc_set_wait_limit", "vc_aaa_intervals", "vc_objective",
+    "vc_set_wait_limit", "vc_aaa_intervals", "vc_objective", "vc_build_binary_mdp", "vc_set_block_iteration",
+    "vc_block_iteration_info", "vc_batch_set_block_iteration",
 ]
 
 
@@ -59,6 +61,15 @@ class Params(ctypes.Structure):
         ("H", ctypes.c_int32), ("C", ctypes.c_int32), ("Q", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("lam", ctypes.c_double), ("f", ctypes.c_double), ("gamma", ctypes.c_double),
         ("w_occ", ctypes.c_double), ("w_loss", ctypes.c_double), ("w_q", ctypes.c_double),
+        ("mu", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class BinaryParams(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int32), ("C", ctypes.c_int32), ("J", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("lam", ctypes.c_double), ("gamma", ctypes.c_double), ("beta_vc", ctypes.c_double),
+        ("beta_tc", ctypes.c_double), ("gamma_vc", ctypes.c_double),
         ("mu", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -163,6 +174,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_set_wait_limit.argtypes = [vp, i64]
         L.vc_aaa_intervals.argtypes = [vp, vp, vp, i32, i32, i32, dbl, dbl, dbl, vp, vp, vp]
         L.vc_objective.argtypes = [vp, vp, i64, vp, vp]
+        L.vc_build_binary_mdp.argtypes = [ctypes.POINTER(BinaryParams), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.vc_set_block_iteration.argtypes = [vp, i32, i32]
+        L.vc_block_iteration_info.argtypes = [vp, vp, vp, vp]
+        L.vc_batch_set_block_iteration.argtypes = [vp, i32, i32, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -206,6 +221,16 @@ def _params(p: dict):
     return c, (mu, delta)
 
 
+def _binary_params(p: dict):
+    H = int(p["H"])
+    mu = (ctypes.c_double * H)(*[float(v) for v in p["mu"][:H]])
+    delta = (ctypes.c_double * H)(*[float(v) for v in p["delta"][:H]])
+    c = BinaryParams(H, int(p["C"]), int(p["J"]), 0, float(p["lam"]), float(p["gamma"]), float(p["beta_vc"]),
+                     float(p["beta_tc"]), float(p["gamma_vc"]), ctypes.cast(mu, ctypes.POINTER(ctypes.c_double)),
+                     ctypes.cast(delta, ctypes.POINTER(ctypes.c_double)))
+    return c, (mu, delta)
+
+
 def _dev():
     if not torch.cuda.is_available():
         raise RuntimeError("vcmdp needs a CUDA device")
@@ -230,6 +255,20 @@ class MDP:
         cp, keep = _params(params)
         h = ctypes.c_void_p()
         _check(L.vc_build_mdp(ctypes.byref(cp), code, _stream(stream), ctypes.byref(h)))
+        del keep
+        return cls(h)
+
+    @classmethod
+    def build_binary(cls, params: dict, fmt: str = "csr_f32", direct: bool = False, sliced: bool = False,
+                     stream=None) -> "MDP":
+        """The paper's binary-action model (A = {-1, 1}; action 0 is -1, the paid cloud)
+        as an explicit CSR built on the device, exact FP64 rows kept for the refinement."""
+        L = load()
+        _dev()
+        code = FORMATS[fmt] | (VC_DIRECT if direct else 0) | (VC_SLICED if sliced else 0)
+        cp, keep = _binary_params(params)
+        h = ctypes.c_void_p()
+        _check(L.vc_build_binary_mdp(ctypes.byref(cp), code, _stream(stream), ctypes.byref(h)))
         del keep
         return cls(h)
 
@@ -291,13 +330,16 @@ class MDP:
     # ------------------------------------------------------------------------- solve
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
                       want_v64: bool = True, want_pi: bool = True, stream=None, raise_on_nonconvergence=True,
-                      accurate: bool = False, plain_correction: bool = False, self_loop: bool = False):
+                      accurate: bool = False, plain_correction: bool = False, self_loop: bool = False,
+                      block: bool = False):
         """Algorithm 3 on the device.  Returns (V fp32, V64 fp64 or None, pi int32 or None, stats dict).
 
         accurate=True certifies the error rather than the residual: max|V64 - V*| <= tol / 2.
         plain_correction=True solves the refinement's correction equation by fixed-point
         sweeps instead of BiCGSTAB.  self_loop=True runs the FP32 sweeps with each action's
-        self-transition solved exactly (VC_ITER_SELF_LOOP: same V*, fewer sweeps)."""
+        self-transition solved exactly (VC_ITER_SELF_LOOP: same V*, fewer sweeps).  block=True
+        (implicit handles) adds Algorithm 4's in-block passes (VC_ITER_BLOCK, shaped by
+        set_block_iteration)."""
         dev = _dev()
         S = self.S
         if V is None:
@@ -306,13 +348,24 @@ class MDP:
         pi = torch.empty(S, dtype=torch.int32, device=dev) if want_pi else None
         st = Stats()
         flags = ((VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
-                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0) | (VC_ITER_SELF_LOOP if self_loop else 0))
+                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0) | (VC_ITER_SELF_LOOP if self_loop else 0)
+                 | (VC_ITER_BLOCK if block else 0))
         rc = load().vc_value_iterate(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                      flags, ctypes.byref(st), _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
         d = st.as_dict()
         d["status"] = rc
         return V, V64, pi, d
+
+    def set_block_iteration(self, inner_hosts: int = -1, passes: int = 4) -> None:
+        """Blocks of 2(Q+1)(C+1)^inner_hosts states (-1: the largest up to 1024) and the local
+        passes per global sweep of the in-block iteration."""
+        _check(load().vc_set_block_iteration(self._h, int(inner_hosts), int(passes)))
+
+    def block_iteration_info(self) -> dict:
+        h, B, p = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().vc_block_iteration_info(self._h, ctypes.byref(h), ctypes.byref(B), ctypes.byref(p)))
+        return {"inner_hosts": h.value, "block_states": B.value, "passes": p.value}
 
     def extract_policy(self, V, stream=None):
         dev = _dev()
@@ -444,12 +497,13 @@ class Batch:
 
     def value_iterate(self, V=None, tol: float = 1e-6, max_sweeps: int = 1_000_000, fp32_only: bool = False,
                       stream=None, raise_on_nonconvergence=True, accurate: bool = False,
-                      plain_correction: bool = False, self_loop: bool = False):
+                      plain_correction: bool = False, self_loop: bool = False, block: bool = False):
         """Returns (V fp32 [total], V64 [total] or None, pi [total] or None, list of per-instance dicts, status).
 
         accurate=True certifies every instance's error: max|V64_i - V*_i| <= tol / 2.
         plain_correction=True solves the correction equations by fixed-point sweeps.
-        self_loop=True runs the FP32 loop with each action's self-transition solved."""
+        self_loop=True runs the FP32 loop with each action's self-transition solved;
+        block=True adds Algorithm 4's in-block passes (set_block_iteration)."""
         dev = _dev()
         if V is None:
             V = torch.zeros(self.total, dtype=torch.float32, device=dev)
@@ -457,12 +511,18 @@ class Batch:
         pi = torch.empty(self.total, dtype=torch.int32, device=dev)
         st = (BatchStats * self.n)()
         flags = ((VC_ITER_FP32_ONLY if fp32_only else 0) | (VC_ITER_ACCURATE if accurate else 0)
-                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0) | (VC_ITER_SELF_LOOP if self_loop else 0))
+                 | (VC_ITER_PLAIN_CORRECTION if plain_correction else 0) | (VC_ITER_SELF_LOOP if self_loop else 0)
+                 | (VC_ITER_BLOCK if block else 0))
         rc = load().vc_value_iterate_batch(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                            flags, st, _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
         stats = [{k: getattr(s, k) for k, _ in BatchStats._fields_} for s in st]
         return V, V64, pi, stats, rc
+
+    def set_block_iteration(self, threads: int = 512, passes: int = 4, stream=None) -> None:
+        """In-block iteration of every instance: blocks of at most `threads` states (the
+        largest 2(Q+1)(C+1)^h that fits), `passes` local passes per global sweep."""
+        _check(load().vc_batch_set_block_iteration(self._h, int(threads), int(passes), _stream(stream)))
 
     def autotune(self, sweeps: int = 20, stream=None) -> float:
         ms = ctypes.c_double()
