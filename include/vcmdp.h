@@ -304,11 +304,11 @@ int vc_bellman32(vc_mdp* m, const float* V, float* V_out, int32_t* pi, float* qg
 
 /*
  * Shape of the in-block iteration of an implicit handle (VC_ITER_BLOCK; Algorithm 4's
- * "episodes" inside a block, Section V-H): inner_hosts = h gives blocks of
+ * "episodes" inside a block, Section V-H): inner_hosts = h (0..3) gives blocks of
  * B = 2(Q+1)(C+1)^h states (at most 1024; -1 = the largest such h, the default), passes the
  * local passes per global sweep (1..64, default 4; 1 is the plain self-transition sweep).
- * Applies to later solves.  VC_ERR_ARG for explicit handles, passes outside 1..64 or a block
- * of more than 1024 states.
+ * Applies to later solves.  VC_ERR_ARG for explicit handles, passes outside 1..64, h above
+ * 3 or H, or a block of more than 1024 states.
  */
 int vc_set_block_iteration(vc_mdp* m, int32_t inner_hosts, int32_t passes);
 
@@ -518,9 +518,9 @@ int vc_value_iterate_batch(vc_batch* b, float* V, double* V64_out, int32_t* pi_o
 /*
  * Shape of the batched in-block iteration (VC_ITER_BLOCK; Algorithm 4's "episodes", Section
  * V-H): each instance i is cut into blocks of 2(Q_i+1)(C_i+1)^h_i states with the largest
- * h_i that fits `threads` (32..1024, default 512), packed into tiles of whole blocks of at
- * most `threads` states, one thread per state; `passes` (1..64, default 4) local passes per
- * global sweep.  Rebuilds the tile table and recaptures the loop graphs on `stream`
+ * h_i <= 3 that fits `threads` (32..1024, default 512), packed into tiles of whole blocks of
+ * at most `threads` states, one thread per state; `passes` (1..64, default 4) local passes
+ * per global sweep.  Rebuilds the tile table and recaptures the loop graphs on `stream`
  * (synchronised).  VC_ERR_ARG for out-of-range values or an instance whose smallest block
  * 2(Q_i+1) exceeds `threads` (the previous shape is kept).
  */

@@ -264,9 +264,11 @@ __global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __re
     }
 }
 
-// Algorithm 4's in-block iteration for every active instance (VC_ITER_BLOCK): the block
-// tile table cuts each instance into tiles of whole blocks of 2(Q_i+1)(C_i+1)^h_i states
-// (block_tile), one thread per state; each tile closes its share of the instance's sweep.
+// Algorithm 4's in-block iteration for every active instance (VC_ITER_BLOCK).  The block
+// tile table cuts each instance into chunks of whole sub-tiles; a sub-tile (tile.pad_
+// states) is whole blocks of 2(Q_i+1)(C_i+1)^h_i states that block_tile iterates with one
+// thread per state; a chunk loads its descriptor once and closes its share of the
+// instance's sweep once.
 template <int MH>
 __global__ void __launch_bounds__(1024) k_bblock(const InstDesc* __restrict__ descs,
                                                  const BatchTile* __restrict__ tiles, int ntiles, BatchCtl c,
@@ -287,8 +289,20 @@ __global__ void __launch_bounds__(1024) k_bblock(const InstDesc* __restrict__ de
         load_desc(descs, tl.inst, sd);
         __syncthreads();
         float res = 0.0f, vabs = 0.0f;
-        block_tile<MH>(sd.md, sd.c32, sd.blk_h, tl.start, tl.count, passes, V_in + sd.off, U + sd.off, U2 + sd.off,
-                       V_out + sd.off, bb_sm, nullptr, res, vabs);
+        const float* Vi = V_in + sd.off;
+        const float* Ui = U + sd.off;
+        const float* Wi = U2 + sd.off;
+        float* Vo = V_out + sd.off;
+        for (int s0 = tl.start; s0 < tl.start + tl.count; s0 += tl.pad_) {
+            const int cnt = min(tl.pad_, tl.start + tl.count - s0);
+            switch (sd.blk_h) {
+                case 0: block_tile<MH, 0>(sd.md, sd.c32, s0, cnt, passes, Vi, Ui, Wi, Vo, bb_sm, nullptr, res, vabs); break;
+                case 1: block_tile<MH, 1>(sd.md, sd.c32, s0, cnt, passes, Vi, Ui, Wi, Vo, bb_sm, nullptr, res, vabs); break;
+                case 2: block_tile<MH, 2>(sd.md, sd.c32, s0, cnt, passes, Vi, Ui, Wi, Vo, bb_sm, nullptr, res, vabs); break;
+                default: block_tile<MH, 3>(sd.md, sd.c32, s0, cnt, passes, Vi, Ui, Wi, Vo, bb_sm, nullptr, res, vabs); break;
+            }
+            __syncthreads();  // the next sub-tile reuses the shared arrays
+        }
         res = block_max_dyn(res);
         vabs = block_max_dyn(vabs);
         if (threadIdx.x == 0) close_instance(c, tl.inst, res, vabs, parity, parity ^ 1);
@@ -806,6 +820,8 @@ static int build_tiles(Batch* b, cudaStream_t st) {
     return VC_OK;
 }
 
+constexpr int kBlockChunk = 2048;  // states per chunk of the batched in-block iteration
+
 // Block tile table of the in-block iteration: per instance the largest h with a block of
 // B = 2(Q+1)(C+1)^h <= blk_threads states, tiles of floor(blk_threads / B) whole blocks
 // (the last one shorter), tiles of an instance contiguous.
@@ -816,19 +832,20 @@ static int build_block_tiles(Batch* b, cudaStream_t st) {
         InstDesc& d = b->h_desc[i];
         int h = 0;
         long long B = 2LL * (d.md.Q + 1);
-        while (h < d.md.H && B * (d.md.C + 1) <= b->blk_threads) {
+        while (h < d.md.H && h < kBlockMaxInner && B * (d.md.C + 1) <= b->blk_threads) {
             B *= (d.md.C + 1);
             h++;
         }
         if (B > b->blk_threads) return fail(VC_ERR_ARG, "an instance's smallest block exceeds the block threads");
         d.blk_h = h;
-        const int T = (int)(B * (b->blk_threads / B));
-        for (int s0 = 0; s0 < d.S; s0 += T) {
+        const int T = (int)(B * (b->blk_threads / B));        // sub-tile: whole blocks
+        const int chunk = T * std::max(1, kBlockChunk / T);    // chunk: whole sub-tiles
+        for (int s0 = 0; s0 < d.S; s0 += chunk) {
             BatchTile t;
             t.inst = i;
             t.start = s0;
-            t.count = std::min(T, d.S - s0);
-            t.pad_ = 0;
+            t.count = std::min(chunk, d.S - s0);
+            t.pad_ = T;
             tiles.push_back(t);
             b->h_btiles_of[i]++;
         }
@@ -870,7 +887,7 @@ static void enqueue_vi_blk_body(Batch* b, cudaStream_t cs, cudaGraphConditionalH
     BatchCtl c = ctl_of(b);
     c.tiles_of = b->btiles_of;  // the block tiles close each instance's sweep
     const int threads = (b->blk_threads + 31) / 32 * 32;
-    const size_t smem = 3 * sizeof(float) * (size_t)threads;
+    const size_t smem = 4 * sizeof(float) * (size_t)threads;
     if (b->blk_grid <= 0) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bblock<MH>, threads, smem) != cudaSuccess)

@@ -17,6 +17,7 @@ constexpr int kMaxH = VC_MAX_HOSTS;
 constexpr int kRing = 64;          // residual slots, indexed by sweep number mod kRing
 constexpr int kStallSweeps = 64;   // FP32 sweeps without a new best residual = FP32 floor
 constexpr int kThreads = 256;      // block size of the state-parallel kernels
+constexpr int kBlockMaxInner = 3;  // inner hosts of an in-block iteration block (VC_ITER_BLOCK)
 
 // ------------------------------------------------------------------ error plumbing
 void set_error(const std::string& msg);
@@ -421,21 +422,24 @@ __device__ __forceinline__ float block_max_dyn(float v) {
 // back, to s - 2.  The first pass therefore reproduces the plain self-transition sweep bit
 // for bit; p passes over blocks of B states are the block iteration of the oracle's CSR
 // routine with tile B (the sums differ only in rounding).  One thread per state (blockDim
-// >= count); smem holds 3 x blockDim floats; res / vabs accumulate max|V' - V| and |V'|.
-template <int MH>
-__device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c, int h, int start, int count,
+// >= count); smem holds 4 x blockDim floats; res / vabs accumulate max|V' - V| and |V'|.
+// HIN = h, the inner hosts, a compile-time constant so the inner loops are static and the
+// outer hosts' digits die after the set-up.
+template <int MH, int HIN>
+__device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c, int start, int count,
                                            int passes, const float* __restrict__ Vin, const float* __restrict__ U,
                                            const float* __restrict__ W, float* __restrict__ V_out, float* smem,
                                            Ctl* ctl, float& res, float& vabs) {
-    float* Vg = smem;                    // previous iterate on the tile
-    float* Vl = smem + blockDim.x;       // local values of the previous pass
-    float* Ul = smem + 2 * blockDim.x;   // corrected pass-1 values of the current pass
+    float* Vg = smem;                     // previous iterate on the tile
+    float* Vl = smem + blockDim.x;        // local values, double-buffered across passes
+    float* Vn = smem + 2 * blockDim.x;
+    float* Ul = smem + 3 * blockDim.x;    // corrected pass-1 values of the current pass
     const int i = threadIdx.x;
     const bool act = i < count;
     const int s = start + i;
     Digits d;
-    float ug = 0.0f, wg = 0.0f, vg = 0.0f, pm = 0.0f, den = 1.0f;
-    float uo[MH], pin[MH];
+    float ug = 0.0f, wg = 0.0f, vg = 0.0f, g1 = 0.0f, gd = 0.0f;
+    float uo[MH], gp[MH];
     if (act) {
         decode<MH>(md, s, d);
         vg = Vin[s];
@@ -444,6 +448,7 @@ __device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c
         Vg[i] = vg;
         Vl[i] = vg;
         // probability that an event leaves s read as a post-decision state (pass-1 order)
+        float pm = 0.0f;
 #pragma unroll
         for (int k = 0; k < MH; k++) {
             if (k < md.H) {
@@ -458,15 +463,16 @@ __device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c
         }
         if (d.q < md.Q) pm += c.pa;
         pm += d.ph ? c.pf1 : c.pf0;
-        den = fmaf(c.gamma, pm, 1.0f - c.gamma);
-        // placements on outer hosts: the pass-1 value of their post-decision state and the
-        // probability of its one event back into the block
+        g1 = c.gamma * (1.0f - pm);
+        gd = __fdiv_rn(c.gamma, fmaf(c.gamma, pm, 1.0f - c.gamma));
+        // placements on outer hosts: the pass-1 value of their post-decision state and
+        // gamma times the probability of its one event back into the block
 #pragma unroll
         for (int k = 0; k < MH; k++) {
-            const bool f = k >= h && d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1) &&
+            const bool f = k >= HIN && d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1) &&
                            VC_IN_BOUNDS(ctl, s + md.stride[k] - 2 < md.S);
             uo[k] = f ? U[s + md.stride[k] - 2] : -INFINITY;
-            pin[k] = k < md.H ? c.pc[k] * (float)(d.occ[k] + 1) + (d.occ[k] == 0 ? c.pd[k] : 0.0f) : 0.0f;
+            gp[k] = k < md.H ? c.gamma * (c.pc[k] * (float)(d.occ[k] + 1) + (d.occ[k] == 0 ? c.pd[k] : 0.0f)) : 0.0f;
         }
     }
     __syncthreads();
@@ -477,7 +483,7 @@ __device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c
             float D = 0.0f;
 #pragma unroll
             for (int k = 0; k < MH; k++) {
-                if (k < h) {
+                if (k < HIN) {
                     const int o = d.occ[k];
                     const int j1 = i - md.stride[k];
                     if (o == 1) {
@@ -492,8 +498,8 @@ __device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c
             if (d.q < md.Q) D = fmaf(c.pa, Vl[i + 2] - Vg[i + 2], D);
             const int jf = d.ph ? i - 1 : i + 1;
             D = fmaf(d.ph ? c.pf1 : c.pf0, Vl[jf] - Vg[jf], D);
-            Ul[i] = ug + c.gamma * fmaf(1.0f - pm, Vl[i] - Vg[i], D);
-            wl = wg + __fdiv_rn(c.gamma * D, den);
+            Ul[i] = fmaf(g1, Vl[i] - Vg[i], fmaf(c.gamma, D, ug));
+            wl = fmaf(gd, D, wg);
         }
         __syncthreads();
         if (act) {
@@ -502,20 +508,22 @@ __device__ __forceinline__ void block_tile(const Model& md, const Coef<float>& c
 #pragma unroll
             for (int k = 0; k < MH; k++) {
                 float u = -INFINITY;
-                if (k < h) {
+                if (k < HIN) {
                     if (d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1))
                         u = Ul[i + md.stride[k] - 2];
                 } else if (uo[k] != -INFINITY) {
-                    u = uo[k] + c.gamma * pin[k] * back;
+                    u = fmaf(gp[k], back, uo[k]);
                 }
                 if (u > best) best = u;
             }
             if (wl > best) best = wl;  // defer last: ties keep the lower action
             vnew = best;
+            Vn[i] = vnew;
         }
         __syncthreads();
-        if (act) Vl[i] = vnew;
-        __syncthreads();
+        float* t = Vl;
+        Vl = Vn;
+        Vn = t;
     }
     if (act) {
         V_out[s] = vnew;

@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
 // ------------------------------------------------------- implicit: in-block iteration
 // (block_tile, the local passes over one tile of blocks, lives in vc_internal.cuh: the
 // batched loop runs the same routine per instance.)
-template <int MH>
-__global__ void __launch_bounds__(1024) k_block(Model md, Coef<float> c, int h, int T, int passes,
+template <int MH, int HIN>
+__global__ void __launch_bounds__(1024) k_block(Model md, Coef<float> c, int T, int passes,
                                                 const float* __restrict__ Vin, const float* __restrict__ U,
                                                 const float* __restrict__ W, float* __restrict__ V_out,
                                                 SweepCtl sc) {
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(1024) k_block(Model md, Coef<float> c, int h, 
     float res = 0.0f, vabs = 0.0f;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int start = t * T;
-        block_tile<MH>(md, c, h, start, min(T, md.S - start), passes, Vin, U, W, V_out, blk_sm, sc.ctl, res, vabs);
+        block_tile<MH, HIN>(md, c, start, min(T, md.S - start), passes, Vin, U, W, V_out, blk_sm, sc.ctl, res, vabs);
     }
     if (sc.mode == kModeNone) return;
     res = block_max_dyn(res);
@@ -364,14 +364,15 @@ int block_shape(const Mdp* m, int* h_out, int* B_out) {
     if (h < 0) {
         h = 0;
         long long B = 2LL * (m->md.Q + 1);
-        while (h < m->md.H && B * (m->md.C + 1) <= 1024) {
+        while (h < m->md.H && h < kBlockMaxInner && B * (m->md.C + 1) <= 1024) {
             B *= (m->md.C + 1);
             h++;
         }
     }
     long long B = 2LL * (m->md.Q + 1);
     for (int k = 0; k < h; k++) B *= (m->md.C + 1);
-    if (h > m->md.H || B > 1024) return fail(VC_ERR_ARG, "a block of the in-block iteration exceeds 1024 states");
+    if (h > m->md.H || h > kBlockMaxInner || B > 1024)
+        return fail(VC_ERR_ARG, "a block of the in-block iteration needs at most 3 inner hosts and 1024 states");
     *h_out = h;
     *B_out = (int)B;
     return VC_OK;
@@ -383,22 +384,23 @@ static int launch_block(Mdp* m, const float* V_in, float* V_out, SweepCtl sc, cu
     // tiles of whole blocks, about 512 states (one block if it is larger)
     const int T = B * std::max(1, 512 / B);
     const int threads = (T + 31) / 32 * 32;
-    const size_t smem = 3 * sizeof(float) * (size_t)threads;
+    const size_t smem = 4 * sizeof(float) * (size_t)threads;
     const int g = state_grid(m);
     SweepCtl sc1 = sc;
     if (sc1.mode != kModeLoop32) sc1.mode = kModeNone;
     count_launches(2);
     return by_h(m, [&](auto mh) {
         constexpr int MH = decltype(mh)::value;
+        auto kern = h == 0 ? k_block<MH, 0> : h == 1 ? k_block<MH, 1> : h == 2 ? k_block<MH, 2> : k_block<MH, 3>;
         if (m->blk_grid <= 0) {
             int per_sm = 0;
-            VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_block<MH>, threads, smem));
+            VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
             m->blk_grid = std::max(1, per_sm) * (m->num_sms > 0 ? m->num_sms : 148);
         }
         const int ntiles = (m->S + T - 1) / T;
         k_post<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
-        k_block<MH><<<std::min(ntiles, m->blk_grid), threads, smem, st>>>(m->md, m->c32, h, T, m->blk_passes, V_in,
-                                                                           m->U32, m->U32s, V_out, sc);
+        kern<<<std::min(ntiles, m->blk_grid), threads, smem, st>>>(m->md, m->c32, T, m->blk_passes, V_in, m->U32,
+                                                                   m->U32s, V_out, sc);
         VC_CUDA(cudaGetLastError());
         return (int)VC_OK;
     });
