@@ -390,6 +390,7 @@ def run_batched(args):
         "residual64": max(s["residual64"] for s in last),
         "build_ms": build_ms,
         "schedule": {k: int(binfo[k]) for k in ("tile_states", "blocks_per_sm", "grid", "tiles")},
+        "whole_instance_in_one_block": b.small_instances(),
         "autotune": b.autotune_report().strip().splitlines() if tune_ms else None,
         "gpu_launches": int(launches),
         "clocks": ck,
@@ -506,6 +507,7 @@ def batched_record(args, native, torch, dev, stream, steps: int = 5):
         "residual64": max(x["residual64"] for x in last),
         "schedule": {k: int(binfo[k]) for k in ("tile_states", "blocks_per_sm", "grid", "tiles")},
         "autotuned_sweep_ms": tune_ms / 20,
+        "whole_instance_in_one_block": b.small_instances(),
     }
     out["vs_per_instance"] = batched_vs_per_instance(args, ps, b, native, torch, dev, stream)
     out["self_loop"] = batched_self_loop(args, b, torch, dev, stream)
@@ -534,7 +536,7 @@ def batched_self_loop(args, b, torch, dev, stream):
            "max_abs_V64_difference": float((V1 - V0).abs().max())}
     # Algorithm 4's in-block passes on every instance (blocks of at most `threads` states)
     shapes, best = [], None
-    for threads, passes in ((256, 2), (256, 4), (512, 2), (512, 4), (1024, 4)):
+    for threads, passes in ((256, 2), (256, 4), (512, 2), (512, 4), (512, 8)):
         b.set_block_iteration(threads, passes)
 
         def solve():

@@ -516,9 +516,25 @@ int vc_value_iterate_batch(vc_batch* b, float* V, double* V64_out, int32_t* pi_o
                            int flags, vc_batch_stats* per_inst, void* stream);
 
 /*
+ * Instances solved whole inside one thread block (no paper counterpart; Algorithm 4's block
+ * taken as the whole instance): before the FP32 graph loop, each instance with S <=
+ * max_states (capped by the device's shared memory: 16 bytes per state for the iterate pair
+ * and the pass-1 values; the default is that cap, about 14,000 states on GB300) is swept in
+ * one CTA with its values in shared memory and its own step-3 test after every sweep --
+ * the loop's arithmetic, so the iterate and the sweep count are the loop's bit for bit --
+ * and the loop skips it.  With VC_ITER_BLOCK such an instance is one block iterated by the
+ * self-transition sweeps to its test.  0 disables the path.  Synchronises `stream`.
+ * VC_ERR_ARG for max_states < 0.
+ */
+int vc_batch_set_small_instances(vc_batch* b, int32_t max_states, void* stream);
+
+/* Instances taking that path and the state limit in force (host outputs, nullable). */
+int vc_batch_small_instances(const vc_batch* b, int32_t* count, int32_t* max_states);
+
+/*
  * Shape of the batched in-block iteration (VC_ITER_BLOCK; Algorithm 4's "episodes", Section
  * V-H): each instance i is cut into blocks of 2(Q_i+1)(C_i+1)^h_i states with the largest
- * h_i <= 3 that fits `threads` (32..1024, default 512), packed into tiles of whole blocks of
+ * h_i <= 3 that fits `threads` (32..512, default 512), packed into tiles of whole blocks of
  * at most `threads` states, one thread per state; `passes` (1..64, default 4) local passes
  * per global sweep.  Rebuilds the tile table and recaptures the loop graphs on `stream`
  * (synchronised).  VC_ERR_ARG for out-of-range values or an instance whose smallest block

@@ -751,11 +751,18 @@ int vc_value_iterate(vc_mdp* mh, float* V, double* V64_out, int32_t* pi_out, dou
         // below tol (up to FP32 rounding of e).
         int32_t* pcur = m->pi;
         int32_t* pnew = m->pi2;
-        {
+        if ((rc = launch_f32_to_f64(V, m->V64a, m->S, st))) goto out;
+        if ((m->fmt & 0xF) == VC_CSR_BF16 && (m->has_model || m->val64)) {
+            // BF16 storage: the FP32 iterate carries the BF16 matrix's modelling error, so
+            // the first policy is the argmax of an FP64 backup of it with the exact model
+            // (one policy-improvement step of the exact MDP from that iterate) rather than
+            // the stored matrix's argmax, which would only be corrected by a later round
+            SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
+            if ((rc = launch_bellman64(m, m->V64a, m->V64b, pcur, nullptr, sc, st))) goto out;
+        } else {
             SweepCtl sc{m->ctl, kModeNone, 0, nullptr};
             if ((rc = launch_sweep32(m, V, nullptr, pcur, nullptr, sc, st))) goto out;
         }
-        if ((rc = launch_f32_to_f64(V, m->V64a, m->S, st))) goto out;
         double* cur = m->V64a;
         double* other = m->V64b;
         const long long eval_max = std::max<long long>(100000, max_sweeps);

@@ -26,6 +26,14 @@
 
 namespace vc {
 
+// Named check of the kernel launches just enqueued (a refused launch leaves its error
+// pending; this reports it where it happened instead of at a later call).
+#define VC_LAUNCHED(what)                                                  \
+    do {                                                                   \
+        const cudaError_t le_ = cudaGetLastError();                        \
+        if (le_ != cudaSuccess) return vc::cuda_fail(le_, "launch: " what); \
+    } while (0)
+
 struct InstDesc {
     Model md;
     Coef<float> c32;
@@ -69,6 +77,28 @@ __device__ __forceinline__ void load_desc(const InstDesc* __restrict__ descs, in
     for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+// Algorithm 3's step-3 test for one instance after sweep k: residual r below
+// max(tol, 4 ulp(max|V|)) -> 1, no new best residual for kStallSweeps sweeps (the FP32
+// floor) -> 3, k reaching max_sweeps -> 2, else 0 (best_res / since_best updated).
+__device__ __forceinline__ int sweep_verdict(double tol, float r, float vm, long long k, long long max_sweeps,
+                                             float& best_res, int& since_best) {
+    int e = 0;
+    frexpf(vm, &e);
+    const double ulp = (vm > 0.0f) ? ldexp(1.0, e - 24) : 0.0;
+    const double tol_eff = fmax(tol, 4.0 * ulp);
+    int done = 0;
+    if ((double)r < tol_eff) {
+        done = 1;
+    } else if (r < best_res) {
+        best_res = r;
+        since_best = 0;
+    } else if (++since_best >= kStallSweeps) {
+        done = 3;
+    }
+    if (!done && k >= max_sweeps) done = 2;
+    return done;
+}
+
 // Closes an instance's sweep once its last tile arrives (thread 0 of that tile).
 __device__ void close_instance(const BatchCtl& c, int i, float res, float vmax, int parity, int out_buf) {
     const double tol = *c.tol * (c.tol_scale ? (double)c.tol_scale[i] : 1.0);
@@ -87,20 +117,11 @@ __device__ void close_instance(const BatchCtl& c, int i, float res, float vmax, 
     const int k = c.sweeps[i] + 1;
     c.sweeps[i] = k;
     c.final_buf[i] = out_buf;
-    int e = 0;
-    frexpf(vm, &e);
-    const double ulp = (vm > 0.0f) ? ldexp(1.0, e - 24) : 0.0;
-    const double tol_eff = fmax(tol, 4.0 * ulp);
-    int done = 0;
-    if ((double)r < tol_eff) {
-        done = 1;
-    } else if (r < c.best_res[i]) {
-        c.best_res[i] = r;
-        c.since_best[i] = 0;
-    } else if (++c.since_best[i] >= kStallSweeps) {
-        done = 3;
-    }
-    if (!done && k >= *c.max_sweeps) done = 2;
+    float best = c.best_res[i];
+    int since = c.since_best[i];
+    const int done = sweep_verdict(tol, r, vm, k, *c.max_sweeps, best, since);
+    c.best_res[i] = best;
+    c.since_best[i] = since;
     if (done) {
         c.done[i] = done;
         atomicSub(c.active, 1);
@@ -308,6 +329,99 @@ __global__ void __launch_bounds__(1024) k_bblock(const InstDesc* __restrict__ de
         if (threadIdx.x == 0) close_instance(c, tl.inst, res, vabs, parity, parity ^ 1);
         __syncthreads();
     }
+}
+
+// Whole-instance solve in one CTA for instances whose values fit in shared memory: the
+// same Jacobi sweeps as the graph loop (k_bpost + k_bmax arithmetic, Eq. 18's backup or the
+// self-transition solve) with V, U (and W) in shared memory, the instance's own step-3 test
+// after every sweep (sweep_verdict, as close_instance applies it), and no kernel launch or
+// grid-wide exchange per sweep: Algorithm 4's in-block iteration with the whole instance as
+// the block.  Iterates and sweep counts are those of the graph loop bit for bit.  The
+// result goes to Va (final_buf 0).  It runs on side streams concurrently with the graph
+// loop, which skips these instances (k_bmark_small flags them before either starts and the
+// loop's active count leaves them out).
+template <int MH, bool SL>
+__global__ void __launch_bounds__(512) k_bsmall(const InstDesc* __restrict__ descs, const int* __restrict__ list,
+                                                 int nlist, BatchCtl c, float* __restrict__ Va) {
+    extern __shared__ float sm_small[];
+    __shared__ InstDesc sd;
+    __shared__ int sh_done;
+    for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+        const int inst = list[li];
+        load_desc(descs, inst, sd);
+        __syncthreads();
+        const int S = sd.S;
+        float* Vc = sm_small;          // current iterate
+        float* Vn = sm_small + S;      // next iterate
+        float* Us = sm_small + 2 * S;  // pass-1 values
+        float* Ws = sm_small + 3 * S;  // defer's self-transition-solved values (SL)
+        float* Vg = Va + sd.off;
+        for (int j = threadIdx.x; j < S; j += blockDim.x) Vc[j] = Vg[j];
+        const double tol = *c.tol * (c.tol_scale ? (double)c.tol_scale[inst] : 1.0);
+        const long long max_sweeps = *c.max_sweeps;
+        float best_res = INFINITY;
+        int since_best = 0;
+        long long k = 0;
+        if (threadIdx.x == 0) sh_done = 0;
+        __syncthreads();
+        while (true) {
+            for (int x = threadIdx.x; x < S; x += blockDim.x) {
+                Digits d;
+                decode<MH>(sd.md, x, d);
+                const float rx = b_reward<MH>(sd.md, sd.c32, d);
+                if constexpr (SL) {
+                    float u, w;
+                    post_and_defer<MH>(sd.md, sd.c32, Vc, x, d, rx, u, w);
+                    Us[x] = u;
+                    Ws[x] = w;
+                } else {
+                    Us[x] = rx + sd.c32.gamma * b_expect<MH>(sd.md, sd.c32, Vc, x, d);
+                }
+            }
+            __syncthreads();
+            float res = 0.0f, vabs = 0.0f;
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
+                Digits d;
+                decode<MH>(sd.md, s, d);
+                float best = -INFINITY;
+                if (d.q >= 1) {
+#pragma unroll
+                    for (int kk = 0; kk < MH; kk++) {
+                        if (kk < sd.md.H && d.occ[kk] < sd.md.C && (kk == sd.md.H - 1 || d.ph == 1)) {
+                            const float u = Us[s + sd.md.stride[kk] - 2];
+                            if (u > best) best = u;
+                        }
+                    }
+                }
+                const float u = SL ? Ws[s] : Us[s];
+                if (u > best) best = u;
+                Vn[s] = best;
+                res = fmaxf(res, fabsf(best - Vc[s]));
+                vabs = fmaxf(vabs, fabsf(best));
+            }
+            res = block_max_dyn(res);
+            vabs = block_max_dyn(vabs);
+            k++;
+            if (threadIdx.x == 0) sh_done = sweep_verdict(tol, res, vabs, k, max_sweeps, best_res, since_best);
+            __syncthreads();
+            float* t = Vc;
+            Vc = Vn;
+            Vn = t;
+            if (sh_done) break;
+        }
+        for (int j = threadIdx.x; j < S; j += blockDim.x) Vg[j] = Vc[j];
+        if (threadIdx.x == 0) {
+            c.sweeps[inst] = (int)k;
+            c.final_buf[inst] = 0;
+            c.done[inst] = sh_done;
+        }
+        __syncthreads();
+    }
+}
+
+// Flags the instances of the whole-instance path so that the graph loop skips them.
+__global__ void k_bmark_small(int* __restrict__ done, const int* __restrict__ list, int n) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) done[list[j]] = 5;
 }
 
 // Keeps the graph's while loop running while instances are active and budget remains.
@@ -720,6 +834,20 @@ struct Batch {
     std::vector<int> h_btiles_of;
     BatchTile* d_btiles = nullptr;
     int* btiles_of = nullptr;
+    // instances solved whole in one CTA's shared memory (k_bsmall) before the graph loop
+    int small_cap = 0;       // states that fit: (opt-in shared memory - reserve) / 16 bytes
+    int small_max = 0;       // instances with S <= small_max take that path (0: none)
+    int n_small = 0;
+    int* d_small = nullptr;  // the instances, grouped by size class
+    // size classes (largest S of a class at most small_cap / 8, / 4, / 2, / 1): each class
+    // is one launch on its own side stream with shared memory for its largest instance
+    static constexpr int kSmallClasses = 4;
+    int cls_first[kSmallClasses] = {0, 0, 0, 0};
+    int cls_count[kSmallClasses] = {0, 0, 0, 0};
+    int cls_S[kSmallClasses] = {0, 0, 0, 0};
+    cudaStream_t side[kSmallClasses] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kSmallClasses] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraph_t g_vi = nullptr, g_vi_sl = nullptr, g_corr = nullptr, g_kry = nullptr, g_vi_blk = nullptr;
     cudaGraphExec_t x_vi = nullptr, x_vi_sl = nullptr, x_corr = nullptr, x_kry = nullptr, x_vi_blk = nullptr;
     std::vector<void*> owned;
@@ -787,8 +915,41 @@ static BatchKrylov kry_of(Batch* b) {
     return K;
 }
 
+// Destroys every captured loop graph.  The graphs hold the tile tables' device addresses,
+// so they go before a table is freed or rebuilt: a failed rebuild then leaves no graph that
+// could run on freed memory, and the solves refuse to start until build_graphs succeeds.
+static std::string g_destroy_note;  // first failed destroy (diagnostics)
+
+static void destroy_graphs(Batch* b) {
+    cudaGraphExec_t* xs[] = {&b->x_vi, &b->x_vi_sl, &b->x_vi_blk, &b->x_corr, &b->x_kry};
+    cudaGraph_t* gs[] = {&b->g_vi, &b->g_vi_sl, &b->g_vi_blk, &b->g_corr, &b->g_kry};
+    int k = 0;
+    for (auto* x : xs) {
+        if (*x) {
+            const cudaError_t e = cudaGraphExecDestroy(*x);
+            if (e != cudaSuccess && g_destroy_note.empty())
+                g_destroy_note = "exec " + std::to_string(k) + ": " + cudaGetErrorString(e);
+        }
+        *x = nullptr;
+        k++;
+    }
+    k = 0;
+    for (auto* g : gs) {
+        if (*g) {
+            const cudaError_t e = cudaGraphDestroy(*g);
+            if (e != cudaSuccess && g_destroy_note.empty())
+                g_destroy_note = "graph " + std::to_string(k) + ": " + cudaGetErrorString(e);
+        }
+        *g = nullptr;
+        k++;
+    }
+}
+
+static bool graphs_ready(const Batch* b) { return b->x_vi && b->x_vi_sl && b->x_vi_blk && b->x_corr && b->x_kry; }
+
 // Tile table for tile size ts; tiles of an instance are contiguous in the table.
 static int build_tiles(Batch* b, cudaStream_t st) {
+    destroy_graphs(b);
     std::vector<BatchTile> tiles;
     b->h_tiles_of.assign(b->n, 0);
     for (int i = 0; i < b->n; i++) {
@@ -826,6 +987,7 @@ constexpr int kBlockChunk = 2048;  // states per chunk of the batched in-block i
 // B = 2(Q+1)(C+1)^h <= blk_threads states, tiles of floor(blk_threads / B) whole blocks
 // (the last one shorter), tiles of an instance contiguous.
 static int build_block_tiles(Batch* b, cudaStream_t st) {
+    destroy_graphs(b);
     std::vector<BatchTile> tiles;
     b->h_btiles_of.assign(b->n, 0);
     for (int i = 0; i < b->n; i++) {
@@ -862,6 +1024,68 @@ static int build_block_tiles(Batch* b, cudaStream_t st) {
     return VC_OK;
 }
 
+// List of the instances solved whole in one CTA (S <= small_max), grouped into size
+// classes and uploaded for k_bsmall.
+static int build_small_list(Batch* b, cudaStream_t st) {
+    std::vector<int> list;
+    b->n_small = 0;
+    for (int c = 0; c < Batch::kSmallClasses; c++) {
+        const int hi = b->small_cap >> (Batch::kSmallClasses - 1 - c);
+        const int lo = c == 0 ? 0 : (b->small_cap >> (Batch::kSmallClasses - c));
+        b->cls_first[c] = (int)list.size();
+        b->cls_S[c] = 0;
+        for (int i = 0; i < b->n; i++) {
+            const int S = b->h_desc[i].S;
+            if (S <= b->small_max && S > lo && S <= hi) {
+                list.push_back(i);
+                b->cls_S[c] = std::max(b->cls_S[c], S);
+            }
+        }
+        b->cls_count[c] = (int)list.size() - b->cls_first[c];
+    }
+    b->n_small = (int)list.size();
+    if (b->d_small) cudaFree(b->d_small);
+    b->d_small = nullptr;
+    if (list.empty()) return VC_OK;
+    VC_CUDA(cudaMalloc((void**)&b->d_small, sizeof(int) * list.size()));
+    VC_CUDA(cudaMemcpyAsync(b->d_small, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    return VC_OK;
+}
+
+// Starts the whole-instance solves (Eq. 18's backup, or the self-transition solve: SL,
+// which the in-block iteration uses for a whole-instance block): flags them for the loop
+// on `st`, then one launch per size class on its side stream, forked from `st`.
+template <int MH>
+static int launch_small(Batch* b, bool sl, cudaStream_t st) {
+    if (b->n_small == 0) return VC_OK;
+    count_launches(1);
+    k_bmark_small<<<(b->n_small + 255) / 256, 256, 0, st>>>(b->done, b->d_small, b->n_small);
+    VC_LAUNCHED("k_bmark_small");
+    VC_CUDA(cudaEventRecord(b->fork_ev, st));
+    auto kern = sl ? k_bsmall<MH, true> : k_bsmall<MH, false>;
+    for (int c = 0; c < Batch::kSmallClasses; c++) {
+        if (b->cls_count[c] == 0) continue;
+        const size_t smem = 16 * (size_t)b->cls_S[c];
+        const int threads = b->cls_S[c] <= 2048 ? 128 : b->cls_S[c] <= 4096 ? 256 : 512;
+        VC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        VC_CUDA(cudaStreamWaitEvent(b->side[c], b->fork_ev, 0));
+        count_launches(1);
+        kern<<<b->cls_count[c], threads, smem, b->side[c]>>>(b->d_desc, b->d_small + b->cls_first[c],
+                                                              b->cls_count[c], ctl_of(b), b->Va);
+        VC_LAUNCHED("the whole-instance kernel");
+        VC_CUDA(cudaEventRecord(b->join_ev[c], b->side[c]));
+    }
+    return VC_OK;
+}
+
+// Makes `st` wait for the whole-instance solves.
+static int join_small(Batch* b, cudaStream_t st) {
+    for (int c = 0; c < Batch::kSmallClasses; c++)
+        if (b->n_small && b->cls_count[c]) VC_CUDA(cudaStreamWaitEvent(st, b->join_ev[c], 0));
+    return VC_OK;
+}
+
 // Kernels in one pass of each loop body (two sweeps per pass); the launch counter adds
 // passes x this after every graph launch, since the graph runs them without a host call.
 constexpr int kViBodyKernels = 5;
@@ -888,12 +1112,6 @@ static void enqueue_vi_blk_body(Batch* b, cudaStream_t cs, cudaGraphConditionalH
     c.tiles_of = b->btiles_of;  // the block tiles close each instance's sweep
     const int threads = (b->blk_threads + 31) / 32 * 32;
     const size_t smem = 4 * sizeof(float) * (size_t)threads;
-    if (b->blk_grid <= 0) {
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bblock<MH>, threads, smem) != cudaSuccess)
-            per_sm = 1;
-        b->blk_grid = std::max(1, std::min(b->nbtiles, std::max(1, per_sm) * b->num_sms));
-    }
     k_bpost<MH, float, true><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U,
                                                            b->U2);
     k_bblock<MH><<<b->blk_grid, threads, smem, cs>>>(b->d_desc, b->d_btiles, b->nbtiles, c, 0, b->blk_passes, b->U,
@@ -927,7 +1145,7 @@ static void enqueue_kry_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHand
 // One graph: a WHILE node (default condition 1 at every launch) whose body is built by
 // capturing `body` on a private stream.
 template <typename Body>
-static int make_loop_graph(cudaGraph_t* g, cudaGraphExec_t* x, Body&& body) {
+static int make_loop_graph(cudaGraph_t* g, cudaGraphExec_t* x, const std::string& name, Body&& body) {
     if (*x) cudaGraphExecDestroy(*x);
     if (*g) cudaGraphDestroy(*g);
     *x = nullptr;
@@ -947,16 +1165,55 @@ static int make_loop_graph(cudaGraph_t* g, cudaGraphExec_t* x, Body&& body) {
     VC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     VC_CUDA(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     body(cs, h);
+    const cudaError_t le = cudaGetLastError();  // a launch refused while capturing
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &captured);
     cudaStreamDestroy(cs);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (batched loop body)");
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (captured && captured != bodyg) cudaGraphDestroy(captured);
+        cudaGraphDestroy(*g);
+        *g = nullptr;
+        if (le != cudaSuccess)
+            return cuda_fail(le, ("kernel launch while capturing the batched loop body (" + name + ")").c_str());
+        return cuda_fail(e, "cudaStreamEndCapture (batched loop body)");
+    }
     VC_CUDA(cudaGraphInstantiate(x, *g, 0));
     return VC_OK;
 }
 
+// Resident grid of the batched in-block kernel for the current block threads (queried
+// before any capture; a failed query falls back to one CTA per SM).
+template <int MH>
+static void block_grid_of(Batch* b) {
+    const int threads = (b->blk_threads + 31) / 32 * 32;
+    const size_t smem = 4 * sizeof(float) * (size_t)threads;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bblock<MH>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    b->blk_grid = std::max(1, std::min(b->nbtiles, std::max(1, per_sm) * b->num_sms));
+}
+
+static int build_graphs_once(Batch* b);
+
+// Captures every loop graph, all or nothing: after a failure no graph is left.
 static int build_graphs(Batch* b) {
+    destroy_graphs(b);
+    const int rc = build_graphs_once(b);
+    if (rc) destroy_graphs(b);
+    return rc;
+}
+
+static int build_graphs_once(Batch* b) {
     int rc;
+    {
+        const cudaError_t pe = cudaGetLastError();
+        if (pe != cudaSuccess)
+            return cuda_fail(pe, ("pending before the graph captures; destroy note: " + g_destroy_note).c_str());
+    }
+    by_mh(b->mh, [&](auto m) { block_grid_of<decltype(m)::value>(b); });
+    VC_LAUNCHED("pending after the block-kernel occupancy query");
     auto vi = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
         by_mh(b->mh, [&](auto m) { enqueue_vi_body<decltype(m)::value, false>(b, cs, h); });
     };
@@ -969,42 +1226,41 @@ static int build_graphs(Batch* b) {
     auto kry = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
         by_mh(b->mh, [&](auto m) { enqueue_kry_body<decltype(m)::value>(b, cs, h); });
     };
-    if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, vi))) return rc;
-    if ((rc = make_loop_graph(&b->g_vi_sl, &b->x_vi_sl, vi_sl))) return rc;
+    if ((rc = make_loop_graph(&b->g_vi, &b->x_vi, "Eq. 18 loop", vi))) return rc;
+    if ((rc = make_loop_graph(&b->g_vi_sl, &b->x_vi_sl, "self-transition loop", vi_sl))) return rc;
     auto vi_blk = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
         by_mh(b->mh, [&](auto m) { enqueue_vi_blk_body<decltype(m)::value>(b, cs, h); });
     };
-    if ((rc = make_loop_graph(&b->g_vi_blk, &b->x_vi_blk, vi_blk))) return rc;
-    if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, corr))) return rc;
-    if ((rc = make_loop_graph(&b->g_kry, &b->x_kry, kry))) return rc;
+    const std::string blk = "in-block loop: grid " + std::to_string(b->blk_grid) + " threads " +
+                            std::to_string((b->blk_threads + 31) / 32 * 32) + " tiles " + std::to_string(b->nbtiles);
+    if ((rc = make_loop_graph(&b->g_vi_blk, &b->x_vi_blk, blk, vi_blk))) return rc;
+    if ((rc = make_loop_graph(&b->g_corr, &b->x_corr, "correction loop", corr))) return rc;
+    if ((rc = make_loop_graph(&b->g_kry, &b->x_kry, "BiCGSTAB loop", kry))) return rc;
     return VC_OK;
 }
 
 static void free_batch(Batch* b) {
     if (!b) return;
-    if (b->x_vi) cudaGraphExecDestroy(b->x_vi);
-    if (b->g_vi) cudaGraphDestroy(b->g_vi);
-    if (b->x_vi_sl) cudaGraphExecDestroy(b->x_vi_sl);
-    if (b->g_vi_sl) cudaGraphDestroy(b->g_vi_sl);
-    if (b->x_corr) cudaGraphExecDestroy(b->x_corr);
-    if (b->g_corr) cudaGraphDestroy(b->g_corr);
-    if (b->x_kry) cudaGraphExecDestroy(b->x_kry);
-    if (b->g_kry) cudaGraphDestroy(b->g_kry);
-    if (b->x_vi_blk) cudaGraphExecDestroy(b->x_vi_blk);
-    if (b->g_vi_blk) cudaGraphDestroy(b->g_vi_blk);
+    destroy_graphs(b);
+    for (int c = 0; c < Batch::kSmallClasses; c++) {
+        if (b->side[c]) cudaStreamDestroy(b->side[c]);
+        if (b->join_ev[c]) cudaEventDestroy(b->join_ev[c]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     if (b->d_btiles) cudaFree(b->d_btiles);
+    if (b->d_small) cudaFree(b->d_small);
     for (void* p : b->owned) cudaFree(p);
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->kr_part) cudaFree(b->kr_part);
     delete b;
 }
 
-static int reset_loop(Batch* b, double tol, long long max_sweeps, cudaStream_t st) {
+static int reset_loop(Batch* b, double tol, long long max_sweeps, cudaStream_t st, int skipped = 0) {
     VC_CUDA(cudaMemcpyAsync(b->tol_d, &tol, sizeof(double), cudaMemcpyHostToDevice, st));
     VC_CUDA(cudaMemcpyAsync(b->max_d, &max_sweeps, sizeof(long long), cudaMemcpyHostToDevice, st));
     count_launches(1);
-    k_binit<<<(b->n + 255) / 256, 256, 0, st>>>(ctl_of(b), b->n, b->n);
-    VC_CUDA(cudaGetLastError());
+    k_binit<<<(b->n + 255) / 256, 256, 0, st>>>(ctl_of(b), b->n, b->n - skipped);
+    VC_LAUNCHED("k_binit");
     // the parameters live in pageable host memory: make the copies complete before return
     VC_CUDA(cudaStreamSynchronize(st));
     return VC_OK;
@@ -1120,8 +1376,21 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
         cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc.data(), sizeof(InstDesc) * N, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(descriptors)");
     }
+    if (!rc) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        b->small_cap = std::max(0, (optin - 4096) / 16);
+        b->small_max = b->small_cap;
+        cudaError_t e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+        for (int c = 0; c < Batch::kSmallClasses && e == cudaSuccess; c++) {
+            e = cudaStreamCreateWithFlags(&b->side[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[c], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) rc = cuda_fail(e, "side streams of the whole-instance path");
+    }
     if (!rc) rc = build_tiles(b, st);
     if (!rc) rc = build_block_tiles(b, st);
+    if (!rc) rc = build_small_list(b, st);
     if (!rc) rc = build_graphs(b);
     if (rc) {
         free_batch(b);
@@ -1164,17 +1433,33 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     cudaStream_t st = (cudaStream_t)stream;
     const size_t T = (size_t)b->total, N = (size_t)b->n;
     int rc;
+    {
+        const cudaError_t pe = cudaGetLastError();
+        if (pe != cudaSuccess) return cuda_fail(pe, "an earlier CUDA call left an error pending");
+    }
+    if (!graphs_ready(b)) return fail(VC_ERR_CUDA, "the batch's loop graphs are not built (a schedule change failed)");
     // ---- FP32 value iteration of every instance: one graph launch
     VC_CUDA(cudaMemcpyAsync(b->Va, V, 4 * T, cudaMemcpyDeviceToDevice, st));
-    if ((rc = reset_loop(b, tol, max_sweeps, st))) return rc;
+    if ((rc = reset_loop(b, tol, max_sweeps, st, b->n_small))) return rc;
+    {
+        const bool sl = (flags & (VC_ITER_SELF_LOOP | VC_ITER_BLOCK)) != 0;
+        int rs = VC_OK;
+        by_mh(b->mh, [&](auto m) { rs = launch_small<decltype(m)::value>(b, sl, st); });
+        if (rs) return rs;
+    }
     VC_CUDA(cudaGraphLaunch((flags & VC_ITER_BLOCK) ? b->x_vi_blk : (flags & VC_ITER_SELF_LOOP) ? b->x_vi_sl : b->x_vi,
                             st));
+    {
+        const cudaError_t ge = cudaGetLastError();
+        if (ge != cudaSuccess) return cuda_fail(ge, "after the FP32 loop graph launch");
+    }
+    if ((rc = join_small(b, st))) return rc;
     long long vi_iters = 0, corr_iters = 0;
     VC_CUDA(cudaMemcpyAsync(&vi_iters, b->iters, 8, cudaMemcpyDeviceToHost, st));
     count_launches(1);
     k_bselect<float, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->final_buf, b->Va,
                                                           b->Vb, V);
-    VC_CUDA(cudaGetLastError());
+    VC_LAUNCHED("k_bselect");
     std::vector<int> done(N), sweeps(N), csweeps(N, 0), cert(N, 0);
     std::vector<double> r64(N, INFINITY);
     VC_CUDA(cudaMemcpyAsync(done.data(), b->done, 4 * N, cudaMemcpyDeviceToHost, st));
@@ -1187,8 +1472,10 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
         // by BiCGSTAB (one graph launch; fixed-point sweeps as the fallback), FP64 update,
         // FP64 Bellman certificate; repeat on failures.
         by_mh(b->mh, [&](auto m) { enqueue_extract<decltype(m)::value>(b, V, b->pi, st); });
+        VC_LAUNCHED("policy extraction");
         count_launches(3);
         k_f32_to_f64_n<<<b->grid, kThreads, 0, st>>>(V, b->V64, (long long)T);
+        VC_LAUNCHED("k_f32_to_f64_n");
         const long long eval_max = std::max<long long>(100000, max_sweeps);
         // Per-instance target of the FP64 residual: tol, or, in accuracy mode,
         // tol (1 - gamma_i) / (2 gamma_i), which bounds max|V64 - V*| by tol / 2.
@@ -1204,6 +1491,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             VC_CUDA(cudaMemsetAsync(b->err, 0, 4, st));
             count_launches(2);
             by_mh(b->mh, [&](auto m) { enqueue_resid<decltype(m)::value>(b, st); });
+            VC_LAUNCHED("FP64 policy residual");
             int herr = 0;
             VC_CUDA(cudaMemcpyAsync(&herr, b->err, 4, cudaMemcpyDeviceToHost, st));
             std::vector<int> cs(N, 0);
@@ -1214,7 +1502,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
                 count_launches(2);
                 k_bkr_reset<<<(b->n + 255) / 256, 256, 0, st>>>(K, b->n, 0.5 * tol, b->tol_scale);
                 k_bkr_init<<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, K);
-                VC_CUDA(cudaGetLastError());
+                VC_LAUNCHED("BiCGSTAB start");
                 VC_CUDA(cudaGraphLaunch(b->x_kry, st));
                 long long kit = 0;
                 std::vector<int> kd(N), ki(N);
@@ -1241,6 +1529,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
                 count_launches(1);
                 k_baxpy<<<b->grid, kThreads, 0, st>>>(b->E0, b->E1, b->d_desc, b->d_tiles, b->ntiles, b->final_buf,
                                                       b->V64);
+                VC_LAUNCHED("k_baxpy");
                 std::vector<int> cs2(N);
                 VC_CUDA(cudaMemcpyAsync(cs2.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
                 VC_CUDA(cudaStreamSynchronize(st));
@@ -1251,6 +1540,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             VC_CUDA(cudaMemsetAsync(b->res64, 0, 8 * N, st));
             count_launches(2);
             by_mh(b->mh, [&](auto m) { enqueue_cert<decltype(m)::value>(b, st); });
+            VC_LAUNCHED("FP64 certificate");
             std::vector<unsigned long long> rb(N);
             VC_CUDA(cudaMemcpyAsync(rb.data(), b->res64, 8 * N, cudaMemcpyDeviceToHost, st));
             VC_CUDA(cudaMemcpyAsync(b->V64, b->V64b, 8 * T, cudaMemcpyDeviceToDevice, st));
@@ -1272,12 +1562,15 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
         if (pi_out) VC_CUDA(cudaMemcpyAsync(pi_out, b->pi, 4 * T, cudaMemcpyDeviceToDevice, st));
     } else {
         if (pi_out) by_mh(b->mh, [&](auto m) { enqueue_extract<decltype(m)::value>(b, V, pi_out, st); });
+        VC_LAUNCHED("policy extraction (FP32 only)");
         if (V64_out) {
             count_launches(1);
             k_f32_to_f64_n<<<b->grid, kThreads, 0, st>>>(V, V64_out, (long long)T);
+            VC_LAUNCHED("k_f32_to_f64_n (FP32 only)");
         }
     }
     VC_CUDA(cudaStreamSynchronize(st));
+    VC_LAUNCHED("end of the batched solve");
     bool any_max = false;
     for (size_t i = 0; i < N; i++) {
         if (done[i] == 0 || done[i] == 2) any_max = true;
@@ -1297,26 +1590,65 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     return VC_OK;
 }
 
+int vc_batch_set_small_instances(vc_batch* bh, int32_t max_states, void* stream) {
+    set_error("");
+    if (!bh) return fail(VC_ERR_ARG, "NULL handle");
+    Batch* b = (Batch*)bh;
+    if (max_states < 0) return fail(VC_ERR_ARG, "max_states must be >= 0");
+    b->small_max = std::min(max_states, b->small_cap);
+    return build_small_list(b, (cudaStream_t)stream);
+}
+
+int vc_batch_small_instances(const vc_batch* bh, int32_t* count, int32_t* max_states) {
+    set_error("");
+    if (!bh) return fail(VC_ERR_ARG, "NULL handle");
+    const Batch* b = (const Batch*)bh;
+    if (count) *count = b->n_small;
+    if (max_states) *max_states = b->small_max;
+    return VC_OK;
+}
+
 int vc_batch_set_block_iteration(vc_batch* bh, int32_t threads, int32_t passes, void* stream) {
     set_error("");
     if (!bh) return fail(VC_ERR_ARG, "NULL handle");
-    if (threads < 32 || threads > 1024) return fail(VC_ERR_ARG, "threads must be in 32..1024");
+    if (threads < 32 || threads > 512) return fail(VC_ERR_ARG, "threads must be in 32..512");
     if (passes < 1 || passes > 64) return fail(VC_ERR_ARG, "passes must be in 1..64");
     Batch* b = (Batch*)bh;
     cudaStream_t st = (cudaStream_t)stream;
+    VC_LAUNCHED("pending before the block shape change");
+    g_destroy_note.clear();
+    {
+        // the kernel's own limit (registers x threads) may be below 1024
+        int lim = 1024;
+        by_mh(b->mh, [&](auto m) {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, k_bblock<decltype(m)::value>) == cudaSuccess) lim = fa.maxThreadsPerBlock;
+            else cudaGetLastError();
+        });
+        if (threads > lim)
+            return fail(VC_ERR_ARG, "threads exceeds the in-block kernel's limit of " + std::to_string(lim));
+    }
+    VC_LAUNCHED("pending after the thread-limit query");
     const int old_t = b->blk_threads, old_p = b->blk_passes;
     b->blk_threads = threads;
     b->blk_passes = passes;
     int rc = build_block_tiles(b, st);
+    if (!rc) {
+        const cudaError_t pe = cudaGetLastError();
+        if (pe != cudaSuccess)
+            rc = cuda_fail(pe, ("pending after the block tile table; destroy note: " + g_destroy_note).c_str());
+    }
+    if (!rc) rc = build_graphs(b);
     if (rc) {
+        // back to the previous shape; if even that cannot be rebuilt, the graphs stay
+        // destroyed and the solves report it
         const std::string why = vc_last_error();
         b->blk_threads = old_t;
         b->blk_passes = old_p;
-        build_block_tiles(b, st);
-        build_graphs(b);
+        if (!build_block_tiles(b, st)) build_graphs(b);
         return fail(rc, why);
     }
-    return build_graphs(b);
+    return VC_OK;
 }
 
 // Times the FP32 loop graph for every (tile size, blocks per SM) schedule on this batch
@@ -1348,6 +1680,7 @@ int vc_batch_autotune(vc_batch* bh, int sweeps, double* best_ms, void* stream) {
                 if ((rc = reset_loop(b, 1e-30, sweeps, st))) return rc;
                 VC_CUDA(cudaEventRecord(e0, st));
                 count_launches((sweeps + 1) / 2 * kViBodyKernels);
+                if (!graphs_ready(b)) return fail(VC_ERR_CUDA, "the batch's loop graphs are not built");
                 VC_CUDA(cudaGraphLaunch(b->x_vi, st));
                 VC_CUDA(cudaEventRecord(e1, st));
                 VC_CUDA(cudaEventSynchronize(e1));

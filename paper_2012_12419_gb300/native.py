@@ -46,7 +46,8 @@ EXPORTS = [
     "vc_value_grad", "vc_build_batch", "vc_batch_info", "vc_batch_offsets", "vc_value_iterate_batch",
     "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
     "vc_set_wait_limit", "vc_aaa_intervals", "vc_objective", "vc_build_binary_mdp", "vc_set_block_iteration",
-    "vc_block_iteration_info", "vc_batch_set_block_iteration",
+    "vc_block_iteration_info", "vc_batch_set_block_iteration", "vc_batch_set_small_instances",
+    "vc_batch_small_instances",
 ]
 
 
@@ -178,6 +179,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_set_block_iteration.argtypes = [vp, i32, i32]
         L.vc_block_iteration_info.argtypes = [vp, vp, vp, vp]
         L.vc_batch_set_block_iteration.argtypes = [vp, i32, i32, vp]
+        L.vc_batch_set_small_instances.argtypes = [vp, i32, vp]
+        L.vc_batch_small_instances.argtypes = [vp, vp, vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -518,6 +521,16 @@ class Batch:
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
         stats = [{k: getattr(s, k) for k, _ in BatchStats._fields_} for s in st]
         return V, V64, pi, stats, rc
+
+    def set_small_instances(self, max_states: int, stream=None) -> None:
+        """Instances of at most max_states states are swept whole in one thread block
+        before the graph loop (0: none; capped by shared memory)."""
+        _check(load().vc_batch_set_small_instances(self._h, int(max_states), _stream(stream)))
+
+    def small_instances(self) -> dict:
+        n, mx = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().vc_batch_small_instances(self._h, ctypes.byref(n), ctypes.byref(mx)))
+        return {"count": n.value, "max_states": mx.value}
 
     def set_block_iteration(self, threads: int = 512, passes: int = 4, stream=None) -> None:
         """In-block iteration of every instance: blocks of at most `threads` states (the

@@ -177,6 +177,7 @@ def test_batched_block_iteration_against_the_oracle(threads, passes):
     ps = [p for p in inputs.batch_params(512, seed=2) if inputs.num_states(p["H"], p["C"], p["Q"]) <= 4000][:14]
     assert {p["gamma"] for p in ps} == {0.9, 0.95, 0.99}
     b = native.Batch(ps)
+    b.set_small_instances(0)  # these instances would otherwise be swept whole in one CTA each
     off = b.offsets
     V0 = _seeded(int(off[-1]), 6, 30.0)
     # one local pass: the self-transition loop, bit for bit
@@ -219,8 +220,13 @@ def test_batched_block_iteration_against_the_oracle(threads, passes):
         assert np.max(np.abs(V64[sl] - Vs)) <= 5e-7 + 1e-9
         assert policy_mismatches(pi[sl], pis, gaps)[0] == 0
     assert sum(s["sweeps"] for s in stats) < sum(s["sweeps"] for s in st_sl)
-    with pytest.raises(native.VcError):
-        b.set_block_iteration(16, 4)  # below the smallest block 2(Q+1) of these instances
+    for threads, passes in ((16, 4), (1024, 4), (512, 0)):
+        with pytest.raises(native.VcError) as e:
+            b.set_block_iteration(threads, passes)
+        assert e.value.code == native.VC_ERR_ARG
+    # a rejected shape keeps the previous one: the batch still solves
+    _, V64b, _, stats, rc = b.value_iterate(tol=1e-6, accurate=True, block=True)
+    assert rc == native.VC_OK and all(s["certified"] == 1 for s in stats)
     b.close()
 
 
