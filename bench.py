@@ -60,12 +60,17 @@ def parse():
     ap.add_argument("--self-loop", dest="self_loop", action="store_true",
                     help="FP32 sweeps solve each action's self-transition exactly (VC_ITER_SELF_LOOP; same V*, "
                          "fewer sweeps); by default the step runs Eq. 18's backup as Algorithm 3 states it")
+    ap.add_argument("--block", action="store_true",
+                    help="implicit form only: FP32 sweeps run Algorithm 4's in-block iteration (VC_ITER_BLOCK, the "
+                         "handle's default block shape)")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and the variants")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default CSR schedule (profiling runs: no tuning launches before the timed ones)")
     args = ap.parse_args()
     args.padded = args.layout == "padded" and args.form != "implicit"
     args.sliced = args.sliced and args.form != "implicit"
+    if args.block and args.form != "implicit":
+        ap.error("--block needs --form implicit")
     return args
 
 
@@ -164,7 +169,7 @@ def run_native(args):
 
     def step():
         V.zero_()  # Algorithm 3, step 1
-        _, V64, pi, st = m.value_iterate(V, tol=args.tol, self_loop=args.self_loop)
+        _, V64, pi, st = m.value_iterate(V, tol=args.tol, self_loop=args.self_loop, block=args.block)
         return st
 
     for _ in range(max(3, args.warmup)):
@@ -256,7 +261,8 @@ def step_config(args, nnz_logical, world):
         "parallelism": "replicas" if world > 1 else "single",
         "l2": "256 MiB buffer written between steps, outside the step events",
         "step": "V=0 -> FP32 sweeps -> argmax -> FP64 policy evaluation -> FP64 Bellman certificate",
-        "sweep": "self-transition solved" if args.self_loop else "Eq. 18 backup",
+        "sweep": ("in-block iteration, self-transitions solved" if getattr(args, "block", False) else
+                  "self-transition solved" if args.self_loop else "Eq. 18 backup"),
     }
 
 
@@ -888,7 +894,7 @@ def e2e(args, p, native, torch, nnz):
         m = native.MDP.build(p, fmt=args.form, padded=args.padded, sliced=args.sliced)
         torch.cuda.synchronize()
         tb = time.perf_counter()
-        V, V64, pi, st = m.value_iterate(tol=args.tol, self_loop=args.self_loop)
+        V, V64, pi, st = m.value_iterate(tol=args.tol, self_loop=args.self_loop, block=args.block)
         hv.copy_(V64, non_blocking=True)
         hp.copy_(pi, non_blocking=True)
         torch.cuda.synchronize()
@@ -949,7 +955,7 @@ def block_comparison(args, mi, Vi, torch, stream, t_self_loop):
     several shapes, each device-timed to the same certified residual."""
     out = {"shapes": []}
     best = None
-    for h, passes in ((1, 4), (2, 2), (2, 4), (2, 8)):
+    for h, passes in ((0, 4), (1, 2), (1, 4), (1, 8)):
         try:
             mi.set_block_iteration(h, passes)
         except Exception:

@@ -305,10 +305,10 @@ int vc_bellman32(vc_mdp* m, const float* V, float* V_out, int32_t* pi, float* qg
 /*
  * Shape of the in-block iteration of an implicit handle (VC_ITER_BLOCK; Algorithm 4's
  * "episodes" inside a block, Section V-H): inner_hosts = h (0..3) gives blocks of
- * B = 2(Q+1)(C+1)^h states (at most 1024; -1 = the largest such h, the default), passes the
+ * B = 2(Q+1)(C+1)^h states (at most 512; -1 = the largest such h, the default), passes the
  * local passes per global sweep (1..64, default 4; 1 is the plain self-transition sweep).
  * Applies to later solves.  VC_ERR_ARG for explicit handles, passes outside 1..64, h above
- * 3 or H, or a block of more than 1024 states.
+ * 3 or H, or a block of more than 512 states.
  */
 int vc_set_block_iteration(vc_mdp* m, int32_t inner_hosts, int32_t passes);
 

@@ -18,6 +18,7 @@ constexpr int kRing = 64;          // residual slots, indexed by sweep number mo
 constexpr int kStallSweeps = 64;   // FP32 sweeps without a new best residual = FP32 floor
 constexpr int kThreads = 256;      // block size of the state-parallel kernels
 constexpr int kBlockMaxInner = 3;  // inner hosts of an in-block iteration block (VC_ITER_BLOCK)
+constexpr int kBlockThreads = 512; // states of a block, and of a tile of blocks, at most
 
 // ------------------------------------------------------------------ error plumbing
 void set_error(const std::string& msg);

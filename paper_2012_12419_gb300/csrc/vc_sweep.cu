@@ -144,7 +144,7 @@ __device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<flo
 // ---------------------------------------------------------------- implicit: pass 1
 // SL (FP32 only): also U2(x) = defer's backup with the self-transition solved.
 template <int MH, typename T, bool SL>
-__global__ void __launch_bounds__(kThreads) k_post(Model md, Coef<T> c, const T* __restrict__ V, T* __restrict__ U,
+__global__ void __launch_bounds__(kThreads, SL ? 4 : 1) k_post(Model md, Coef<T> c, const T* __restrict__ V, T* __restrict__ U,
                                                    T* __restrict__ U2, SweepCtl sc) {
     static_assert(!SL || std::is_same<T, float>::value, "self-transition solve in FP32 sweeps only");
     if (loop_done(sc)) return;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_max(Model md, const T* __restrict_
 // (block_tile, the local passes over one tile of blocks, lives in vc_internal.cuh: the
 // batched loop runs the same routine per instance.)
 template <int MH, int HIN>
-__global__ void __launch_bounds__(1024) k_block(Model md, Coef<float> c, int T, int passes,
+__global__ void __launch_bounds__(kBlockThreads, 3) k_block(Model md, Coef<float> c, int T, int passes,
                                                 const float* __restrict__ Vin, const float* __restrict__ U,
                                                 const float* __restrict__ W, float* __restrict__ V_out,
                                                 SweepCtl sc) {
@@ -364,15 +364,15 @@ int block_shape(const Mdp* m, int* h_out, int* B_out) {
     if (h < 0) {
         h = 0;
         long long B = 2LL * (m->md.Q + 1);
-        while (h < m->md.H && h < kBlockMaxInner && B * (m->md.C + 1) <= 1024) {
+        while (h < m->md.H && h < kBlockMaxInner && B * (m->md.C + 1) <= kBlockThreads) {
             B *= (m->md.C + 1);
             h++;
         }
     }
     long long B = 2LL * (m->md.Q + 1);
     for (int k = 0; k < h; k++) B *= (m->md.C + 1);
-    if (h > m->md.H || h > kBlockMaxInner || B > 1024)
-        return fail(VC_ERR_ARG, "a block of the in-block iteration needs at most 3 inner hosts and 1024 states");
+    if (h > m->md.H || h > kBlockMaxInner || B > kBlockThreads)
+        return fail(VC_ERR_ARG, "a block of the in-block iteration needs at most 3 inner hosts and 512 states");
     *h_out = h;
     *B_out = (int)B;
     return VC_OK;
@@ -381,8 +381,8 @@ int block_shape(const Mdp* m, int* h_out, int* B_out) {
 static int launch_block(Mdp* m, const float* V_in, float* V_out, SweepCtl sc, cudaStream_t st) {
     int h = 0, B = 0, rc;
     if ((rc = block_shape(m, &h, &B))) return rc;
-    // tiles of whole blocks, about 512 states (one block if it is larger)
-    const int T = B * std::max(1, 512 / B);
+    // tiles of whole blocks, at most kBlockThreads states
+    const int T = B * (kBlockThreads / B);
     const int threads = (T + 31) / 32 * 32;
     const size_t smem = 4 * sizeof(float) * (size_t)threads;
     const int g = state_grid(m);
@@ -394,6 +394,8 @@ static int launch_block(Mdp* m, const float* V_in, float* V_out, SweepCtl sc, cu
         auto kern = h == 0 ? k_block<MH, 0> : h == 1 ? k_block<MH, 1> : h == 2 ? k_block<MH, 2> : k_block<MH, 3>;
         if (m->blk_grid <= 0) {
             int per_sm = 0;
+            VC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared));
             VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
             m->blk_grid = std::max(1, per_sm) * (m->num_sms > 0 ? m->num_sms : 148);
         }
