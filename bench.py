@@ -277,8 +277,8 @@ def layout_of(args, info):
         d["streamed"] = "nothing per transition: successors generated in registers from the state code"
     elif sliced:
         d["streamed"] = (f"sliced copy of the {'padded' if args.padded else 'canonical'} CSR ({nnz_stored:,} "
-                         f"entries): infeasible rows dropped, each 32-state block padded to its longest row, "
-                         f"{int(info['nnz_sliced']):,} entries")
+                         f"entries): infeasible rows and explicit zeros dropped, each 32-state block padded to its "
+                         f"longest row, {int(info['nnz_sliced']):,} entries")
     else:
         d["streamed"] = f"{'padded' if args.padded else 'canonical'} CSR, {nnz_stored:,} entries"
     return d

@@ -9,7 +9,9 @@
 // slice g holds a block of width(g, a) rows of 32 entries stored lane-fastest; width is
 // the longest feasible row of the block and shorter rows are padded with (column = the
 // lane's own state, value 0), which leaves every row sum bitwise unchanged.  Infeasible
-// rows (R = -inf) store nothing.
+// rows (R = -inf) store nothing, and neither do a stored row's explicit zeros (a padded
+// CSR's filler entries): a zero term leaves the row's fused multiply-add chain bitwise
+// unchanged for finite V, so the row is its non-zero entries in column order.
 //
 // Everything one slice needs is one contiguous record in a byte slab, every region on a
 // 128-byte boundary:
@@ -78,10 +80,23 @@ __host__ __device__ inline RecLayout rec_layout(int A, long long rows, int vt, b
 }
 
 // ------------------------------------------------------------------------ build
-// Sort key of a state: feasible-action mask (bits 32..62), 2^20 - 1 - total row length
-// (bits 12..31), index inside its window (bits 0..11).  Padding states past S get ~0.
-__global__ void k_sell_keys(const int64_t* __restrict__ row_ptr, const float* __restrict__ R, int S, int A,
-                            int64_t n_pad, uint64_t* __restrict__ keys) {
+__device__ __forceinline__ bool nonzero_val(float v) { return v != 0.0f; }
+__device__ __forceinline__ bool nonzero_val(uint16_t b) { return (b & 0x7FFFu) != 0u; }
+
+// Non-zero entries of stored row r (the entries the sliced layout keeps).
+template <typename VT>
+__device__ __forceinline__ int row_nonzeros(const int64_t* __restrict__ row_ptr, const VT* __restrict__ val,
+                                            int64_t r) {
+    int n = 0;
+    for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; ++j) n += nonzero_val(val[j]) ? 1 : 0;
+    return n;
+}
+
+// Sort key of a state: feasible-action mask (bits 32..62), 2^20 - 1 - total non-zero row
+// length (bits 12..31), index inside its window (bits 0..11).  Padding states past S get ~0.
+template <typename VT>
+__global__ void k_sell_keys(const int64_t* __restrict__ row_ptr, const VT* __restrict__ val,
+                            const float* __restrict__ R, int S, int A, int64_t n_pad, uint64_t* __restrict__ keys) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (s >= S) {
@@ -94,7 +109,7 @@ __global__ void k_sell_keys(const int64_t* __restrict__ row_ptr, const float* __
             const int64_t r = s * A + a;
             if (R[r] != -INFINITY) {
                 mask |= 1u << (a < 30 ? a : 30);
-                tot += row_ptr[r + 1] - row_ptr[r];
+                tot += row_nonzeros(row_ptr, val, r);
             }
         }
         const uint64_t len = (uint64_t)(tot < 0xFFFFF ? tot : 0xFFFFF);
@@ -130,11 +145,12 @@ __global__ void __launch_bounds__(1024) k_sell_sort(const uint64_t* __restrict__
     }
 }
 
-// Warp per slice: width(g, a) = longest feasible row among the slice's lanes; the record
-// size of the slice in units of 128 bytes.
-__global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const float* __restrict__ R,
-                             const int32_t* __restrict__ perm, int A, int64_t G, int vt, int has_scale,
-                             int32_t* __restrict__ width, int32_t* __restrict__ rec_units) {
+// Warp per slice: width(g, a) = longest feasible row (non-zero entries) among the slice's
+// lanes; the record size of the slice in units of 128 bytes.
+template <typename VT>
+__global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const VT* __restrict__ val,
+                             const float* __restrict__ R, const int32_t* __restrict__ perm, int A, int64_t G, int vt,
+                             int has_scale, int32_t* __restrict__ width, int32_t* __restrict__ rec_units) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
@@ -144,7 +160,7 @@ __global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const float* _
             int len = 0;
             if (s >= 0) {
                 const int64_t r = (int64_t)s * A + a;
-                if (R[r] != -INFINITY) len = (int)(row_ptr[r + 1] - row_ptr[r]);
+                if (R[r] != -INFINITY) len = row_nonzeros(row_ptr, val, r);
             }
             const int w = __reduce_max_sync(0xffffffffu, len);
             if (lane == 0) width[g * A + a] = w;
@@ -186,8 +202,7 @@ __global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* 
         int row0 = 0;
         for (int a = 0; a < A; ++a) {
             const int w = __shfl_sync(0xffffffffu, wl, a);
-            int64_t lo = 0;
-            int len = 0;
+            int64_t lo = 0, hi = 0;
             float rr = -INFINITY, sc = 1.0f;
             if (s >= 0) {
                 const int64_t r = (int64_t)s * A + a;
@@ -195,18 +210,23 @@ __global__ void k_sell_fill(const int64_t* __restrict__ row_ptr, const int32_t* 
                 if (has_scale) sc = scale[r];
                 if (rr != -INFINITY) {
                     lo = row_ptr[r];
-                    len = (int)(row_ptr[r + 1] - lo);
+                    hi = row_ptr[r + 1];
                 }
             }
-            for (int j = 0; j < w; ++j) {
+            // the row's non-zero entries in column order, then padding
+            int j = 0;
+            for (int64_t k = lo; k < hi; ++k) {
+                const VT v = val[k];
+                if (!nonzero_val(v)) continue;
                 const int64_t e = (int64_t)(row0 + j) * kSellC + lane;
-                if (j < len) {
-                    cr[e] = col[lo + j];
-                    vr[e] = val[lo + j];
-                } else {
-                    cr[e] = s >= 0 ? s : 0;
-                    vr[e] = VT(0);
-                }
+                cr[e] = col[k];
+                vr[e] = v;
+                ++j;
+            }
+            for (; j < w; ++j) {
+                const int64_t e = (int64_t)(row0 + j) * kSellC + lane;
+                cr[e] = s >= 0 ? s : 0;
+                vr[e] = VT(0);
             }
             Rr[a * kSellC + lane] = rr;
             if (has_scale) Sr[a * kSellC + lane] = sc;
@@ -259,11 +279,19 @@ int build_sliced(Mdp* m, cudaStream_t st) {
         return rc;
     }
     count_launches(3);
-    k_sell_keys<<<warp_grid(n_pad / 32 + 1, m->num_sms), kThreads, 0, st>>>(m->row_ptr, m->R, (int)S, A, n_pad,
-                                                                            keys);
+    if (bf16)
+        k_sell_keys<uint16_t><<<warp_grid(n_pad / 32 + 1, m->num_sms), kThreads, 0, st>>>(
+            m->row_ptr, (const uint16_t*)m->val, m->R, (int)S, A, n_pad, keys);
+    else
+        k_sell_keys<float><<<warp_grid(n_pad / 32 + 1, m->num_sms), kThreads, 0, st>>>(
+            m->row_ptr, (const float*)m->val, m->R, (int)S, A, n_pad, keys);
     k_sell_sort<<<(unsigned)(n_pad / kSellSigma), 1024, 0, st>>>(keys, perm);
-    k_sell_width<<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(m->row_ptr, m->R, perm, A, G, vt, bf16 ? 1 : 0,
-                                                                width, units);
+    if (bf16)
+        k_sell_width<uint16_t><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(
+            m->row_ptr, (const uint16_t*)m->val, m->R, perm, A, G, vt, 1, width, units);
+    else
+        k_sell_width<float><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(m->row_ptr, (const float*)m->val, m->R,
+                                                                           perm, A, G, vt, 0, width, units);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         cleanup();

@@ -144,7 +144,7 @@ __device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<flo
 // ---------------------------------------------------------------- implicit: pass 1
 // SL (FP32 only): also U2(x) = defer's backup with the self-transition solved.
 template <int MH, typename T, bool SL>
-__global__ void __launch_bounds__(kThreads, SL ? 4 : 1) k_post(Model md, Coef<T> c, const T* __restrict__ V, T* __restrict__ U,
+__global__ void __launch_bounds__(kThreads) k_post(Model md, Coef<T> c, const T* __restrict__ V, T* __restrict__ U,
                                                    T* __restrict__ U2, SweepCtl sc) {
     static_assert(!SL || std::is_same<T, float>::value, "self-transition solve in FP32 sweeps only");
     if (loop_done(sc)) return;

@@ -35,11 +35,16 @@ def _sweep(m, V):
     return Vo, pi, gap
 
 
-def _host_slice_rows(row_ptr, R, S, A, C=32, sigma=4096):
+def _host_slice_rows(row_ptr, R, S, A, val=None, C=32, sigma=4096):
     """Rows (of 32 entries) of every slice of the sliced layout, recomputed on the host from
-    the layout's definition: states sorted in windows by (feasible mask, -total length,
-    index); per slice and action the longest feasible row."""
-    L = np.diff(row_ptr).reshape(S, A)
+    the layout's definition: rows keep their non-zero entries; states sorted in windows by
+    (feasible mask, -total length, index); per slice and action the longest feasible row."""
+    row_ptr = np.asarray(row_ptr)
+    if val is None:
+        L = np.diff(row_ptr).reshape(S, A)
+    else:
+        nz = np.concatenate([[0], np.cumsum(np.asarray(val) != 0)])
+        L = (nz[row_ptr[1:]] - nz[row_ptr[:-1]]).reshape(S, A)
     feas = np.asarray(R).reshape(S, A) != -np.inf
     L = np.where(feas, L, 0)
     mask = (feas[:, : min(A, 30)] * (1 << np.arange(min(A, 30)))).sum(axis=1)
@@ -57,14 +62,14 @@ def _host_slice_rows(row_ptr, R, S, A, C=32, sigma=4096):
     return Lo.reshape(-1, C, A).max(axis=1).sum(axis=1)
 
 
-def _host_sliced_entries(row_ptr, R, S, A):
-    return int(_host_slice_rows(row_ptr, R, S, A).sum()) * 32
+def _host_sliced_entries(row_ptr, R, S, A, val=None):
+    return int(_host_slice_rows(row_ptr, R, S, A, val).sum()) * 32
 
 
-def _host_sweep_bytes(row_ptr, R, S, A, vbytes):
+def _host_sweep_bytes(row_ptr, R, S, A, vbytes, val=None):
     """Slab bytes (one record per slice: header, state map, R [and scale], col, val rows,
     each region rounded to 128 bytes) + record offsets + V in and out."""
-    rows = _host_slice_rows(row_ptr, R, S, A)
+    rows = _host_slice_rows(row_ptr, R, S, A, val)
     r128 = lambda x: (x + 127) // 128 * 128
     rec = 256 + 128 * A * (2 if vbytes == 2 else 1) + 128 * rows + r128(32 * vbytes * rows)
     G = len(rows)
@@ -86,9 +91,13 @@ def test_sliced_sweep_equals_csr_sweep(which, fmt, padded):
     assert info["csr_pipelined"] == 1 and md.info()["csr_pipelined"] == 0
     S, A = info["S"], info["A"]
     rp, col, val, R = oracle.build_csr(p, padded=padded)[:4]
-    assert info["nnz_sliced"] == _host_sliced_entries(rp, R, S, A)
+    assert info["nnz_sliced"] == _host_sliced_entries(rp, R, S, A, val)
     vbytes = 2 if fmt == "csr_bf16" else 4
-    assert info["sweep_bytes"] == _host_sweep_bytes(rp, R, S, A, vbytes)
+    assert info["sweep_bytes"] == _host_sweep_bytes(rp, R, S, A, vbytes, val)
+    if padded:
+        # the padded matrix's filler zeros are not stored: its sliced copy is the canonical one's
+        rc, _, vc, Rc = oracle.build_csr(p, padded=False)[:4]
+        assert info["nnz_sliced"] == _host_sliced_entries(rc, Rc, S, A, vc)
     g = torch.Generator(device="cuda").manual_seed(5)
     for scale in (100.0, 1e-3):
         V = torch.rand(S, device="cuda", generator=g) * scale - scale / 3
