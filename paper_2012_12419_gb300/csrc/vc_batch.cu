@@ -243,33 +243,49 @@ __global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __re
         const T* Ui = U + sd.off;
         const T* Vi = V_in + sd.off;
         T res = T(0), vabs = T(0);
-        for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
-            const int s = tl.start + j;
-            Digits d;
-            decode<MH>(sd.md, s, d);
-            T best = -INFINITY;
-            int arg = sd.md.H;
-            if (d.q >= 1) {
+        // two states per thread and step: every gather of both is issued before either
+        // maximum (more loads in flight); same arithmetic and order per state
+        for (int j0 = threadIdx.x; j0 < tl.count; j0 += 2 * blockDim.x) {
+            T uk[2][MH], ud[2], vin[2];
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int j = j0 + t * blockDim.x;
+                const bool live = j < tl.count;
+                const int s = tl.start + (live ? j : 0);
+                Digits d;
+                decode<MH>(sd.md, s, d);
 #pragma unroll
                 for (int k = 0; k < MH; k++) {
-                    if (k < sd.md.H && d.occ[k] < sd.md.C && (k == sd.md.H - 1 || d.ph == 1)) {
-                        const T u = Ui[s + sd.md.stride[k] - 2];
-                        if (u > best) {
-                            best = u;
-                            arg = k;
-                        }
+                    const bool f = live && d.q >= 1 && k < sd.md.H && d.occ[k] < sd.md.C &&
+                                   (k == sd.md.H - 1 || d.ph == 1);
+                    uk[t][k] = f ? Ui[s + sd.md.stride[k] - 2] : T(-INFINITY);
+                }
+                ud[t] = live ? (SL ? U2[sd.off + s] : Ui[s]) : T(-INFINITY);
+                vin[t] = live ? Vi[s] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int j = j0 + t * blockDim.x;
+                if (j >= tl.count) continue;
+                const int s = tl.start + j;
+                T best = -INFINITY;
+                int arg = sd.md.H;
+#pragma unroll
+                for (int k = 0; k < MH; k++) {
+                    if (uk[t][k] > best) {
+                        best = uk[t][k];
+                        arg = k;
                     }
                 }
+                if (ud[t] > best) {
+                    best = ud[t];
+                    arg = sd.md.H;
+                }
+                if (V_out) V_out[sd.off + s] = best;
+                if (pi) pi[sd.off + s] = arg;
+                res = fmax(res, fabs(best - vin[t]));
+                vabs = fmax(vabs, fabs(best));
             }
-            const T u = SL ? U2[sd.off + s] : Ui[s];
-            if (u > best) {
-                best = u;
-                arg = sd.md.H;
-            }
-            if (V_out) V_out[sd.off + s] = best;
-            if (pi) pi[sd.off + s] = arg;
-            res = fmax(res, fabs(best - Vi[s]));
-            vabs = fmax(vabs, fabs(best));
         }
         if (loop || res64) {
             res = block_max<T, kThreads>(res);

@@ -238,6 +238,75 @@ __global__ void __launch_bounds__(kBlockThreads, 3) k_block(Model md, Coef<float
     finish_block<float>(sc, res, vabs, sweep);
 }
 
+// FP32 pass 2 with two states per thread and loop step: both states' gathers are issued
+// before either maximum is taken, so twice as many independent loads are in flight per
+// warp (the pass waits on the L2 latency of its gathers).  Same arithmetic and order as
+// k_max, so the same results bit for bit.
+template <int MH, bool SL>
+__global__ void __launch_bounds__(kThreads) k_max2(Model md, const float* __restrict__ U, const float* __restrict__ U2,
+                                                   const float* __restrict__ V_in, float* __restrict__ V_out,
+                                                   int32_t* __restrict__ pi, float* __restrict__ qgap, SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    float res = 0.0f, vabs = 0.0f;
+    const int step = gridDim.x * kThreads;
+    for (int s0 = blockIdx.x * kThreads + threadIdx.x; s0 < md.S; s0 += 2 * step) {
+        float uk[2][MH], ud[2], vin[2];
+        int sv[2];
+        bool live[2];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const int s = s0 + t * step;
+            sv[t] = s;
+            live[t] = s < md.S;
+            Digits d;
+            decode<MH>(md, live[t] ? s : 0, d);
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                const bool f = live[t] && d.q >= 1 && k < md.H && d.occ[k] < md.C && (k == md.H - 1 || d.ph == 1) &&
+                               VC_IN_BOUNDS(sc.ctl, s + md.stride[k] - 2 >= 0 && s + md.stride[k] - 2 < md.S);
+                uk[t][k] = f ? U[s + md.stride[k] - 2] : -INFINITY;
+            }
+            ud[t] = live[t] ? (SL ? U2[s] : U[s]) : -INFINITY;
+            vin[t] = live[t] ? V_in[s] : 0.0f;
+        }
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            if (!live[t]) continue;
+            float best = -INFINITY, second = -INFINITY;
+            int arg = md.H;
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                if (uk[t][k] > best) {
+                    second = best;
+                    best = uk[t][k];
+                    arg = k;
+                } else if (uk[t][k] > second) {
+                    second = uk[t][k];
+                }
+            }
+            const float u = ud[t];
+            if (u > best) {
+                second = best;
+                best = u;
+                arg = md.H;
+            } else if (u > second) {
+                second = u;
+            }
+            const int s = sv[t];
+            if (V_out) V_out[s] = best;
+            if (pi) pi[s] = arg;
+            if (qgap) qgap[s] = (second == -INFINITY) ? INFINITY : best - second;
+            res = fmaxf(res, fabsf(best - vin[t]));
+            vabs = fmaxf(vabs, fabsf(best));
+        }
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<float, kThreads>(res);
+    vabs = block_max<float, kThreads>(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
 // ------------------------------------------------ implicit: mixed-precision refinement
 // Policy residual in FP64, r(s) = U64(x_pi(s)) - V64(s) with U64 = R + gamma E[V64(next) | x]
 // from the FP64 pass-1 kernel over every post-decision state (coalesced: thread x gathers
@@ -423,10 +492,10 @@ int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* 
         constexpr int MH = decltype(mh)::value;
         if (sc.self_loop) {
             k_post<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
-            k_max<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->U32, m->U32s, V_in, V_out, pi, qgap, sc);
+            k_max2<MH, true><<<g, kThreads, 0, st>>>(m->md, m->U32, m->U32s, V_in, V_out, pi, qgap, sc);
         } else {
             k_post<MH, float, false><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, nullptr, sc1);
-            k_max<MH, float, false><<<g, kThreads, 0, st>>>(m->md, m->U32, nullptr, V_in, V_out, pi, qgap, sc);
+            k_max2<MH, false><<<g, kThreads, 0, st>>>(m->md, m->U32, nullptr, V_in, V_out, pi, qgap, sc);
         }
         return 0;
     });
