@@ -412,6 +412,16 @@ int vc_autotune(vc_mdp* m, int reps, double* best_us, void* stream);
  */
 int64_t vc_autotune_report(const vc_mdp* m, char* buf, int64_t len);
 
+/*
+ * The autotuner's candidate schedules without timing: *count (host, nullable) receives the
+ * number of candidates of this CSR handle, in the order of vc_autotune_report's rows (CSR
+ * tilings, the direct CSR kernel, then with a sliced copy the ring sweep's launch shapes
+ * and the direct sliced kernel); index >= 0 switches the handle to that candidate for later
+ * sweeps, index < 0 only counts.  The schedule never changes results (see vc_autotune).
+ * VC_ERR_ARG for an implicit handle or an index >= *count; the handle keeps its schedule.
+ */
+int vc_sweep_schedule(vc_mdp* m, int32_t index, int32_t* count, void* stream);
+
 /* Statistics of vc_value_grad (host struct). */
 typedef struct vc_grad_stats {
     int64_t sweeps;          /* FP32 products by P_pi^T in the first solve */

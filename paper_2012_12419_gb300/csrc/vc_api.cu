@@ -552,6 +552,21 @@ int vc_autotune(vc_mdp* mh, int reps, double* best_us, void* stream) {
     return autotune_csr(m, reps, (cudaStream_t)stream, best_us);
 }
 
+int vc_sweep_schedule(vc_mdp* mh, int32_t index, int32_t* count, void* stream) {
+    g_err.clear();
+    if (!mh) return fail(VC_ERR_ARG, "NULL handle");
+    Mdp* m = (Mdp*)mh;
+    if ((m->fmt & 0xF) == VC_IMPLICIT) return fail(VC_ERR_ARG, "an implicit handle has one sweep schedule");
+    std::vector<CsrPlan> cands;
+    int rc = csr_candidates(m, (cudaStream_t)stream, cands);
+    if (rc) return rc;
+    if (count) *count = (int32_t)cands.size();
+    if (index < 0) return VC_OK;
+    if (index >= (int32_t)cands.size()) return fail(VC_ERR_ARG, "schedule index out of range");
+    m->plan = cands[(size_t)index];
+    return VC_OK;
+}
+
 int64_t vc_autotune_report(const vc_mdp* mh, char* buf, int64_t len) {
     if (!mh) return 0;
     const std::string& r = ((const Mdp*)mh)->tune_report;

@@ -860,10 +860,10 @@ int csr_correct32(Mdp* m, const int32_t* pi, const float* r, const float* e_in, 
     return VC_OK;
 }
 
-// Times every candidate tiling (and the direct kernel) on this handle and keeps the
-// fastest: reps FP32 sweeps each after two warm-up sweeps, CUDA events on `st`.
-int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
-    std::vector<CsrPlan> cands;
+// Every candidate schedule of the FP32 sweep, in the autotuner's order: the CSR tilings,
+// the direct CSR kernel, then (with a sliced copy) the ring sweep's shapes and the direct
+// sliced kernel at 2, 4 and 8 CTAs per SM.
+int csr_candidates(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& cands) {
     int rc = enumerate_plans(m, st, cands);
     if (rc) return rc;
     cands.push_back(CsrPlan());  // direct kernel
@@ -878,6 +878,15 @@ int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
             cands.push_back(P);
         }
     }
+    return VC_OK;
+}
+
+// Times every candidate schedule on this handle and keeps the fastest: reps FP32 sweeps
+// each after two warm-up sweeps, CUDA events on `st`.
+int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us) {
+    std::vector<CsrPlan> cands;
+    int rc = csr_candidates(m, st, cands);
+    if (rc) return rc;
     if (reps < 1) reps = 1;
     float* A = m->Vb;
     float* B = m->E0;

@@ -698,6 +698,7 @@ int build_sliced(Mdp* m, cudaStream_t st);
 int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out);
 int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st);
 int64_t sell_sweep_bytes(const Mdp* m);
+int csr_candidates(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& cands);
 int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us);
 
 // Grid of the persistent state-parallel kernels.

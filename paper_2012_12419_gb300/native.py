@@ -47,7 +47,7 @@ EXPORTS = [
     "vc_batch_autotune", "vc_batch_autotune_report", "vc_batch_destroy", "vc_mdp_slice", "vc_greedy_policy",
     "vc_set_wait_limit", "vc_aaa_intervals", "vc_objective", "vc_build_binary_mdp", "vc_set_block_iteration",
     "vc_block_iteration_info", "vc_batch_set_block_iteration", "vc_batch_set_small_instances",
-    "vc_batch_small_instances",
+    "vc_batch_small_instances", "vc_sweep_schedule",
 ]
 
 
@@ -181,6 +181,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         L.vc_batch_set_block_iteration.argtypes = [vp, i32, i32, vp]
         L.vc_batch_set_small_instances.argtypes = [vp, i32, vp]
         L.vc_batch_small_instances.argtypes = [vp, vp, vp]
+        L.vc_sweep_schedule.argtypes = [vp, i32, ctypes.POINTER(i32), vp]
         for name in EXPORTS:
             if name not in ("vc_last_error", "vc_kernel_launches", "vc_autotune_report", "vc_batch_autotune_report"):
                 getattr(L, name).restype = ctypes.c_int
@@ -383,6 +384,18 @@ class MDP:
         _check(load().vc_autotune(self._h, int(reps), ctypes.byref(us), _stream(stream)))
         self._info = None
         return us.value
+
+    def schedules(self, stream=None) -> int:
+        """Number of candidate sweep schedules (the autotuner's rows, in its order)."""
+        n = ctypes.c_int32()
+        _check(load().vc_sweep_schedule(self._h, -1, ctypes.byref(n), _stream(stream)))
+        return n.value
+
+    def use_schedule(self, index: int, stream=None) -> None:
+        """Switch later sweeps to candidate schedule `index` (no timing)."""
+        n = ctypes.c_int32()
+        _check(load().vc_sweep_schedule(self._h, int(index), ctypes.byref(n), _stream(stream)))
+        self._info = None
 
     def autotune_report(self) -> str:
         """Candidates and times of the last autotune, one line each."""

@@ -7,6 +7,8 @@
 * the copy's size (entries incl. padding) equals a host-side recomputation of the layout
   from the oracle's CSR (sort key, slice widths) exactly;
 * a full solve on the sliced copy is certified and matches the oracle within 1e-6;
+* every candidate schedule (selected with vc_sweep_schedule) gives the same sweep bit for
+  bit, in Eq. 18's backup and the self-transition solve;
 * the autotuner's sliced candidates keep the results; invalid requests are errors.
 """
 import numpy as np
@@ -129,7 +131,11 @@ def test_sliced_arbitrary_csr(S, A, seed):
     ref = _sweep(mc, V)
     for x, y in zip(ref, _sweep(ms, V)):
         assert torch.equal(x, y)
-    # every schedule the autotuner may pick (pipelined / direct, CSR / sliced)
+    # every schedule the autotuner may pick (pipelined / direct, CSR / sliced), each one
+    for k in range(ms.schedules()):
+        ms.use_schedule(k)
+        for x, y in zip(ref, _sweep(ms, V)):
+            assert torch.equal(x, y), k
     ms.autotune(reps=2)
     for x, y in zip(ref, _sweep(ms, V)):
         assert torch.equal(x, y)
@@ -167,6 +173,42 @@ def test_sliced_solve_matches_oracle(fmt, padded):
     mc.close()
 
 
+@pytest.mark.parametrize("fmt,padded", CSR_FORMS)
+def test_every_schedule_is_bitwise_equal(fmt, padded):
+    """Every candidate schedule (CSR tilings, ring sweep launch shapes and tile sizes,
+    direct kernels): one sweep equal bit for bit to the
+    direct CSR kernel's, and the self-transition solve's FP32 iterate and sweep count equal
+    to the CSR handle's."""
+    native = native_or_skip()
+    import torch
+
+    mc = native.MDP.build(MID, fmt=fmt, padded=padded, direct=True)
+    ms = native.MDP.build(MID, fmt=fmt, padded=padded, sliced=True)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    V = torch.rand(ms.S, device="cuda", generator=g) * 80 - 20
+    ref = _sweep(mc, V)
+    Vr, _, _, sr = mc.value_iterate(tol=1e-6, fp32_only=True, self_loop=True)
+    n = ms.schedules()
+    rep_kinds = set()
+    for k in range(n):
+        ms.use_schedule(k)
+        info = ms.info()
+        rep_kinds.add((info["csr_sliced"], info["csr_pipelined"]))
+        for x, y in zip(ref, _sweep(ms, V)):
+            assert torch.equal(x, y), k
+        Vk, _, _, sk = ms.value_iterate(tol=1e-6, fp32_only=True, self_loop=True)
+        assert sk["sweeps"] == sr["sweeps"] and torch.equal(Vk, Vr), k
+    assert rep_kinds == {(0, 0), (0, 1), (1, 0), (1, 1)}
+    # the autotuner's table lists the same candidates in the same order
+    ms.autotune(reps=1)
+    rows = ms.autotune_report().strip().splitlines()[1:]
+    assert len(rows) == n
+    with pytest.raises(native.VcError):
+        ms.use_schedule(n)
+    mc.close()
+    ms.close()
+
+
 def test_autotune_with_sliced_candidates_keeps_results():
     native = native_or_skip()
     import torch
@@ -193,6 +235,8 @@ def test_sliced_errors():
     mi = native.MDP.build(TINY, fmt="implicit")
     with pytest.raises(native.VcError):
         mi.slice()
+    with pytest.raises(native.VcError):
+        mi.schedules()
     mi.close()
     S, A = 40, 32
     mdp = inputs.random_csr_mdp(S, A, max_succ=8, seed=9, gamma=0.9)
