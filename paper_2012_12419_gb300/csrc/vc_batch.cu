@@ -222,17 +222,20 @@ __global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __r
 
 // Pass 2: V'(s) = max_a U(x_a(s)); per-instance residual and close (loop mode, ctl given),
 // or plain extraction with policy / FP64 certificate residual into res64 (ctl null).  SL:
-// defer takes U2(s) (its backup with the self-transition solved).
+// defer takes U2(s) (its backup with the self-transition solve).  Outside loop mode,
+// instances with a non-zero entry in `skipped` (nullable) are left untouched.
 template <int MH, typename T, bool SL>
 __global__ void k_bmax(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
                        BatchCtl c, int loop, int parity, const T* __restrict__ U, const T* __restrict__ U2,
                        const T* __restrict__ V_in,
-                       T* __restrict__ V_out, int32_t* __restrict__ pi, unsigned long long* __restrict__ res64) {
+                       T* __restrict__ V_out, int32_t* __restrict__ pi, unsigned long long* __restrict__ res64,
+                       const int* __restrict__ skipped = nullptr) {
     __shared__ InstDesc sd;
     __shared__ int skip;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
-        if (threadIdx.x == 0) skip = loop ? (*((volatile int*)&c.done[tl.inst]) != 0) : 0;
+        if (threadIdx.x == 0)
+            skip = loop ? (*((volatile int*)&c.done[tl.inst]) != 0) : (skipped ? skipped[tl.inst] != 0 : 0);
         __syncthreads();
         if (skip) {
             __syncthreads();
@@ -449,16 +452,23 @@ __global__ void k_bcond(cudaGraphConditionalHandle h, BatchCtl c, int sweeps_per
 }
 
 // Policy residual in FP64: r = U64(x_pi) - V64 (as float), U64 from the FP64 pass-1
-// kernel over every post-decision state (one gather per state here).
+// kernel over every post-decision state (one gather per state here).  Instances with a
+// non-zero entry in `skipped` (nullable; already certified) get r = 0, so every correction
+// solve retires them at its first step with a zero correction.
 template <int MH>
 __global__ void k_bresid64(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
                            const int32_t* __restrict__ pi, const double* __restrict__ U, const double* __restrict__ V,
-                           float* __restrict__ r, int* err) {
+                           float* __restrict__ r, int* err, const int* __restrict__ skipped) {
     __shared__ InstDesc sd;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchTile tl = tiles[t];
         load_desc(descs, tl.inst, sd);
         __syncthreads();
+        if (skipped && skipped[tl.inst]) {
+            for (int j = threadIdx.x; j < tl.count; j += blockDim.x) r[sd.off + tl.start + j] = 0.0f;
+            __syncthreads();
+            continue;
+        }
         const double* Ui = U + sd.off;
         const double* Vi = V + sd.off;
         for (int j = threadIdx.x; j < tl.count; j += blockDim.x) {
@@ -833,6 +843,7 @@ struct Batch {
     long long* max_d = nullptr;
     double* tol_d = nullptr;
     float* tol_scale = nullptr;  // per-instance factor of the correction loop's tolerance
+    int* certified = nullptr;    // [n] 1: certified in an earlier refinement round (skipped)
     // BiCGSTAB correction solve: vectors r, p, v, s, t ([5][total]; x is E0), tile partials,
     // per-instance scalars
     float* kr = nullptr;
@@ -1290,20 +1301,21 @@ static void enqueue_extract(Batch* b, const float* V, int32_t* pi, cudaStream_t 
                                                            nullptr, V, nullptr, pi, nullptr);
 }
 
+// skipped (nullable): instances certified in an earlier round, left untouched.
 template <int MH>
-static void enqueue_cert(Batch* b, cudaStream_t st) {
-    k_bpost<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64,
+static void enqueue_cert(Batch* b, const int* skipped, cudaStream_t st) {
+    k_bpost<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, skipped, b->V64,
                                                              b->U64, nullptr);
     k_bmax<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U64,
-                                                            nullptr, b->V64, b->V64b, b->pi2, b->res64);
+                                                            nullptr, b->V64, b->V64b, b->pi2, b->res64, skipped);
 }
 
 template <int MH>
-static void enqueue_resid(Batch* b, cudaStream_t st) {
-    k_bpost<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, b->V64,
+static void enqueue_resid(Batch* b, const int* skipped, cudaStream_t st) {
+    k_bpost<MH, double, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, skipped, b->V64,
                                                              b->U64, nullptr);
     k_bresid64<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->pi, b->U64, b->V64, b->Rr,
-                                                 b->err);
+                                                 b->err, skipped);
 }
 
 
@@ -1372,6 +1384,7 @@ int vc_build_batch(const vc_params* p, int32_t n, void* stream, vc_batch** out) 
     if (!rc) rc = balloc(b, (void**)&b->max_d, 16);
     if (!rc) rc = balloc(b, (void**)&b->tol_d, 16);
     if (!rc) rc = balloc(b, (void**)&b->tol_scale, 4 * N);
+    if (!rc) rc = balloc(b, (void**)&b->certified, 4 * N);
     if (!rc) rc = balloc(b, (void**)&b->kr, 20 * T);
     void** kd[] = {(void**)&b->kr_rho, (void**)&b->kr_alpha, (void**)&b->kr_omega, (void**)&b->kr_beta,
                    (void**)&b->kr_target};
@@ -1503,10 +1516,14 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             }
         VC_CUDA(cudaMemcpyAsync(b->tol_scale, scale.data(), 4 * N, cudaMemcpyHostToDevice, st));
         const bool plain = (flags & VC_ITER_PLAIN_CORRECTION) != 0;
+        // instances certified in an earlier round keep their values, policy and residual:
+        // later rounds skip them in every pass
+        std::vector<int> skip_h(N, 0);
+        const int* skipped = nullptr;
         for (int round = 0; round < 20; round++) {
             VC_CUDA(cudaMemsetAsync(b->err, 0, 4, st));
             count_launches(2);
-            by_mh(b->mh, [&](auto m) { enqueue_resid<decltype(m)::value>(b, st); });
+            by_mh(b->mh, [&](auto m) { enqueue_resid<decltype(m)::value>(b, skipped, st); });
             VC_LAUNCHED("FP64 policy residual");
             int herr = 0;
             VC_CUDA(cudaMemcpyAsync(&herr, b->err, 4, cudaMemcpyDeviceToHost, st));
@@ -1555,7 +1572,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             }
             VC_CUDA(cudaMemsetAsync(b->res64, 0, 8 * N, st));
             count_launches(2);
-            by_mh(b->mh, [&](auto m) { enqueue_cert<decltype(m)::value>(b, st); });
+            by_mh(b->mh, [&](auto m) { enqueue_cert<decltype(m)::value>(b, skipped, st); });
             VC_LAUNCHED("FP64 certificate");
             std::vector<unsigned long long> rb(N);
             VC_CUDA(cudaMemcpyAsync(rb.data(), b->res64, 8 * N, cudaMemcpyDeviceToHost, st));
@@ -1566,6 +1583,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             all_cert = true;
             for (size_t i = 0; i < N; i++) {
                 csweeps[i] += cs[i];
+                if (skip_h[i]) continue;
                 double r;
                 memcpy(&r, &rb[i], 8);
                 r64[i] = r;
@@ -1573,6 +1591,9 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
                 all_cert = all_cert && cert[i];
             }
             if (all_cert) break;
+            for (size_t i = 0; i < N; i++) skip_h[i] = cert[i];
+            VC_CUDA(cudaMemcpyAsync(b->certified, skip_h.data(), 4 * N, cudaMemcpyHostToDevice, st));
+            skipped = b->certified;
         }
         if (V64_out) VC_CUDA(cudaMemcpyAsync(V64_out, b->V64, 8 * T, cudaMemcpyDeviceToDevice, st));
         if (pi_out) VC_CUDA(cudaMemcpyAsync(pi_out, b->pi, 4 * T, cudaMemcpyDeviceToDevice, st));
