@@ -37,6 +37,8 @@ WORKLOAD_DESC = {
     "tiny": "tiny MDP: H=3 C=3 Q=4, S=640, A=4, gamma=0.95",
     "precision": "precision MDP: H=8 C=4 Q=15, S=12,500,000, A=9, gamma=0.95",
     "grad": "differentiation MDP: H=6 C=4 Q=10, S=343,750, A=7, gamma=0.95",
+    "medium": "medium MDP: H=7 C=3 Q=15, S=524,288, A=8, gamma=0.95 (the large MDP's structure at a fifth of "
+              "its size: stored matrix above L2, under 1 GB on the device)",
     "batched": "512 uneven instances: H in 2..5, C in 2..6, Q in 3..12, gamma in {0.9, 0.95, 0.99}, "
                "S in [72, 436,982]",
 }
@@ -754,9 +756,9 @@ def comparisons(args, native, torch, dev, stream):
 # of this exact kernel source each (large workload, padded and canonical CSR with the sliced
 # copy); reported only while the sources hash the same, since a changed kernel voids them.
 TRAFFIC_SOURCES = ("vc_sell.cu", "vc_internal.cuh", "vc_ptx.cuh")
-TRAFFIC_SOURCE_SHA = "880d8334f04273b6ecbd70a780127e8b6f718f32adbd8e2b554fa9e8562d2db6"
-TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_494_338_560,
-                 ("large", "csr_f32", False, True): 1_196_775_680}
+TRAFFIC_SOURCE_SHA = "1cbc1e9e67692e622dc28ca79c6498b96dc770c59057a935d249cf789e47d67a"
+TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_195_904_000,
+                 ("large", "csr_f32", False, True): 1_196_635_392}
 
 
 # ncu speed-of-light figures of the batched loop's pass-1 kernel on the 512-instance batch,
@@ -764,9 +766,9 @@ TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_494_338_560,
 # by gather latency at half occupancy, not by a memory roof, and these say how far each
 # unit is from its own peak.
 BATCH_SOL_SOURCES = ("vc_batch.cu", "vc_internal.cuh")
-BATCH_SOL_SHA = "59b8815b5b88ffffad5427db8f580ac8a2b8a2760184aeb3b5ca7b536de4db46"
-BATCH_SOL = {"kernel": "k_bpost<5, float, false>", "dram_pct": 7.9, "l2_pct": 10.5, "sm_pct": 55.2,
-             "warps_active_pct": 46.9, "registers_per_thread": 63, "top_stall": "long scoreboard (V gathers)"}
+BATCH_SOL_SHA = "2d4d4b2f7521b85bb435019e516918f9a9ec047995f113c7b36864ad95253500"
+BATCH_SOL = {"kernel": "k_bpost<5, float, false>", "dram_pct": 7.7, "l2_pct": 10.3, "sm_pct": 55.5,
+             "warps_active_pct": 46.8, "registers_per_thread": 63, "top_stall": "long scoreboard (V gathers)"}
 
 
 def _sources_sha(names):
@@ -794,10 +796,11 @@ def captured_traffic(args, info):
 # attached to that variant while the kernel source hashes as captured: the sweep is bound
 # by gather latency and issue, not by a memory roof (its HBM fraction is low by design).
 IMPLICIT_SOL_SOURCES = ("vc_sweep.cu",)
-IMPLICIT_SOL_SHA = "db4f4870c06ef9c3fad75d988e2fe6139b9aabbbd83bb168a67a3a840f4687ef"
-IMPLICIT_SOL = {"kernels": "k_post<7, float, 0> / k_max<7, float, 0>", "sm_issue_pct": [58.2, 50.0],
-                "l1tex_pct": [17.3, 13.5], "l2_pct": [10.5, 8.4], "dram_pct": [3.8, 7.5],
-                "warps_active_pct": [56.5, 73.8], "bound": "gather latency and instruction issue"}
+IMPLICIT_SOL_SHA = "f324856119c49673ce32afa3295c8a33c64c2c145e207c721af00250beded105"
+IMPLICIT_SOL = {"kernels": "k_post<7, float, 0> / k_max2<7, 0>", "sm_pct": [58.2, 44.5],
+                "l2_pct": [10.5, 9.8], "dram_pct": [3.9, 8.7], "warps_active_pct": [56.2, 56.6],
+                "top_stall": ["not selected (issue-bound)", "long scoreboard (U gathers)"],
+                "bound": "instruction issue (pass 1) and gather latency (pass 2)"}
 
 
 def implicit_sol():

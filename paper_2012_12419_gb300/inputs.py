@@ -33,6 +33,7 @@ WORKLOADS = {
     "precision": dict(seed=3, H=8, C=4, Q=15, gamma=0.95),    # S = 12,500,000, A = 9
     "precision_sub": dict(seed=3, H=5, C=4, Q=15, gamma=0.95),  # S = 100,000,   A = 6
     "grad": dict(seed=4, H=6, C=4, Q=10, gamma=0.95),         # S = 343,750,    A = 7
+    "medium": dict(seed=1, H=7, C=3, Q=15, gamma=0.95),       # S = 524,288,    A = 8
 }
 
 # The paper's binary-action model (A = {-1, 1}): H vehicular clouds of C VMs each, requests
