@@ -134,19 +134,45 @@ __device__ __forceinline__ double bf16_to_double(uint16_t b) { return (double)__
 // The per-occupancy probabilities mu_k o / Lam and delta_k o / Lam of every host, formed
 // on the host (the same FP64 operations as the device formula) and placed in device
 // memory, so the row kernels read them instead of dividing in FP64.
+// Also the FP32 tables of the FP32 fill (their roundings and non-zero flags), one upload.
 int upload_rate_table(Mdp* m, cudaStream_t st) {
-    const int c1 = m->rates.tab_c1;
-    std::vector<double> tab((size_t)2 * kMaxH * c1, 0.0);
+    Rates& r = m->rates;
+    const int c1 = r.tab_c1;
+    const size_t n64 = (size_t)2 * kMaxH * c1, n32 = (size_t)kMaxH * c1;
+    const size_t bytes = 8 * n64 + 4 * n32 + n32;
+    std::vector<unsigned char> buf(bytes, 0);
+    double* tab = reinterpret_cast<double*>(buf.data());
+    float* tab32 = reinterpret_cast<float*>(buf.data() + 8 * n64);
+    unsigned char* nz = buf.data() + 8 * n64 + 4 * n32;
     for (int k = 0; k < kMaxH; k++)
         for (int o = 0; o < c1; o++) {
-            tab[(size_t)k * c1 + o] = m->rates.mu[k] * (double)o / m->rates.Lam;
-            tab[(size_t)(kMaxH + k) * c1 + o] = m->rates.delta[k] * (double)o / m->rates.Lam;
+            const double pc = r.mu[k] * (double)o / r.Lam;
+            tab[(size_t)k * c1 + o] = pc;
+            tab[(size_t)(kMaxH + k) * c1 + o] = r.delta[k] * (double)o / r.Lam;
+            tab32[(size_t)k * c1 + o] = (float)pc;
+            nz[(size_t)k * c1 + o] = pc != 0.0 ? 1 : 0;
         }
+    r.nz_pdep = r.nz_p1 = 0u;
+    for (int k = 0; k < kMaxH; k++) {
+        const double p1 = tab[(size_t)k * c1 + 1] + r.pdep[k];
+        r.pdep32[k] = (float)r.pdep[k];
+        r.p1_32[k] = (float)p1;
+        if (r.pdep[k] != 0.0) r.nz_pdep |= 1u << k;
+        if (p1 != 0.0) r.nz_p1 |= 1u << k;
+    }
+    r.parr32 = (float)r.parr;
+    r.nz_parr = r.parr != 0.0;
+    for (int ph = 0; ph < 2; ph++) {
+        r.pflip32[ph] = (float)r.pflip[ph];
+        r.nz_pflip[ph] = r.pflip[ph] != 0.0;
+    }
     int rc;
-    if ((rc = alloc_dev(m, (void**)&m->rate_tab, sizeof(double) * tab.size()))) return rc;
-    VC_CUDA(cudaMemcpyAsync(m->rate_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
-    VC_CUDA(cudaStreamSynchronize(st));  // tab is pageable host memory
-    m->rates.occ_tab = m->rate_tab;
+    if ((rc = alloc_dev(m, (void**)&m->rate_tab, bytes))) return rc;
+    VC_CUDA(cudaMemcpyAsync(m->rate_tab, buf.data(), bytes, cudaMemcpyHostToDevice, st));
+    VC_CUDA(cudaStreamSynchronize(st));  // buf is pageable host memory
+    r.occ_tab = m->rate_tab;
+    r.occ_tab32 = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(m->rate_tab) + 8 * n64);
+    r.occ_nz = reinterpret_cast<const unsigned char*>(m->rate_tab) + 8 * n64 + 4 * n32;
     return VC_OK;
 }
 
@@ -246,6 +272,138 @@ __global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const 
         nz += __shfl_xor_sync(0xffffffffu, nz, o);
     }
     if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&tallies[0], feas);
+        atomicAdd(&tallies[1], nz);
+    }
+}
+
+// model_row_emit with FP32 values, for the FP32 fill: the same successors in the same order,
+// each value the FP32 rounding of model_row_emit's FP64 probability.  The per-event values
+// and their non-zero tests come from the host-formed tables of Rates; only what a row sums
+// (the self-loop remainder and the reward) is formed here in FP64, with model_row_emit's
+// operations in its order (the occupancy sum, exact in FP64, is kept as an integer).
+template <int MH, typename Emit>
+__device__ __forceinline__ int model_row_emit_f32(const Model& md, const Rates& rt, int s, int a, double* R,
+                                                  Emit&& emit) {
+    Digits d;
+    decode<MH>(md, s, d);
+    int x = s;
+    if (a < md.H && !apply_action<MH>(md, s, a, d, x)) return -1;
+    const int c1 = rt.tab_c1;
+    double total = 0.0, self_extra = 0.0, lost = 0.0;
+    int occ_sum = 0;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            const double pdep = rt.pdep[k];
+            total += __ldg(rt.occ_tab + (size_t)k * c1 + o) + pdep;
+            occ_sum += o;
+            lost += __ldg(rt.occ_tab + (size_t)(kMaxH + k) * c1 + o);
+            if (o == 0) self_extra += pdep;
+        }
+    }
+    const double parr = rt.parr;
+    total += parr;
+    if (d.q >= md.Q) {
+        self_extra += parr;
+        lost += parr;
+    }
+    total += d.ph ? rt.pflip[1] : rt.pflip[0];
+    const double pself = (1.0 - total) + self_extra;
+    *R = rt.w_occ * (double)occ_sum + rt.w_q * d.q + rt.w_loss * lost;
+    int n = 0;
+#pragma unroll
+    for (int k = MH - 1; k >= 0; k--) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o == 1) {
+                if ((rt.nz_p1 >> k) & 1u) emit(n++, x - md.stride[k], rt.p1_32[k]);
+            } else if (o > 1) {
+                if ((rt.nz_pdep >> k) & 1u) emit(n++, x - o * md.stride[k], rt.pdep32[k]);
+                if (__ldg(rt.occ_nz + (size_t)k * c1 + o)) emit(n++, x - md.stride[k], __ldg(rt.occ_tab32 + (size_t)k * c1 + o));
+            }
+        }
+    }
+    const float pflip32 = d.ph ? rt.pflip32[1] : rt.pflip32[0];
+    const int nzflip = d.ph ? rt.nz_pflip[1] : rt.nz_pflip[0];
+    if (d.ph) {
+        if (nzflip) emit(n++, x - 1, pflip32);
+        if (pself != 0.0) emit(n++, x, (float)pself);
+    } else {
+        if (pself != 0.0) emit(n++, x, (float)pself);
+        if (nzflip) emit(n++, x + 1, pflip32);
+    }
+    if (d.q < md.Q && rt.nz_parr) emit(n++, x + 2, rt.parr32);
+    return n;
+}
+
+// FP32 fill: a warp's 32 consecutive rows occupy one contiguous range of the CSR, so each
+// lane writes its row into the warp's shared-memory stage and the warp then stores the
+// range lane-consecutively (coalesced) instead of each lane striding through its own row.
+constexpr int kFillThreads = 128;
+
+template <int MH>
+__global__ void __launch_bounds__(kFillThreads) k_row_fill32(Model md, Rates rt, int64_t nrows, int padded,
+                                                             const int64_t* __restrict__ row_ptr,
+                                                             int32_t* __restrict__ col, float* __restrict__ val,
+                                                             float* __restrict__ R, unsigned long long* tallies) {
+    constexpr int kW = 2 * MH + 3;  // most entries of a row
+    __shared__ int32_t s_col[kFillThreads / 32][32 * kW];
+    __shared__ float s_val[kFillThreads / 32][32 * kW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * kFillThreads + warp * 32;
+    if (r0 >= nrows) return;  // whole warps only
+    const int64_t r = r0 + lane;
+    const int64_t rend = (r0 + 32 < nrows) ? r0 + 32 : nrows;
+    const int64_t b0 = row_ptr[r0];
+    const int width = 2 * md.H + 3;
+    unsigned long long feas = 0, nz = 0;
+    if (r < nrows) {
+        const int s = (int)(r / md.A), a = (int)(r % md.A);
+        const int off = (int)(row_ptr[r] - b0);
+        int32_t* cs = &s_col[warp][off];
+        float* vs = &s_val[warp][off];
+        double Rv;
+        int last = s;
+        const int n = model_row_emit_f32<MH>(md, rt, s, a, &Rv, [&](int j, int c, float p) {
+            cs[j] = c;
+            vs[j] = p;
+            last = c;
+        });
+        if (n < 0) {
+            R[r] = -INFINITY;
+            if (padded)
+                for (int j = 0; j < width; j++) {
+                    cs[j] = s;
+                    vs[j] = 0.0f;
+                }
+        } else {
+            R[r] = (float)Rv;
+            if (padded)
+                for (int j = n; j < width; j++) {
+                    cs[j] = last;
+                    vs[j] = 0.0f;
+                }
+            feas = 1;
+            nz = (unsigned long long)n;
+        }
+    }
+    __syncwarp();
+    const int nent = (int)(row_ptr[rend] - b0);
+#ifdef VC_DEBUG_BOUNDS
+    if (nent > 32 * kW) return;
+#endif
+    for (int i = lane; i < nent; i += 32) {
+        col[b0 + i] = s_col[warp][i];
+        val[b0 + i] = s_val[warp][i];
+    }
+    if (!tallies) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        feas += __shfl_xor_sync(0xffffffffu, feas, o);
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    }
+    if (lane == 0) {
         atomicAdd(&tallies[0], feas);
         atomicAdd(&tallies[1], nz);
     }
@@ -434,8 +592,8 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
             k_row_fill<MH, true><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val,
                                                   m->scale, m->R, fill_tallies);
         else
-            k_row_fill<MH, false><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val,
-                                                   nullptr, m->R, fill_tallies);
+            k_row_fill32<MH><<<(unsigned)((nrows + kFillThreads - 1) / kFillThreads), kFillThreads, 0, st>>>(
+                m->md, m->rates, nrows, padded, m->row_ptr, m->col, (float*)m->val, m->R, fill_tallies);
     });
     VC_CUDA(cudaGetLastError());
     if (padded) {

@@ -98,6 +98,16 @@ struct Rates {
     double pflip[2];         // f / Lam, (1 - f) / Lam
     const double* occ_tab;   // device [2][kMaxH][C+1]: mu_k o / Lam, delta_k o / Lam (or null)
     int tab_c1;              // C + 1
+    // The FP32 roundings (to nearest) of the probabilities the CSR rows hold, formed on the
+    // host from the FP64 values above, and their non-zero tests taken on those FP64 values,
+    // so the FP32 fill emits exactly the FP64 path's entries and their rounded values.
+    float pdep32[kMaxH];            // (float) pdep[k]
+    float p1_32[kMaxH];             // (float)(mu_k / Lam + pdep[k]): occ_k = 1 (completion and departure merged)
+    float parr32, pflip32[2];
+    uint32_t nz_pdep, nz_p1;        // bit k: pdep[k] != 0, mu_k / Lam + pdep[k] != 0
+    int nz_parr, nz_pflip[2];
+    const float* occ_tab32;         // device [kMaxH][C+1]: (float)(mu_k o / Lam)
+    const unsigned char* occ_nz;    // device [kMaxH][C+1]: mu_k o / Lam != 0
 };
 
 // Digits of a state code.
