@@ -34,36 +34,55 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 static void free_mdp(Mdp* m) {
     if (!m) return;
-    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->val64, m->R64, m->rate_tab, m->Vb, m->U32, m->U32s, m->U64, m->V64a,
-                    m->V64b, m->E0, m->E1, m->Rres, m->pi, m->pi2, m->kr, m->kr_part, m->kctl, m->ctl,
+    void* ptrs[] = {m->row_ptr, m->col, m->val, m->scale, m->R, m->val64, m->R64, m->rate_tab, m->work,
                     m->sell_rec, m->sell_slab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (m->ctl_host) cudaFreeHost(m->ctl_host);
-    if (m->kctl_host) cudaFreeHost(m->kctl_host);
+    if (m->work_host) cudaFreeHost(m->work_host);
     delete m;
 }
 
+// The handle's work buffers, one device allocation carved into 256-byte-aligned parts (a
+// cudaMalloc per buffer costs tens of microseconds each), and the pinned mirrors of the two
+// control blocks, one pinned allocation.
 static int alloc_work(Mdp* m) {
-    int rc;
     const size_t S = (size_t)m->S;
-    if ((rc = alloc_dev(m, (void**)&m->Vb, 4 * S))) return rc;
-    if ((m->fmt & 0xF) == VC_IMPLICIT && (rc = alloc_dev(m, (void**)&m->U32, 4 * S))) return rc;
-    if ((m->fmt & 0xF) == VC_IMPLICIT && (rc = alloc_dev(m, (void**)&m->U32s, 4 * S))) return rc;
-    if (m->has_model && (rc = alloc_dev(m, (void**)&m->U64, 8 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->V64a, 8 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->V64b, 8 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->E0, 4 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->E1, 4 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->Rres, 4 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->pi, 4 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->pi2, 4 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->kr, 20 * S))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->kr_part, 24 * (size_t)state_grid(m)))) return rc;
-    if ((rc = alloc_dev(m, (void**)&m->kctl, sizeof(KrylovCtl)))) return rc;
-    VC_CUDA(cudaMallocHost((void**)&m->kctl_host, sizeof(KrylovCtl)));
-    if ((rc = alloc_dev(m, (void**)&m->ctl, sizeof(Ctl)))) return rc;
-    VC_CUDA(cudaMallocHost((void**)&m->ctl_host, sizeof(Ctl)));
+    const bool implicit = (m->fmt & 0xF) == VC_IMPLICIT;
+    struct Part {
+        void** p;
+        size_t bytes;
+    };
+    const Part parts[] = {
+        {(void**)&m->Vb, 4 * S},
+        {(void**)&m->U32, implicit ? 4 * S : 0},
+        {(void**)&m->U32s, implicit ? 4 * S : 0},
+        {(void**)&m->U64, m->has_model ? 8 * S : 0},
+        {(void**)&m->V64a, 8 * S},
+        {(void**)&m->V64b, 8 * S},
+        {(void**)&m->E0, 4 * S},
+        {(void**)&m->E1, 4 * S},
+        {(void**)&m->Rres, 4 * S},
+        {(void**)&m->pi, 4 * S},
+        {(void**)&m->pi2, 4 * S},
+        {(void**)&m->kr, 20 * S},
+        {(void**)&m->kr_part, 24 * (size_t)state_grid(m)},
+        {(void**)&m->kctl, sizeof(KrylovCtl)},
+        {(void**)&m->ctl, sizeof(Ctl)},
+    };
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t total = 0;
+    for (const Part& q : parts) total += up(q.bytes);
+    int rc;
+    if ((rc = alloc_dev(m, &m->work, total))) return rc;
+    size_t off = 0;
+    for (const Part& q : parts) {
+        *q.p = q.bytes ? static_cast<void*>(static_cast<unsigned char*>(m->work) + off) : nullptr;
+        off += up(q.bytes);
+    }
+    const size_t kbytes = up(sizeof(KrylovCtl));
+    VC_CUDA(cudaMallocHost(&m->work_host, kbytes + sizeof(Ctl)));
+    m->kctl_host = static_cast<KrylovCtl*>(m->work_host);
+    m->ctl_host = reinterpret_cast<Ctl*>(static_cast<unsigned char*>(m->work_host) + kbytes);
     memset(m->ctl_host, 0, sizeof(Ctl));
     VC_CUDA(cudaMemset(m->ctl, 0, sizeof(Ctl)));
     return VC_OK;

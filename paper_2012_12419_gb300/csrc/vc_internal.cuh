@@ -651,8 +651,11 @@ struct Mdp {
     int64_t sell_slices = 0, nnz_sliced = 0, sell_bytes = 0;
     int64_t* sell_rec = nullptr;          // [G + 1] record offsets in units of 128 bytes
     unsigned char* sell_slab = nullptr;   // the records
-    std::vector<int64_t> sell_slice_rows;  // host: rows of 32 entries per slice (planning)
-    // work buffers (owned)
+    int64_t sell_max_tile[3] = {0, 0, 0};  // bytes of the largest tile of 1, 2, 4 slice records (planning)
+    // work buffers: carved out of one owned allocation (work), the two pinned mirrors out
+    // of one pinned allocation (work_host)
+    void* work = nullptr;
+    void* work_host = nullptr;
     float* Vb = nullptr;        // FP32 ping-pong partner
     float* U32 = nullptr;       // FP32 post-decision values (implicit)
     float* U32s = nullptr;      // FP32 defer values with the self-transition solved (implicit)

@@ -94,9 +94,12 @@ __device__ __forceinline__ int row_nonzeros(const int64_t* __restrict__ row_ptr,
 
 // Sort key of a state: feasible-action mask (bits 32..62), 2^20 - 1 - total non-zero row
 // length (bits 12..31), index inside its window (bits 0..11).  Padding states past S get ~0.
+// Every row's non-zero count also goes to nzc (255: 255 or more, to be counted again),
+// which the width pass reads instead of the values.
 template <typename VT>
 __global__ void k_sell_keys(const int64_t* __restrict__ row_ptr, const VT* __restrict__ val,
-                            const float* __restrict__ R, int S, int A, int64_t n_pad, uint64_t* __restrict__ keys) {
+                            const float* __restrict__ R, int S, int A, int64_t n_pad, uint64_t* __restrict__ keys,
+                            unsigned char* __restrict__ nzc) {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad;
          s += (int64_t)gridDim.x * blockDim.x) {
         if (s >= S) {
@@ -107,10 +110,13 @@ __global__ void k_sell_keys(const int64_t* __restrict__ row_ptr, const VT* __res
         int64_t tot = 0;
         for (int a = 0; a < A; ++a) {
             const int64_t r = s * A + a;
+            int n = 0;
             if (R[r] != -INFINITY) {
                 mask |= 1u << (a < 30 ? a : 30);
-                tot += row_nonzeros(row_ptr, val, r);
+                n = row_nonzeros(row_ptr, val, r);
+                tot += n;
             }
+            nzc[r] = (unsigned char)(n < 255 ? n : 255);
         }
         const uint64_t len = (uint64_t)(tot < 0xFFFFF ? tot : 0xFFFFF);
         keys[s] = ((uint64_t)mask << 32) | ((0xFFFFFull - len) << 12) | (uint64_t)(s & (kSellSigma - 1));
@@ -145,12 +151,15 @@ __global__ void __launch_bounds__(1024) k_sell_sort(const uint64_t* __restrict__
     }
 }
 
-// Warp per slice: width(g, a) = longest feasible row (non-zero entries) among the slice's
-// lanes; the record size of the slice in units of 128 bytes.
+// Warp per slice: width(g, a) = longest feasible row (non-zero entries, from nzc) among
+// the slice's lanes; the record size of the slice in units of 128 bytes; the slice's rows
+// added to stats[0].
 template <typename VT>
 __global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const VT* __restrict__ val,
-                             const float* __restrict__ R, const int32_t* __restrict__ perm, int A, int64_t G, int vt,
-                             int has_scale, int32_t* __restrict__ width, int32_t* __restrict__ rec_units) {
+                             const float* __restrict__ R, const unsigned char* __restrict__ nzc,
+                             const int32_t* __restrict__ perm, int A, int64_t G, int vt, int has_scale,
+                             int32_t* __restrict__ width, int32_t* __restrict__ rec_units,
+                             unsigned long long* __restrict__ stats) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
@@ -160,13 +169,45 @@ __global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const VT* __re
             int len = 0;
             if (s >= 0) {
                 const int64_t r = (int64_t)s * A + a;
-                if (R[r] != -INFINITY) len = row_nonzeros(row_ptr, val, r);
+                if (R[r] != -INFINITY) {
+                    len = nzc[r];
+                    if (len == 255) len = row_nonzeros(row_ptr, val, r);
+                }
             }
             const int w = __reduce_max_sync(0xffffffffu, len);
             if (lane == 0) width[g * A + a] = w;
             rows += w;
         }
-        if (lane == 0) rec_units[g] = (int32_t)(rec_layout(A, rows, vt, has_scale != 0).bytes / 128);
+        if (lane == 0) {
+            rec_units[g] = (int32_t)(rec_layout(A, rows, vt, has_scale != 0).bytes / 128);
+            atomicAdd(&stats[0], (unsigned long long)rows);
+        }
+    }
+}
+
+// Largest tile of TS = 1, 2 and 4 consecutive slice records, in bytes, from the record
+// offsets (units of 128 bytes): stats[1..3] (the pipelined sweep's ring must hold it).
+__global__ void k_sell_tile_max(const int64_t* __restrict__ rec, int64_t G, unsigned long long* __restrict__ stats) {
+    // a tile of at most 4 records of at most 2^31 / 4 bytes each: 32-bit maxima per warp
+    unsigned int m1 = 0, m2 = 0, m4 = 0;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r0 = rec[g];
+        // bytes of the tiles starting here, clamped to 32 bits (no ring holds 4 GB)
+        auto bytes = [&](int64_t g1) {
+            const long long b = (rec[g1 < G ? g1 : G] - r0) * 128LL;
+            return (unsigned int)(b < 0xFFFFFFFFLL ? b : 0xFFFFFFFFLL);
+        };
+        m1 = max(m1, bytes(g + 1));
+        if ((g & 1) == 0) m2 = max(m2, bytes(g + 2));
+        if ((g & 3) == 0) m4 = max(m4, bytes(g + 4));
+    }
+    m1 = __reduce_max_sync(0xffffffffu, m1);
+    m2 = __reduce_max_sync(0xffffffffu, m2);
+    m4 = __reduce_max_sync(0xffffffffu, m4);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&stats[1], (unsigned long long)m1);
+        atomicMax(&stats[2], (unsigned long long)m2);
+        atomicMax(&stats[3], (unsigned long long)m4);
     }
 }
 
@@ -257,22 +298,26 @@ int build_sliced(Mdp* m, cudaStream_t st) {
     const int64_t n_pad = (S + kSellSigma - 1) / kSellSigma * kSellSigma;
     const int64_t G = (S + kSellC - 1) / kSellC;
     int rc;
-    // temporaries: keys, state map, widths, record sizes (freed below)
-    uint64_t* keys = nullptr;
-    int32_t *perm = nullptr, *width = nullptr, *units = nullptr;
-    auto cleanup = [&]() {
-        cudaFree(keys);
-        cudaFree(perm);
-        cudaFree(width);
-        cudaFree(units);
-    };
-    cudaError_t e = cudaMalloc((void**)&keys, 8 * (size_t)n_pad);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&perm, 4 * (size_t)n_pad);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&width, 4 * (size_t)(G * A + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&units, 4 * (size_t)(G + 1));
-    if (e != cudaSuccess) {
+    // temporaries, one allocation (freed below): keys, state map, widths, record sizes,
+    // per-row non-zero counts, and the statistics read back at the end
+    const size_t o_keys = 0, o_perm = o_keys + 8 * (size_t)n_pad, o_width = o_perm + 4 * (size_t)n_pad;
+    const size_t o_units = o_width + ((4 * (size_t)(G * A + 1) + 255) & ~(size_t)255);
+    const size_t o_nzc = o_units + ((4 * (size_t)(G + 1) + 255) & ~(size_t)255);
+    const size_t o_stats = o_nzc + (((size_t)S * A + 255) & ~(size_t)255);
+    const size_t tmp_bytes = o_stats + 64;
+    unsigned char* tmp = nullptr;
+    cudaError_t e = cudaMalloc((void**)&tmp, tmp_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(sliced layout temporaries)");
+    auto cleanup = [&]() { cudaFree(tmp); };
+    uint64_t* keys = reinterpret_cast<uint64_t*>(tmp + o_keys);
+    int32_t* perm = reinterpret_cast<int32_t*>(tmp + o_perm);
+    int32_t* width = reinterpret_cast<int32_t*>(tmp + o_width);
+    int32_t* units = reinterpret_cast<int32_t*>(tmp + o_units);
+    unsigned char* nzc = tmp + o_nzc;
+    unsigned long long* stats = reinterpret_cast<unsigned long long*>(tmp + o_stats);  // rows, max tiles (1, 2, 4)
+    if ((e = cudaMemsetAsync(stats, 0, 64, st)) != cudaSuccess) {
         cleanup();
-        return cuda_fail(e, "cudaMalloc(sliced layout temporaries)");
+        return cuda_fail(e, "sliced layout: statistics reset");
     }
     if ((rc = alloc_dev(m, (void**)&m->sell_rec, 8 * (size_t)(G + 2)))) {
         cleanup();
@@ -281,17 +326,17 @@ int build_sliced(Mdp* m, cudaStream_t st) {
     count_launches(3);
     if (bf16)
         k_sell_keys<uint16_t><<<warp_grid(n_pad / 32 + 1, m->num_sms), kThreads, 0, st>>>(
-            m->row_ptr, (const uint16_t*)m->val, m->R, (int)S, A, n_pad, keys);
+            m->row_ptr, (const uint16_t*)m->val, m->R, (int)S, A, n_pad, keys, nzc);
     else
         k_sell_keys<float><<<warp_grid(n_pad / 32 + 1, m->num_sms), kThreads, 0, st>>>(
-            m->row_ptr, (const float*)m->val, m->R, (int)S, A, n_pad, keys);
+            m->row_ptr, (const float*)m->val, m->R, (int)S, A, n_pad, keys, nzc);
     k_sell_sort<<<(unsigned)(n_pad / kSellSigma), 1024, 0, st>>>(keys, perm);
     if (bf16)
         k_sell_width<uint16_t><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(
-            m->row_ptr, (const uint16_t*)m->val, m->R, perm, A, G, vt, 1, width, units);
+            m->row_ptr, (const uint16_t*)m->val, m->R, nzc, perm, A, G, vt, 1, width, units, stats);
     else
-        k_sell_width<float><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(m->row_ptr, (const float*)m->val, m->R,
-                                                                           perm, A, G, vt, 0, width, units);
+        k_sell_width<float><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(
+            m->row_ptr, (const float*)m->val, m->R, nzc, perm, A, G, vt, 0, width, units, stats);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         cleanup();
@@ -314,7 +359,7 @@ int build_sliced(Mdp* m, cudaStream_t st) {
         cleanup();
         return rc;
     }
-    count_launches(1);
+    count_launches(2);
     if (bf16)
         k_sell_fill<uint16_t><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(
             m->row_ptr, m->col, (const uint16_t*)m->val, m->R, m->scale, perm, width, A, G, m->sell_rec,
@@ -322,22 +367,17 @@ int build_sliced(Mdp* m, cudaStream_t st) {
     else
         k_sell_fill<float><<<warp_grid(G, m->num_sms), kThreads, 0, st>>>(
             m->row_ptr, m->col, (const float*)m->val, m->R, nullptr, perm, width, A, G, m->sell_rec, m->sell_slab);
+    k_sell_tile_max<<<(unsigned)std::min<int64_t>((G + kThreads - 1) / kThreads, (int64_t)m->num_sms * 4), kThreads,
+                      0, st>>>(m->sell_rec, G, stats);
     e = cudaGetLastError();
-    // rows per slice (host copy of the widths) for planning and the entry count
-    std::vector<int32_t> w((size_t)(G * A));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w.data(), width, 4 * w.size(), cudaMemcpyDeviceToHost, st);
+    // the rows of the copy and its largest tiles, for the entry count and the planner
+    unsigned long long sh[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sh, stats, sizeof(sh), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "sliced layout: fill");
-    m->sell_slice_rows.assign((size_t)G, 0);
-    int64_t rows = 0;
-    for (int64_t g = 0; g < G; ++g) {
-        int64_t r = 0;
-        for (int a = 0; a < A; ++a) r += w[(size_t)(g * A + a)];
-        m->sell_slice_rows[(size_t)g] = r;
-        rows += r;
-    }
-    m->nnz_sliced = rows * kSellC;
+    m->nnz_sliced = (int64_t)sh[0] * kSellC;
+    for (int k = 0; k < 3; ++k) m->sell_max_tile[k] = (int64_t)sh[k + 1];
     return VC_OK;
 }
 
@@ -752,24 +792,17 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
     out.clear();
     if (!m->sell_slab) return VC_OK;
     const bool bf16 = (m->fmt & 0xF) == VC_CSR_BF16;
-    const int vt = bf16 ? 2 : 4;
     const int A = m->A;
     int dev = 0, smem_sm = 0, smem_blk = 0;
     VC_CUDA(cudaGetDevice(&dev));
     VC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     VC_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const std::vector<int64_t>& rows = m->sell_slice_rows;
+
     // (CTAs per SM, consumer warps, register budget), preferred first
     const int shapes[][3] = {{2, 12, 1}, {2, 16, 2}, {3, 10, 2}, {1, 24, 1}, {2, 8, 1}, {3, 8, 1}};
     for (int TS : {1, 2, 4}) {
         static_assert(kMaxTS >= 4, "the last block's registers cover every planned tile size");
-        long long max_tile = 0;  // largest tile of TS slice records
-        for (int64_t g0 = 0; g0 < (int64_t)rows.size(); g0 += TS) {
-            long long b = 0;
-            const int ns = (int)std::min<int64_t>(TS, (int64_t)rows.size() - g0);
-            for (int k = 0; k < ns; ++k) b += rec_layout(A, rows[g0 + k], vt, bf16).bytes;
-            max_tile = std::max<long long>(max_tile, b);
-        }
+        const long long max_tile = m->sell_max_tile[TS == 1 ? 0 : (TS == 2 ? 1 : 2)];  // largest tile of TS records
         for (auto& sh : shapes) {
             const int ctas = sh[0], nrw = sh[1], mb = sh[2];
             const void* fn = ring_fn(bf16, mb, false);
