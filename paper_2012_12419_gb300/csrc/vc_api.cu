@@ -7,7 +7,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "vc_internal.cuh"
 #include "vc_krylov.cuh"
@@ -86,6 +89,61 @@ static int alloc_work(Mdp* m) {
     memset(m->ctl_host, 0, sizeof(Ctl));
     VC_CUDA(cudaMemset(m->ctl, 0, sizeof(Ctl)));
     return VC_OK;
+}
+
+namespace {
+std::mutex g_cache_mu;
+std::map<std::pair<int, const void*>, cudaFuncAttributes> g_attr_cache;
+std::map<std::pair<int, const void*>, int> g_smem_cache;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_occ_cache;
+
+int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev;
+}
+}  // namespace
+
+cudaError_t cached_func_attributes(const void* fn, cudaFuncAttributes* fa) {
+    const auto key = std::make_pair(current_device(), fn);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_attr_cache.find(key);
+    if (it != g_attr_cache.end()) {
+        *fa = it->second;
+        return cudaSuccess;
+    }
+    const cudaError_t e = cudaFuncGetAttributes(fa, fn);
+    if (e == cudaSuccess) g_attr_cache[key] = *fa;
+    return e;
+}
+
+cudaError_t cached_set_max_dyn_smem(const void* fn, int bytes) {
+    const auto key = std::make_pair(current_device(), fn);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_smem_cache.find(key);
+    if (it != g_smem_cache.end() && it->second == bytes) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) {
+        g_smem_cache[key] = bytes;
+        // occupancy answers depend on the attribute: drop this kernel's cached ones
+        for (auto o = g_occ_cache.begin(); o != g_occ_cache.end();)
+            o = (std::get<0>(o->first) == key.first && std::get<1>(o->first) == fn) ? g_occ_cache.erase(o)
+                                                                                      : std::next(o);
+    }
+    return e;
+}
+
+cudaError_t cached_occupancy(const void* fn, int threads, size_t smem, int* per_sm) {
+    const auto key = std::make_tuple(current_device(), fn, threads, smem);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_occ_cache.find(key);
+    if (it != g_occ_cache.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads, smem);
+    if (e == cudaSuccess) g_occ_cache[key] = *per_sm;
+    return e;
 }
 
 static int device_sms() {

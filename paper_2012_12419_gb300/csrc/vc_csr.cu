@@ -605,21 +605,20 @@ static int pow2_at_least(int a) {
 template <typename VT, int APAD>
 static cudaError_t set_tma_smem(int bytes, int* dyn_limit) {
     cudaFuncAttributes fa, fb;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_csr_tma<VT, APAD, false>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fb, k_csr_tma<VT, APAD, true>);
+    cudaError_t e = cached_func_attributes((const void*)k_csr_tma<VT, APAD, false>, &fa);
+    if (e == cudaSuccess) e = cached_func_attributes((const void*)k_csr_tma<VT, APAD, true>, &fb);
     if (e != cudaSuccess) return e;
     *dyn_limit = bytes - (int)std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
-    e = cudaFuncSetAttribute(k_csr_tma<VT, APAD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_limit);
+    e = cached_set_max_dyn_smem((const void*)k_csr_tma<VT, APAD, false>, *dyn_limit);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_csr_tma<VT, APAD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_limit);
+    return cached_set_max_dyn_smem((const void*)k_csr_tma<VT, APAD, true>, *dyn_limit);
 }
 
 template <typename VT, int APAD>
 static cudaError_t tma_occupancy(int bytes, int* per_sm) {
     int a = 0, b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_csr_tma<VT, APAD, false>, (kNW + 1) * 32, bytes);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_tma<VT, APAD, true>, (kNW + 1) * 32, bytes);
+    cudaError_t e = cached_occupancy((const void*)k_csr_tma<VT, APAD, false>, (kNW + 1) * 32, bytes, &a);
+    if (e == cudaSuccess) e = cached_occupancy((const void*)k_csr_tma<VT, APAD, true>, (kNW + 1) * 32, bytes, &b);
     *per_sm = std::min(a, b);
     return e;
 }
@@ -662,28 +661,32 @@ static int enumerate_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
     VC_CUDA(cudaGetDevice(&dev));
     VC_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     VC_CUDA(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    unsigned long long* dcap = nullptr;
-    VC_CUDA(cudaMallocAsync((void**)&dcap, 8, st));
     struct Cand {
         int ts;
         long long cap;
     };
     std::vector<Cand> cands;
-    // tiles of 8, 4, 2, 1 and 1/2 state rows of the consumer warps (multiples of 4 states)
+    // tiles of 8, 4, 2, 1 and 1/2 state rows of the consumer warps (multiples of 4 states);
+    // their largest entry counts, one kernel each, read back together
+    std::vector<int> sizes;
     for (int k2 = 16; k2 >= 1; k2 >>= 1) {
         const int ts = k2 * kNW * spw / 2;
-        if (ts < 4 || ts % 4) continue;
-        const int64_t nt = ((int64_t)m->S + ts - 1) / ts;
-        VC_CUDA(cudaMemsetAsync(dcap, 0, 8, st));
-        count_launches(1);
-        k_tile_cap<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(m->row_ptr, m->S, m->A, ts, nt, dcap);
-        VC_CUDA(cudaGetLastError());
-        unsigned long long cap = 0;
-        VC_CUDA(cudaMemcpyAsync(&cap, dcap, 8, cudaMemcpyDeviceToHost, st));
-        VC_CUDA(cudaStreamSynchronize(st));
-        cands.push_back({ts, (long long)cap + 16});
+        if (ts >= 4 && ts % 4 == 0) sizes.push_back(ts);
     }
+    unsigned long long* dcap = nullptr;
+    unsigned long long hcap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    VC_CUDA(cudaMallocAsync((void**)&dcap, sizeof(hcap), st));
+    VC_CUDA(cudaMemsetAsync(dcap, 0, sizeof(hcap), st));
+    for (size_t i = 0; i < sizes.size(); ++i) {
+        const int64_t nt = ((int64_t)m->S + sizes[i] - 1) / sizes[i];
+        count_launches(1);
+        k_tile_cap<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(m->row_ptr, m->S, m->A, sizes[i], nt, dcap + i);
+    }
+    VC_CUDA(cudaGetLastError());
+    VC_CUDA(cudaMemcpyAsync(hcap, dcap, sizeof(hcap), cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaFreeAsync(dcap, st));
+    VC_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < sizes.size(); ++i) cands.push_back({sizes[i], (long long)hcap[i] + 16});
     // one attribute per kernel instance: allow the largest request, launches ask for less
     int dyn_limit = 0;
     cudaError_t e = bf16 ? set_tma_smem_any<uint16_t>(apad, smem_blk, &dyn_limit)
@@ -721,6 +724,11 @@ static int enumerate_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
 
 // Default plan: the first candidate (the direct kernel if none fits).
 int plan_csr(Mdp* m, cudaStream_t st) {
+    // a handle built with its sliced copy takes its plan from the sliced layout
+    if (m->fmt & VC_SLICED) {
+        m->plan = CsrPlan();
+        return VC_OK;
+    }
     std::vector<CsrPlan> cands;
     int rc = enumerate_plans(m, st, cands);
     if (rc) return rc;

@@ -712,6 +712,12 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out);
 int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qgap, SweepCtl sc, cudaStream_t st);
 int64_t sell_sweep_bytes(const Mdp* m);
 int csr_candidates(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& cands);
+// Per-process caches, keyed by device, of a kernel's attributes, of its dynamic
+// shared-memory limit (set once) and of its occupancy for a launch shape: the queries cost
+// microseconds each and every handle plans its launches again.
+cudaError_t cached_func_attributes(const void* fn, cudaFuncAttributes* fa);
+cudaError_t cached_set_max_dyn_smem(const void* fn, int bytes);
+cudaError_t cached_occupancy(const void* fn, int threads, size_t smem, int* per_sm);
 int autotune_csr(Mdp* m, int reps, cudaStream_t st, double* best_us);
 
 // Grid of the persistent state-parallel kernels.

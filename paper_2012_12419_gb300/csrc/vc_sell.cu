@@ -808,14 +808,14 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             const void* fn = ring_fn(bf16, mb, false);
             const void* fn_sl = ring_fn(bf16, mb, true);
             cudaFuncAttributes fa, fa_sl;
-            VC_CUDA(cudaFuncGetAttributes(&fa, fn));
-            VC_CUDA(cudaFuncGetAttributes(&fa_sl, fn_sl));
+            VC_CUDA(cached_func_attributes(fn, &fa));
+            VC_CUDA(cached_func_attributes(fn_sl, &fa_sl));
             fa.numRegs = std::max(fa.numRegs, fa_sl.numRegs);
             fa.sharedSizeBytes = std::max(fa.sharedSizeBytes, fa_sl.sharedSizeBytes);
             fa.maxThreadsPerBlock = std::min(fa.maxThreadsPerBlock, fa_sl.maxThreadsPerBlock);
             const int dyn_max = smem_blk - (int)fa.sharedSizeBytes;
-            VC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-            VC_CUDA(cudaFuncSetAttribute(fn_sl, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+            VC_CUDA(cached_set_max_dyn_smem(fn, dyn_max));
+            VC_CUDA(cached_set_max_dyn_smem(fn_sl, dyn_max));
             const int threads = (nrw + 1) * 32;
             if (threads > fa.maxThreadsPerBlock || (long long)threads * fa.numRegs * ctas > 65536) continue;
             if (nrw > (kSlots - 2) * TS * A) continue;  // claimed blocks stay within kSlots tiles
@@ -827,8 +827,8 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             const int need = qoff + qbytes + ring;
             int per_sm = 0;
             int per_sm_sl = 0;
-            VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, (size_t)need));
-            VC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sl, fn_sl, threads, (size_t)need));
+            VC_CUDA(cached_occupancy(fn, threads, (size_t)need, &per_sm));
+            VC_CUDA(cached_occupancy(fn_sl, threads, (size_t)need, &per_sm_sl));
             per_sm = std::min(per_sm, per_sm_sl);
             if (per_sm < 1) continue;
             CsrPlan P;
