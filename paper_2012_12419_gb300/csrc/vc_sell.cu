@@ -433,13 +433,14 @@ __device__ __forceinline__ float dot_fixed(const int32_t* cp, const VT* vp, cons
         }
     }
     // the values are read from shared memory only once the gathers are in flight, so
-    // they hold no registers meanwhile
+    // they hold no registers meanwhile.  SL: the own-state entries' values are added to
+    // pss in column order in the same pass, fmaf(v, 1, pss) = pss + v for them and
+    // fmaf(v, 0, pss) = pss for the others (v >= 0), so pss is the plain column-order sum
 #pragma unroll
-    for (int u = 0; u < W; ++u) acc = fmaf(ld_val<VT>(vp + u * kSellC), gv[u], acc);
-    if (SL) {
-        // the own-state entries' values in column order (one non-zero at most in a
-        // generated row; padding entries add zeros)
-        for (; own; own &= own - 1) pss += ld_val<VT>(vp + (__ffs(own) - 1) * kSellC);
+    for (int u = 0; u < W; ++u) {
+        const float v = ld_val<VT>(vp + u * kSellC);
+        acc = fmaf(v, gv[u], acc);
+        if (SL) pss = fmaf(v, ((own >> u) & 1u) ? 1.0f : 0.0f, pss);
     }
     return acc;
 }
@@ -492,7 +493,13 @@ __device__ __forceinline__ float block_q(const unsigned char* rec, int A, int a,
     const int self = SL ? reinterpret_cast<const int32_t*>(rec + 128)[lane] : -1;
     const float acc = row_dot<VT, SL>(cp, vp, w, V, self, pss);
     const float sc = has_scale ? reinterpret_cast<const float*>(rec + L.scale)[a * kSellC + lane] : 1.0f;
-    if (SL) return q_self_loop(rr, gamma, has_scale ? sc * acc : acc, has_scale ? sc * pss : pss);
+    if (SL) {
+        const float off = has_scale ? sc * acc : acc, ps = has_scale ? sc * pss : pss;
+        // no self-transition (every placement row of the model): q_self_loop's denominator
+        // is exactly 1 and its quotient the numerator, so the division is skipped
+        if (ps == 0.0f) return fmaf(gamma, off, rr);
+        return q_self_loop(rr, gamma, off, ps);
+    }
     return rr + gamma * (has_scale ? sc * acc : acc);
 }
 
