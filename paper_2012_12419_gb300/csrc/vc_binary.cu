@@ -5,6 +5,8 @@
 // probabilities and rewards, which the FP64 refinement and certificate use.
 #include <math.h>
 
+#include <algorithm>
+
 #include "vc_internal.cuh"
 
 namespace vc {
@@ -71,26 +73,19 @@ __device__ __forceinline__ int bin_row_emit(const BinModel& md, int s, int a, do
     return j;
 }
 
-__global__ void k_bin_count(BinModel md, int64_t nrows, int32_t* cnt, unsigned long long* tallies) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_bin_count(BinModel md, int64_t nrows, int32_t* cnt,
+                                                        unsigned long long* tallies) {
     unsigned long long feas = 0, nz = 0;
-    if (r < nrows) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
         double R;
         const int n = bin_row_emit(md, (int)(r >> 1), (int)(r & 1), &R, [](int, int, double) {});
         cnt[r] = n < 0 ? 0 : n;
         if (n >= 0) {
-            feas = 1;
-            nz = (unsigned long long)n;
+            feas += 1;
+            nz += (unsigned long long)n;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        feas += __shfl_xor_sync(0xffffffffu, feas, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&tallies[0], feas);
-        atomicAdd(&tallies[1], nz);
-    }
+    block_tally<kThreads>(feas, nz, tallies);
 }
 
 // Nearest-even bfloat16 of a positive double through round-to-odd at float precision
@@ -190,7 +185,7 @@ int build_csr_binary(Mdp* m, const vc_binary_params* p, cudaStream_t st) {
     VC_CUDA(cudaMemsetAsync(tallies, 0, sizeof(unsigned long long) * 2, st));
     VC_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * nrows, st));
     count_launches(1);
-    k_bin_count<<<nb, T, 0, st>>>(md, nrows, cnt, tallies);
+    k_bin_count<<<(unsigned)std::min<int64_t>(nb, (int64_t)m->num_sms * 16), kThreads, 0, st>>>(md, nrows, cnt, tallies);
     VC_CUDA(cudaGetLastError());
     VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaStreamSynchronize(st));

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <type_traits>
+#include <algorithm>
 #include <vector>
 
 #include "vc_internal.cuh"
@@ -176,29 +177,23 @@ int upload_rate_table(Mdp* m, cudaStream_t st) {
     return VC_OK;
 }
 
+// Per-row entry counts (grid-stride), with the block's tallies of feasible rows and
+// logical non-zeros added once per block.
 template <int MH>
-__global__ void k_row_count(Model md, Rates rt, int64_t nrows, int32_t* cnt, unsigned long long* tallies) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_row_count(Model md, Rates rt, int64_t nrows, int32_t* cnt,
+                                                        unsigned long long* tallies) {
     unsigned long long feas = 0, nz = 0;
-    if (r < nrows) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(r / md.A), a = (int)(r % md.A);
         double R;
         const int n = model_row_emit<MH>(md, rt, s, a, &R, [](int, int, double) {});
         if (cnt) cnt[r] = n < 0 ? 0 : n;
         if (n >= 0) {
-            feas = 1;
-            nz = (unsigned long long)n;
+            feas += 1;
+            nz += (unsigned long long)n;
         }
     }
-    // block tallies of feasible rows and logical non-zeros
-    for (int o = 16; o > 0; o >>= 1) {
-        feas += __shfl_xor_sync(0xffffffffu, feas, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&tallies[0], feas);
-        atomicAdd(&tallies[1], nz);
-    }
+    block_tally<kThreads>(feas, nz, tallies);
 }
 
 // One row of the CSR fill, written as the row's entries come (ascending columns); returns
@@ -251,30 +246,23 @@ __device__ __forceinline__ int fill_row(const Model& md, const Rates& rt, int64_
     return n;
 }
 
-// Fills every row; with tallies (padded rows, where no count pass precedes the fill) it
-// also adds up the feasible rows and their non-zero successors.
+// Fills every row (BF16 values; grid-stride); with tallies (padded rows, where no count
+// pass precedes the fill) it also adds up the feasible rows and their non-zero successors,
+// once per block.
 template <int MH, bool kBf16>
-__global__ void k_row_fill(Model md, Rates rt, int64_t nrows, int padded, const int64_t* __restrict__ row_ptr,
-                           int32_t* __restrict__ col, void* __restrict__ val, float* __restrict__ scale,
-                           float* __restrict__ R, unsigned long long* tallies) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_row_fill(Model md, Rates rt, int64_t nrows, int padded,
+                                                       const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                                                       void* __restrict__ val, float* __restrict__ scale,
+                                                       float* __restrict__ R, unsigned long long* tallies) {
     unsigned long long feas = 0, nz = 0;
-    if (r < nrows) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
         const int n = fill_row<MH, kBf16>(md, rt, r, padded, row_ptr, col, val, scale, R);
         if (n >= 0) {
-            feas = 1;
-            nz = (unsigned long long)n;
+            feas += 1;
+            nz += (unsigned long long)n;
         }
     }
-    if (!tallies) return;
-    for (int o = 16; o > 0; o >>= 1) {
-        feas += __shfl_xor_sync(0xffffffffu, feas, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&tallies[0], feas);
-        atomicAdd(&tallies[1], nz);
-    }
+    if (tallies) block_tally<kThreads>(feas, nz, tallies);
 }
 
 // model_row_emit with FP32 values, for the FP32 fill: the same successors in the same order,
@@ -352,61 +340,54 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill32(Model md, Rates rt,
     __shared__ int32_t s_col[kFillThreads / 32][32 * kW];
     __shared__ float s_val[kFillThreads / 32][32 * kW];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = (int64_t)blockIdx.x * kFillThreads + warp * 32;
-    if (r0 >= nrows) return;  // whole warps only
-    const int64_t r = r0 + lane;
-    const int64_t rend = (r0 + 32 < nrows) ? r0 + 32 : nrows;
-    const int64_t b0 = row_ptr[r0];
     const int width = 2 * md.H + 3;
     unsigned long long feas = 0, nz = 0;
-    if (r < nrows) {
-        const int s = (int)(r / md.A), a = (int)(r % md.A);
-        const int off = (int)(row_ptr[r] - b0);
-        int32_t* cs = &s_col[warp][off];
-        float* vs = &s_val[warp][off];
-        double Rv;
-        int last = s;
-        const int n = model_row_emit_f32<MH>(md, rt, s, a, &Rv, [&](int j, int c, float p) {
-            cs[j] = c;
-            vs[j] = p;
-            last = c;
-        });
-        if (n < 0) {
-            R[r] = -INFINITY;
-            if (padded)
-                for (int j = 0; j < width; j++) {
-                    cs[j] = s;
-                    vs[j] = 0.0f;
-                }
-        } else {
-            R[r] = (float)Rv;
-            if (padded)
-                for (int j = n; j < width; j++) {
-                    cs[j] = last;
-                    vs[j] = 0.0f;
-                }
-            feas = 1;
-            nz = (unsigned long long)n;
+    // grid-stride over groups of 32 rows, one group per warp and step
+    for (int64_t r0 = ((int64_t)blockIdx.x * (kFillThreads / 32) + warp) * 32; r0 < nrows;
+         r0 += (int64_t)gridDim.x * kFillThreads) {
+        const int64_t r = r0 + lane;
+        const int64_t rend = (r0 + 32 < nrows) ? r0 + 32 : nrows;
+        const int64_t b0 = row_ptr[r0];
+        if (r < nrows) {
+            const int s = (int)(r / md.A), a = (int)(r % md.A);
+            const int off = (int)(row_ptr[r] - b0);
+            int32_t* cs = &s_col[warp][off];
+            float* vs = &s_val[warp][off];
+            double Rv;
+            int last = s;
+            const int n = model_row_emit_f32<MH>(md, rt, s, a, &Rv, [&](int j, int c, float p) {
+                cs[j] = c;
+                vs[j] = p;
+                last = c;
+            });
+            if (n < 0) {
+                R[r] = -INFINITY;
+                if (padded)
+                    for (int j = 0; j < width; j++) {
+                        cs[j] = s;
+                        vs[j] = 0.0f;
+                    }
+            } else {
+                R[r] = (float)Rv;
+                if (padded)
+                    for (int j = n; j < width; j++) {
+                        cs[j] = last;
+                        vs[j] = 0.0f;
+                    }
+                feas += 1;
+                nz += (unsigned long long)n;
+            }
         }
+        __syncwarp();
+        const int nent = (int)(row_ptr[rend] - b0);
+        const bool fits = nent <= 32 * kW;  // always: a row holds at most 2H + 3 entries
+        for (int i = lane; fits && i < nent; i += 32) {
+            col[b0 + i] = s_col[warp][i];
+            val[b0 + i] = s_val[warp][i];
+        }
+        __syncwarp();  // the stage is rewritten by the warp's next group
     }
-    __syncwarp();
-    const int nent = (int)(row_ptr[rend] - b0);
-#ifdef VC_DEBUG_BOUNDS
-    if (nent > 32 * kW) return;
-#endif
-    for (int i = lane; i < nent; i += 32) {
-        col[b0 + i] = s_col[warp][i];
-        val[b0 + i] = s_val[warp][i];
-    }
-    if (!tallies) return;
-    for (int o = 16; o > 0; o >>= 1) {
-        feas += __shfl_xor_sync(0xffffffffu, feas, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&tallies[0], feas);
-        atomicAdd(&tallies[1], nz);
-    }
+    if (tallies) block_tally<kFillThreads>(feas, nz, tallies);
 }
 
 __global__ void k_padded_rowptr(int64_t nrows, int width, int64_t* row_ptr) {
@@ -521,14 +502,13 @@ static void by_h_build(int H, F&& f) {
 
 int count_model_rows(Mdp* m, cudaStream_t st) {
     const int64_t nrows = (int64_t)m->S * m->A;
-    const int T = 256;
+    const unsigned grid = (unsigned)std::min<int64_t>((nrows + kThreads - 1) / kThreads, (int64_t)m->num_sms * 16);
     unsigned long long* tallies = nullptr;
     VC_CUDA(cudaMallocAsync((void**)&tallies, sizeof(unsigned long long) * 2, st));
     VC_CUDA(cudaMemsetAsync(tallies, 0, sizeof(unsigned long long) * 2, st));
     count_launches(1);
     by_h_build(m->md.H, [&](auto mh) {
-        k_row_count<decltype(mh)::value><<<(unsigned)((nrows + T - 1) / T), T, 0, st>>>(m->md, m->rates, nrows,
-                                                                                        nullptr, tallies);
+        k_row_count<decltype(mh)::value><<<grid, kThreads, 0, st>>>(m->md, m->rates, nrows, nullptr, tallies);
     });
     VC_CUDA(cudaGetLastError());
     unsigned long long th[2];
@@ -562,7 +542,8 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
         VC_CUDA(cudaMallocAsync((void**)&cnt, sizeof(int32_t) * nrows, st));
         count_launches(1);
         by_h_build(m->md.H, [&](auto mh) {
-            k_row_count<decltype(mh)::value><<<nb, T, 0, st>>>(m->md, m->rates, nrows, cnt, tallies);
+            k_row_count<decltype(mh)::value><<<(unsigned)std::min<int64_t>(nb, (int64_t)m->num_sms * 16), kThreads, 0,
+                                                st>>>(m->md, m->rates, nrows, cnt, tallies);
         });
         VC_CUDA(cudaGetLastError());
         VC_CUDA(cudaMemcpyAsync(th, tallies, sizeof(th), cudaMemcpyDeviceToHost, st));
@@ -589,9 +570,11 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
     by_h_build(m->md.H, [&](auto mh) {
         constexpr int MH = decltype(mh)::value;
         if (bf16)
-            k_row_fill<MH, true><<<nb, T, 0, st>>>(m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val,
+            k_row_fill<MH, true><<<(unsigned)std::min<int64_t>(nb, (int64_t)m->num_sms * 16), kThreads, 0, st>>>(
+                m->md, m->rates, nrows, padded, m->row_ptr, m->col, m->val,
                                                   m->scale, m->R, fill_tallies);
         else
+            // one group of 32 rows per warp (the kernel strides further if the grid is capped)
             k_row_fill32<MH><<<(unsigned)((nrows + kFillThreads - 1) / kFillThreads), kFillThreads, 0, st>>>(
                 m->md, m->rates, nrows, padded, m->row_ptr, m->col, (float*)m->val, m->R, fill_tallies);
     });
@@ -611,7 +594,7 @@ int build_csr_from_model(Mdp* m, cudaStream_t st) {
 // ------------------------------------------------------------------------ user CSR
 // Per row: columns in range, entries >= 0 and finite, feasible rows summing to 1 (after
 // the scale) within 1e-5, row_ptr non-decreasing.  Per state: one feasible row at least.
-__global__ void k_validate_rows(int S, int A, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_validate_rows(int S, int A, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const void* __restrict__ val, int bf16, float* __restrict__ scale,
                                 int compute_scale, const float* __restrict__ R, int* err,
                                 unsigned long long* tallies) {
@@ -652,14 +635,7 @@ __global__ void k_validate_rows(int S, int A, const int64_t* __restrict__ row_pt
         if (!any) flags |= kErrNoFeasible;
         if (flags) atomicOr(err, flags);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        feas += __shfl_xor_sync(0xffffffffu, feas, o);
-        nz += __shfl_xor_sync(0xffffffffu, nz, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&tallies[0], feas);
-        atomicAdd(&tallies[1], nz);
-    }
+    block_tally<kThreads>(feas, nz, tallies);
 }
 
 int build_csr_user(Mdp* m, const int64_t* row_ptr, const int32_t* col, const void* val, int val_dtype,

@@ -379,6 +379,33 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// Adds a block's two tallies (feasible rows, non-zero successors) to tallies[0..1] with one
+// atomic each (every thread of the block calls it).
+template <int NT>
+__device__ __forceinline__ void block_tally(unsigned long long feas, unsigned long long nz,
+                                            unsigned long long* tallies) {
+    __shared__ unsigned long long part[2][NT / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        feas += __shfl_xor_sync(0xffffffffu, feas, o);
+        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        part[0][w] = feas;
+        part[1][w] = nz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long f = 0, z = 0;
+        for (int i = 0; i < NT / 32; ++i) {
+            f += part[0][i];
+            z += part[1][i];
+        }
+        atomicAdd(&tallies[0], f);
+        atomicAdd(&tallies[1], z);
+    }
+}
+
 // Block-wide max of a non-negative value over NT threads; result valid in thread 0.
 // Every thread of the block must call it.
 template <typename T, int NT>

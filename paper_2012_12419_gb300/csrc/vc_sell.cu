@@ -160,8 +160,12 @@ __global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const VT* __re
                              const int32_t* __restrict__ perm, int A, int64_t G, int vt, int has_scale,
                              int32_t* __restrict__ width, int32_t* __restrict__ rec_units,
                              unsigned long long* __restrict__ stats) {
+    __shared__ unsigned long long s_rows;
+    if (threadIdx.x == 0) s_rows = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long warp_rows = 0;
     for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
         const int s = perm[g * kSellC + lane];
         long long rows = 0;
@@ -178,11 +182,13 @@ __global__ void k_sell_width(const int64_t* __restrict__ row_ptr, const VT* __re
             if (lane == 0) width[g * A + a] = w;
             rows += w;
         }
-        if (lane == 0) {
-            rec_units[g] = (int32_t)(rec_layout(A, rows, vt, has_scale != 0).bytes / 128);
-            atomicAdd(&stats[0], (unsigned long long)rows);
-        }
+        if (lane == 0) rec_units[g] = (int32_t)(rec_layout(A, rows, vt, has_scale != 0).bytes / 128);
+        warp_rows += (unsigned long long)rows;
     }
+    // the rows of the block's slices, one global atomic per block
+    if (lane == 0) atomicAdd(&s_rows, warp_rows);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&stats[0], s_rows);
 }
 
 // Largest tile of TS = 1, 2 and 4 consecutive slice records, in bytes, from the record
