@@ -486,6 +486,9 @@ typedef struct vc_batch_stats {
     double residual64;         /* FP64 max|T V - V| of its certified values */
     int32_t certified;         /* residual64 < tol */
     int32_t termination;       /* FP32 loop: 1 tolerance, 2 max_sweeps, 3 FP32 floor stall */
+    int32_t rounds;            /* refinement rounds until its certificate held (later rounds
+                                  skip it; 0 with VC_ITER_FP32_ONLY or if never certified) */
+    int32_t reserved;
 } vc_batch_stats;
 
 /*

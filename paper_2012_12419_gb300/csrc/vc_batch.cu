@@ -1489,7 +1489,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
     k_bselect<float, float><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, b->final_buf, b->Va,
                                                           b->Vb, V);
     VC_LAUNCHED("k_bselect");
-    std::vector<int> done(N), sweeps(N), csweeps(N, 0), cert(N, 0);
+    std::vector<int> done(N), sweeps(N), csweeps(N, 0), cert(N, 0), rounds(N, 0);
     std::vector<double> r64(N, INFINITY);
     VC_CUDA(cudaMemcpyAsync(done.data(), b->done, 4 * N, cudaMemcpyDeviceToHost, st));
     VC_CUDA(cudaMemcpyAsync(sweeps.data(), b->sweeps, 4 * N, cudaMemcpyDeviceToHost, st));
@@ -1588,6 +1588,7 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
                 memcpy(&r, &rb[i], 8);
                 r64[i] = r;
                 cert[i] = r < tol * (double)scale[i];
+                if (cert[i]) rounds[i] = round + 1;
                 all_cert = all_cert && cert[i];
             }
             if (all_cert) break;
@@ -1617,6 +1618,8 @@ int vc_value_iterate_batch(vc_batch* bh, float* V, double* V64_out, int32_t* pi_
             per_inst[i].residual64 = r64[i];
             per_inst[i].certified = cert[i];
             per_inst[i].termination = done[i];
+            per_inst[i].rounds = rounds[i];
+            per_inst[i].reserved = 0;
         }
     }
     if (flags & VC_ITER_FP32_ONLY) {

@@ -119,7 +119,8 @@ class BatchInfo(ctypes.Structure):
 class BatchStats(ctypes.Structure):
     _fields_ = [
         ("sweeps", ctypes.c_int64), ("correction_sweeps", ctypes.c_int64), ("residual64", ctypes.c_double),
-        ("certified", ctypes.c_int32), ("termination", ctypes.c_int32),
+        ("certified", ctypes.c_int32), ("termination", ctypes.c_int32), ("rounds", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -532,7 +533,7 @@ class Batch:
         rc = load().vc_value_iterate_batch(self._h, _ptr(V), _ptr(V64), _ptr(pi), float(tol), int(max_sweeps),
                                            flags, st, _stream(stream))
         _check(rc, allow=() if raise_on_nonconvergence else (VC_ERR_NOT_CONVERGED,))
-        stats = [{k: getattr(s, k) for k, _ in BatchStats._fields_} for s in st]
+        stats = [{k: getattr(s, k) for k, _ in BatchStats._fields_ if k != "reserved"} for s in st]
         return V, V64, pi, stats, rc
 
     def set_small_instances(self, max_states: int, stream=None) -> None:

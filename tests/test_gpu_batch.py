@@ -10,6 +10,9 @@
   1e-6 (1 - gamma) / (2 gamma); on sampled instances the oracle's own backup of sampled
   states of V64 is within that residual and the policy equals its argmax where the gap
   exceeds 1e-6; the smallest instances are compared with full oracle solves;
+* after an FP32 loop stopped early, the refinement's policy-improvement rounds certify the
+  instances in different rounds, skipping the certified ones, and every instance still
+  ends at the oracle's optimum;
 * every schedule the autotuner may pick gives the same iterates.
 """
 import numpy as np
@@ -55,6 +58,36 @@ def test_small_batch_matches_oracle_and_single_instance_solves():
         assert st2["certified"] == 1
         assert np.max(np.abs(V1_64.cpu().numpy() - Vs)) <= 5e-7 + 1e-9
         m.close()
+    b.close()
+
+
+def test_refinement_rounds_skip_certified_instances():
+    """The FP32 loop stopped after a few sweeps leaves policies far from optimal, so the
+    refinement runs several policy-improvement rounds and the instances certify in
+    different rounds (stats "rounds"); later rounds skip the instances already certified.
+    Every instance must still end at the oracle's optimum, each certified instance's values
+    staying as its certifying round left them."""
+    native = native_or_skip()
+    ps = _small_instances()
+    b = native.Batch(ps)
+    V, V64, pi, stats, rc = b.value_iterate(tol=1e-6, max_sweeps=8, accurate=True, raise_on_nonconvergence=False)
+    assert rc == native.VC_OK
+    rounds = [s["rounds"] for s in stats]
+    assert min(rounds) >= 1 and max(rounds) > min(rounds), rounds  # some instances were skipped
+    V64, pi = V64.cpu().numpy(), pi.cpu().numpy()
+    off = b.offsets
+    for i, p in enumerate(ps):
+        sl = slice(off[i], off[i + 1])
+        g = p["gamma"]
+        assert stats[i]["certified"] == 1 and stats[i]["termination"] == 2
+        assert stats[i]["residual64"] < 1e-6 * (1 - g) / (2 * g)
+        Vs, pis, gaps, _ = oracle.solve(p, tol=1e-12)
+        assert np.max(np.abs(V64[sl] - Vs)) <= 5e-7 + 1e-9, i
+        bad, _ = policy_mismatches(pi[sl], pis, gaps)
+        assert bad == 0, i
+    # FP32-only solves report no refinement round
+    _, _, _, st32, _ = b.value_iterate(tol=1e-6, fp32_only=True)
+    assert all(s["rounds"] == 0 for s in st32)
     b.close()
 
 
