@@ -565,9 +565,7 @@ struct SellRingArgs {
     int TS;           // slices per tile (the last tile may hold fewer)
     int64_t ntiles;
     int ring;         // bytes of the tile ring
-    int qfloats;      // unused (Q values live in the tiles' R rows)
-    int qoff;         // unused
-    int roff;         // byte offset of the ring
+    int roff;         // byte offset of the ring (Q values live in the tiles' own R rows)
 };
 
 // MB = 1: up to 800 threads (24 consumer warps), 80 registers; MB = 2: two CTAs of up to
@@ -832,12 +830,11 @@ int sell_plans(Mdp* m, cudaStream_t st, std::vector<CsrPlan>& out) {
             const int threads = (nrw + 1) * 32;
             if (threads > fa.maxThreadsPerBlock || (long long)threads * fa.numRegs * ctas > 65536) continue;
             if (nrw > (kSlots - 2) * TS * A) continue;  // claimed blocks stay within kSlots tiles
-            const int qoff = kHead;
-            const int qbytes = 0;  // Q values live in the tile's R rows
+            // the ring follows the header; Q values live in the tiles' own R rows
             const int budget = std::min(dyn_max, (smem_sm - 1024 * ctas) / ctas - (int)fa.sharedSizeBytes);
-            const int ring = ((budget - qoff - qbytes) / 128) * 128;
+            const int ring = ((budget - kHead) / 128) * 128;
             if (ring < max_tile + 128) continue;
-            const int need = qoff + qbytes + ring;
+            const int need = kHead + ring;
             int per_sm = 0;
             int per_sm_sl = 0;
             VC_CUDA(cached_occupancy(fn, threads, (size_t)need, &per_sm));
@@ -882,8 +879,6 @@ int sell_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* qg
         t.TS = m->plan.ts;
         t.ntiles = m->plan.ntiles;
         t.ring = (int)m->plan.cap;
-        t.qfloats = 0;
-        t.qoff = kHead;
         t.roff = kHead;
         const long long cap = (long long)m->num_sms * m->plan.ctas_per_sm;
         const unsigned grid = (unsigned)(t.ntiles < cap ? t.ntiles : cap);
