@@ -32,22 +32,13 @@ int state_grid(const Mdp* m) {
 }
 
 // ------------------------------------------------------------------ model arithmetic
-// E[V(next) | x] = V(x) + sum_e p_e (V(y_e) - V(x)): the self-loop probability is never
-// formed, so rounding scales with value differences, not with |V|.
+// E[V(next) | x] = V(x) + sum_e p_e (V(y_e) - V(x)) from the gathered values (vx = V(x),
+// v1 / v0 the completion / departure targets of each host, va the arrival, vf the phase
+// flip): the self-loop probability is never formed, so rounding scales with value
+// differences, not with |V|.  The sum runs in a fixed order.
 template <int MH, typename T>
-__device__ __forceinline__ T expect_next(const Model& md, const Coef<T>& c, const T* __restrict__ V, int x,
-                                         const Digits& d) {
-    // every gather first (independent loads in flight together), then the sum in a fixed order
-    const T vx = V[x];
-    T v1[MH], v0[MH];
-#pragma unroll
-    for (int k = 0; k < MH; k++) {
-        const int o = d.occ[k];
-        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : T(0);
-        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : T(0);
-    }
-    const T va = (d.q < md.Q) ? V[x + 2] : T(0);
-    const T vf = V[d.ph ? x - 1 : x + 1];
+__device__ __forceinline__ T expect_from(const Model& md, const Coef<T>& c, const Digits& d, T vx, const T* v1,
+                                         const T* v0, T va, T vf) {
     T acc = T(0);
 #pragma unroll
     for (int k = 0; k < MH; k++) {
@@ -65,6 +56,23 @@ __device__ __forceinline__ T expect_next(const Model& md, const Coef<T>& c, cons
     if (d.q < md.Q) acc += c.pa * (va - vx);
     acc += (d.ph ? c.pf1 : c.pf0) * (vf - vx);
     return vx + acc;
+}
+
+template <int MH, typename T>
+__device__ __forceinline__ T expect_next(const Model& md, const Coef<T>& c, const T* __restrict__ V, int x,
+                                         const Digits& d) {
+    // every gather first (independent loads in flight together), then the sum
+    const T vx = V[x];
+    T v1[MH], v0[MH];
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        const int o = d.occ[k];
+        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : T(0);
+        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : T(0);
+    }
+    const T va = (d.q < md.Q) ? V[x + 2] : T(0);
+    const T vf = V[d.ph ? x - 1 : x + 1];
+    return expect_from<MH, T>(md, c, d, vx, v1, v0, va, vf);
 }
 
 #ifdef VC_DEBUG_BOUNDS
@@ -101,18 +109,10 @@ __device__ __forceinline__ T post_reward(const Model& md, const Coef<T>& c, cons
 // own: in the single-instance pass 1 this form, next to the plain expect_next, timed
 // faster (93 against 108 us per sweep of the 2.5 M-state instance) than the fused one,
 // which the batched pass uses.
+// (the same from gathered values, as expect_from)
 template <int MH>
-__device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<float>& c, const float* __restrict__ V,
-                                                 int x, const Digits& d, float rx) {
-    float v1[MH], v0[MH];
-#pragma unroll
-    for (int k = 0; k < MH; k++) {
-        const int o = d.occ[k];
-        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : 0.0f;
-        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : 0.0f;
-    }
-    const float va = (d.q < md.Q) ? V[x + 2] : 0.0f;
-    const float vf = V[d.ph ? x - 1 : x + 1];
+__device__ __forceinline__ float defer_from(const Model& md, const Coef<float>& c, const Digits& d, const float* v1,
+                                           const float* v0, float va, float vf, float rx) {
     float sm = 0.0f, pm = 0.0f;
 #pragma unroll
     for (int k = 0; k < MH; k++) {
@@ -141,6 +141,21 @@ __device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<flo
     return __fdiv_rn(fmaf(c.gamma, sm, rx), fmaf(c.gamma, pm, 1.0f - c.gamma));
 }
 
+template <int MH>
+__device__ __forceinline__ float defer_self_loop(const Model& md, const Coef<float>& c, const float* __restrict__ V,
+                                                 int x, const Digits& d, float rx) {
+    float v1[MH], v0[MH];
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        const int o = d.occ[k];
+        v1[k] = (k < md.H && o > 0) ? V[x - md.stride[k]] : 0.0f;
+        v0[k] = (k < md.H && o > 1) ? V[x - o * md.stride[k]] : 0.0f;
+    }
+    const float va = (d.q < md.Q) ? V[x + 2] : 0.0f;
+    const float vf = V[d.ph ? x - 1 : x + 1];
+    return defer_from<MH>(md, c, d, v1, v0, va, vf, rx);
+}
+
 // ---------------------------------------------------------------- implicit: pass 1
 // SL (FP32 only): also U2(x) = defer's backup with the self-transition solved.
 template <int MH, typename T, bool SL>
@@ -157,6 +172,54 @@ __global__ void __launch_bounds__(kThreads) k_post(Model md, Coef<T> c, const T*
         const T rx = post_reward<MH>(md, c, d);
         U[x] = rx + c.gamma * expect_next<MH>(md, c, V, x, d);
         if constexpr (SL) U2[x] = defer_self_loop<MH>(md, c, V, x, d, rx);
+    }
+}
+
+// FP32 pass 1 over pairs of states: x (even, channel phase 0) and x + 1 (phase 1) share
+// their digits and their reward (the phase does not enter it), and every value the two
+// read comes in 8-byte-aligned pairs (the strides are even): V(x - o s_k) and
+// V(x + 1 - o s_k) are adjacent, and each state's phase flip reads the other's V.  One
+// decode, one reward and half the loads and stores per state; each state's arithmetic is
+// expect_from's (and defer_from's), so U and W are those of k_post bit for bit.
+template <int MH, bool SL>
+__global__ void __launch_bounds__(kThreads) k_post_pair(Model md, Coef<float> c, const float* __restrict__ V,
+                                                        float* __restrict__ U, float* __restrict__ U2, SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const int npairs = md.S >> 1;  // S = 2 (Q + 1) (C + 1)^H is even
+    for (int t = blockIdx.x * kThreads + threadIdx.x; t < npairs; t += gridDim.x * kThreads) {
+        const int x = 2 * t;
+        Digits d0;
+        decode<MH>(md, x, d0);  // phase 0
+        Digits d1 = d0;
+        d1.ph = 1;
+#ifdef VC_DEBUG_BOUNDS
+        if (!successors_in_range<MH>(md, x, d0, sc.ctl) || !successors_in_range<MH>(md, x + 1, d1, sc.ctl)) continue;
+#endif
+        const float rx = post_reward<MH>(md, c, d0);
+        const float2 vx = *reinterpret_cast<const float2*>(V + x);
+        float v1a[MH], v1b[MH], v0a[MH], v0b[MH];
+#pragma unroll
+        for (int k = 0; k < MH; k++) {
+            const int o = d0.occ[k];
+            const float2 p1 = (k < md.H && o > 0) ? *reinterpret_cast<const float2*>(V + x - md.stride[k])
+                                                  : make_float2(0.0f, 0.0f);
+            const float2 p0 = (k < md.H && o > 1) ? *reinterpret_cast<const float2*>(V + x - o * md.stride[k])
+                                                  : make_float2(0.0f, 0.0f);
+            v1a[k] = p1.x;
+            v1b[k] = p1.y;
+            v0a[k] = p0.x;
+            v0b[k] = p0.y;
+        }
+        const float2 va = (d0.q < md.Q) ? *reinterpret_cast<const float2*>(V + x + 2) : make_float2(0.0f, 0.0f);
+        // the phase flip of x lands on x + 1, that of x + 1 on x
+        const float e0 = expect_from<MH, float>(md, c, d0, vx.x, v1a, v0a, va.x, vx.y);
+        const float e1 = expect_from<MH, float>(md, c, d1, vx.y, v1b, v0b, va.y, vx.x);
+        *reinterpret_cast<float2*>(U + x) = make_float2(rx + c.gamma * e0, rx + c.gamma * e1);
+        if constexpr (SL) {
+            const float w0 = defer_from<MH>(md, c, d0, v1a, v0a, va.x, vx.y, rx);
+            const float w1 = defer_from<MH>(md, c, d1, v1b, v0b, va.y, vx.x, rx);
+            *reinterpret_cast<float2*>(U2 + x) = make_float2(w0, w1);
+        }
     }
 }
 
@@ -469,7 +532,7 @@ static int launch_block(Mdp* m, const float* V_in, float* V_out, SweepCtl sc, cu
             m->blk_grid = std::max(1, per_sm) * (m->num_sms > 0 ? m->num_sms : 148);
         }
         const int ntiles = (m->S + T - 1) / T;
-        k_post<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
+        k_post_pair<MH, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
         kern<<<std::min(ntiles, m->blk_grid), threads, smem, st>>>(m->md, m->c32, T, m->blk_passes, V_in, m->U32,
                                                                    m->U32s, V_out, sc);
         VC_CUDA(cudaGetLastError());
@@ -491,10 +554,10 @@ int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* 
     by_h(m, [&](auto mh) {
         constexpr int MH = decltype(mh)::value;
         if (sc.self_loop) {
-            k_post<MH, float, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
+            k_post_pair<MH, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
             k_max2<MH, true><<<g, kThreads, 0, st>>>(m->md, m->U32, m->U32s, V_in, V_out, pi, qgap, sc);
         } else {
-            k_post<MH, float, false><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, nullptr, sc1);
+            k_post_pair<MH, false><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, nullptr, sc1);
             k_max2<MH, false><<<g, kThreads, 0, st>>>(m->md, m->U32, nullptr, V_in, V_out, pi, qgap, sc);
         }
         return 0;
