@@ -370,6 +370,83 @@ __global__ void __launch_bounds__(kThreads) k_max2(Model md, const float* __rest
     finish_block<float>(sc, res, vabs, sweep);
 }
 
+// Max over actions in order, lowest index on ties, for one state: its placements uk[] and
+// defer's value u (the highest index).
+template <int MH>
+__device__ __forceinline__ void max_actions(const Model& md, const float* uk, float u, float& best, float& second,
+                                            int& arg) {
+    best = -INFINITY;
+    second = -INFINITY;
+    arg = md.H;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (uk[k] > best) {
+            second = best;
+            best = uk[k];
+            arg = k;
+        } else if (uk[k] > second) {
+            second = uk[k];
+        }
+    }
+    if (u > best) {
+        second = best;
+        best = u;
+        arg = md.H;
+    } else if (u > second) {
+        second = u;
+    }
+}
+
+// Pass 2 over pairs of states s (even, channel phase 0) and s + 1 (phase 1): one decode,
+// and one 8-byte load per action serves both, since their post-decision states of a
+// placement are adjacent (s + s_k - 2 is even) and every placement feasible in phase 0
+// (the RSU) is feasible in phase 1; outputs are written as pairs.  Each state's maximum,
+// argmax and gap are k_max2's.
+template <int MH, bool SL>
+__global__ void __launch_bounds__(kThreads) k_max_pair(Model md, const float* __restrict__ U,
+                                                       const float* __restrict__ U2, const float* __restrict__ V_in,
+                                                       float* __restrict__ V_out, int32_t* __restrict__ pi,
+                                                       float* __restrict__ qgap, SweepCtl sc) {
+    if (loop_done(sc)) return;
+    const long long sweep = loop_sweep(sc);
+    float res = 0.0f, vabs = 0.0f;
+    const int npairs = md.S >> 1;
+    for (int t = blockIdx.x * kThreads + threadIdx.x; t < npairs; t += gridDim.x * kThreads) {
+        const int s = 2 * t;
+        Digits d;
+        decode<MH>(md, s, d);  // phase 0; s + 1 has the same queue and occupancies
+        float uk0[MH], uk1[MH];
+#pragma unroll
+        for (int k = 0; k < MH; k++) {
+            // phase 1: every host with a free slot; phase 0: the RSU (host H - 1) only
+            const bool f1 = d.q >= 1 && k < md.H && d.occ[k] < md.C &&
+                            VC_IN_BOUNDS(sc.ctl, s + md.stride[k] - 2 >= 0 && s + md.stride[k] - 1 < md.S);
+            const bool f0 = f1 && k == md.H - 1;
+            const float2 u2 = f1 ? *reinterpret_cast<const float2*>(U + s + md.stride[k] - 2)
+                                 : make_float2(-INFINITY, -INFINITY);
+            uk0[k] = f0 ? u2.x : -INFINITY;
+            uk1[k] = f1 ? u2.y : -INFINITY;
+        }
+        const float2 ud = *reinterpret_cast<const float2*>((SL ? U2 : U) + s);
+        const float2 vin = *reinterpret_cast<const float2*>(V_in + s);
+        float b0, c0, b1, c1;
+        int a0, a1;
+        max_actions<MH>(md, uk0, ud.x, b0, c0, a0);
+        max_actions<MH>(md, uk1, ud.y, b1, c1, a1);
+        if (V_out) *reinterpret_cast<float2*>(V_out + s) = make_float2(b0, b1);
+        if (pi) *reinterpret_cast<int2*>(pi + s) = make_int2(a0, a1);
+        if (qgap)
+            *reinterpret_cast<float2*>(qgap + s) =
+                make_float2(c0 == -INFINITY ? INFINITY : b0 - c0, c1 == -INFINITY ? INFINITY : b1 - c1);
+        res = fmaxf(res, fmaxf(fabsf(b0 - vin.x), fabsf(b1 - vin.y)));
+        vabs = fmaxf(vabs, fmaxf(fabsf(b0), fabsf(b1)));
+    }
+    if (sc.mode == kModeNone) return;
+    res = block_max<float, kThreads>(res);
+    vabs = block_max<float, kThreads>(vabs);
+    finish_block<float>(sc, res, vabs, sweep);
+}
+
 // ------------------------------------------------ implicit: mixed-precision refinement
 // Policy residual in FP64, r(s) = U64(x_pi(s)) - V64(s) with U64 = R + gamma E[V64(next) | x]
 // from the FP64 pass-1 kernel over every post-decision state (coalesced: thread x gathers
@@ -555,10 +632,10 @@ int launch_sweep32(Mdp* m, const float* V_in, float* V_out, int32_t* pi, float* 
         constexpr int MH = decltype(mh)::value;
         if (sc.self_loop) {
             k_post_pair<MH, true><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, m->U32s, sc1);
-            k_max2<MH, true><<<g, kThreads, 0, st>>>(m->md, m->U32, m->U32s, V_in, V_out, pi, qgap, sc);
+            k_max_pair<MH, true><<<g, kThreads, 0, st>>>(m->md, m->U32, m->U32s, V_in, V_out, pi, qgap, sc);
         } else {
             k_post_pair<MH, false><<<g, kThreads, 0, st>>>(m->md, m->c32, V_in, m->U32, nullptr, sc1);
-            k_max2<MH, false><<<g, kThreads, 0, st>>>(m->md, m->U32, nullptr, V_in, V_out, pi, qgap, sc);
+            k_max_pair<MH, false><<<g, kThreads, 0, st>>>(m->md, m->U32, nullptr, V_in, V_out, pi, qgap, sc);
         }
         return 0;
     });
