@@ -796,9 +796,9 @@ def captured_traffic(args, info):
 # attached to that variant while the kernel source hashes as captured: the sweep is bound
 # by gather latency and issue, not by a memory roof (its HBM fraction is low by design).
 IMPLICIT_SOL_SOURCES = ("vc_sweep.cu",)
-IMPLICIT_SOL_SHA = "f324856119c49673ce32afa3295c8a33c64c2c145e207c721af00250beded105"
-IMPLICIT_SOL = {"kernels": "k_post<7, float, 0> / k_max2<7, 0>", "sm_pct": [58.2, 44.5],
-                "l2_pct": [10.5, 9.8], "dram_pct": [3.9, 8.7], "warps_active_pct": [56.2, 56.6],
+IMPLICIT_SOL_SHA = "79e3021f39c95e9a34dc40bbf3e7c264ba4567f09c922b7da7e06a346d0060c7"
+IMPLICIT_SOL = {"kernels": "k_post_pair<7, 0> / k_max_pair<7, 0>", "sm_pct": [55.0, 43.0],
+                "l2_pct": [14.7, 9.7], "dram_pct": [5.8, 9.1], "warps_active_pct": [49.6, 55.5],
                 "top_stall": ["not selected (issue-bound)", "long scoreboard (U gathers)"],
                 "bound": "instruction issue (pass 1) and gather latency (pass 2)"}
 
