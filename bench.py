@@ -766,9 +766,9 @@ TRAFFIC_BYTES = {("large", "csr_f32", True, True): 1_196_185_088,
 # by gather latency at half occupancy, not by a memory roof, and these say how far each
 # unit is from its own peak.
 BATCH_SOL_SOURCES = ("vc_batch.cu", "vc_internal.cuh")
-BATCH_SOL_SHA = "00f9c86d7f00da542f965a4a622785515a4be1a3b1009dec864de6221cfa3aea"
-BATCH_SOL = {"kernel": "k_bpost<5, float, false>", "dram_pct": 8.0, "l2_pct": 10.7, "sm_pct": 55.7,
-             "warps_active_pct": 46.6, "registers_per_thread": 63, "top_stall": "long scoreboard (V gathers)"}
+BATCH_SOL_SHA = "e67621a040703bc539f2e76a5369e75f8b8b8f6eb229700aff8d1bdc6019604b"
+BATCH_SOL = {"kernel": "k_bpost_pair<5>", "dram_pct": 11.5, "l2_pct": 13.1, "sm_pct": 57.5,
+             "warps_active_pct": 34.6, "registers_per_thread": 80, "top_stall": "long scoreboard (V gathers)"}
 
 
 def _sources_sha(names):

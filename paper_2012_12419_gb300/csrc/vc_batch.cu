@@ -220,6 +220,147 @@ __global__ void k_bpost(const InstDesc* __restrict__ descs, const BatchTile* __r
     }
 }
 
+// b_expect from gathered values (vx = V(x), v1 / v0 the completion / departure targets,
+// va the arrival, vf the phase flip), the same operations in the same order.
+template <int MH>
+__device__ __forceinline__ float b_expect_from(const Model& md, const Coef<float>& c, const Digits& d, float vx,
+                                               const float* v1, const float* v0, float va, float vf) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o > 0) {
+                if (o == 1) {
+                    acc += (c.pc[k] + c.pd[k]) * (v1[k] - vx);
+                } else {
+                    acc += c.pc[k] * float(o) * (v1[k] - vx) + c.pd[k] * (v0[k] - vx);
+                }
+            }
+        }
+    }
+    if (d.q < md.Q) acc += c.pa * (va - vx);
+    acc += (d.ph ? c.pf1 : c.pf0) * (vf - vx);
+    return vx + acc;
+}
+
+// Pass 1 of Eq. 18's FP32 loop over pairs of states x (even, channel phase 0) and x + 1
+// (phase 1), which share their digits and their reward; every value they read comes in
+// 8-byte-aligned pairs (tile starts, tile lengths, instance sizes and offsets are even, and
+// so are the strides).  One decode, one reward, paired loads and stores; each state's
+// value is k_bpost's bit for bit.
+template <int MH>
+__global__ void __launch_bounds__(kThreads, 3) k_bpost_pair(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                             const int* __restrict__ done, const float* __restrict__ V, float* __restrict__ U) {
+    __shared__ InstDesc sd;
+    __shared__ int skip;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x == 0) skip = done ? (*((volatile int*)&done[tl.inst]) != 0) : 0;
+        __syncthreads();
+        if (!skip) {
+            load_desc(descs, tl.inst, sd);
+            __syncthreads();
+            const float* Vi = V + sd.off;
+            float* Ui = U + sd.off;
+            const Coef<float>& c = sd.c32;
+            for (int jj = threadIdx.x; 2 * jj < tl.count; jj += blockDim.x) {
+                const int x = tl.start + 2 * jj;  // even, and x + 1 < start + count (even tiles)
+                Digits d0;
+                decode<MH>(sd.md, x, d0);
+                Digits d1 = d0;
+                d1.ph = 1;
+                const float rx = b_reward<MH>(sd.md, c, d0);  // the phase does not enter the reward
+                const float2 vx = *reinterpret_cast<const float2*>(Vi + x);
+                float v1a[MH], v1b[MH], v0a[MH], v0b[MH];
+#pragma unroll
+                for (int k = 0; k < MH; k++) {
+                    const int o = d0.occ[k];
+                    const float2 p1 = (k < sd.md.H && o > 0)
+                                          ? *reinterpret_cast<const float2*>(Vi + x - sd.md.stride[k])
+                                          : make_float2(0.0f, 0.0f);
+                    const float2 p0 = (k < sd.md.H && o > 1)
+                                          ? *reinterpret_cast<const float2*>(Vi + x - o * sd.md.stride[k])
+                                          : make_float2(0.0f, 0.0f);
+                    v1a[k] = p1.x;
+                    v1b[k] = p1.y;
+                    v0a[k] = p0.x;
+                    v0b[k] = p0.y;
+                }
+                const float2 va = (d0.q < sd.md.Q) ? *reinterpret_cast<const float2*>(Vi + x + 2)
+                                                   : make_float2(0.0f, 0.0f);
+                // the phase flip of x lands on x + 1, that of x + 1 on x
+                const float e0 = b_expect_from<MH>(sd.md, c, d0, vx.x, v1a, v0a, va.x, vx.y);
+                const float e1 = b_expect_from<MH>(sd.md, c, d1, vx.y, v1b, v0b, va.y, vx.x);
+                *reinterpret_cast<float2*>(Ui + x) = make_float2(rx + c.gamma * e0, rx + c.gamma * e1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pass 2 of Eq. 18's FP32 loop over the same pairs: one decode, one 8-byte load per action
+// for both states (phase 0's feasible placements are a subset of phase 1's), paired
+// stores; each state's maximum is k_bmax's, and a tile's residual closes the instance as
+// there.
+template <int MH>
+__global__ void k_bmax_pair(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
+                            BatchCtl c, int parity, const float* __restrict__ U, const float* __restrict__ V_in,
+                            float* __restrict__ V_out) {
+    __shared__ InstDesc sd;
+    __shared__ int skip;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const BatchTile tl = tiles[t];
+        if (threadIdx.x == 0) skip = (*((volatile int*)&c.done[tl.inst]) != 0);
+        __syncthreads();
+        if (skip) {
+            __syncthreads();
+            continue;
+        }
+        load_desc(descs, tl.inst, sd);
+        __syncthreads();
+        const float* Ui = U + sd.off;
+        const float* Vi = V_in + sd.off;
+        float* Vo = V_out + sd.off;
+        float res = 0.0f, vabs = 0.0f;
+        for (int jj = threadIdx.x; 2 * jj < tl.count; jj += blockDim.x) {
+            const int s = tl.start + 2 * jj;  // even, and s + 1 < start + count (even tiles)
+            Digits d;
+            decode<MH>(sd.md, s, d);
+            float uk0[MH], uk1[MH];
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                // s + 1 (phase 1): every host with a free slot; s (phase 0): the RSU only
+                const bool f1 = d.q >= 1 && k < sd.md.H && d.occ[k] < sd.md.C;
+                const bool f0 = f1 && k == sd.md.H - 1;
+                const float2 u2 = f1 ? *reinterpret_cast<const float2*>(Ui + s + sd.md.stride[k] - 2)
+                                     : make_float2(-INFINITY, -INFINITY);
+                uk0[k] = f0 ? u2.x : -INFINITY;
+                uk1[k] = f1 ? u2.y : -INFINITY;
+            }
+            const float2 ud = *reinterpret_cast<const float2*>(Ui + s);
+            const float2 vin = *reinterpret_cast<const float2*>(Vi + s);
+            float b0 = -INFINITY, b1 = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < MH; k++) {
+                if (uk0[k] > b0) b0 = uk0[k];
+                if (uk1[k] > b1) b1 = uk1[k];
+            }
+            if (ud.x > b0) b0 = ud.x;
+            if (ud.y > b1) b1 = ud.y;
+            *reinterpret_cast<float2*>(Vo + s) = make_float2(b0, b1);
+            res = fmax(res, fabs(b0 - vin.x));
+            res = fmax(res, fabs(b1 - vin.y));
+            vabs = fmax(vabs, fabs(b0));
+            vabs = fmax(vabs, fabs(b1));
+        }
+        res = block_max<float, kThreads>(res);
+        vabs = block_max<float, kThreads>(vabs);
+        if (threadIdx.x == 0) close_instance(c, tl.inst, res, vabs, parity, parity ^ 1);
+        __syncthreads();
+    }
+}
+
 // Pass 2: V'(s) = max_a U(x_a(s)); per-instance residual and close (loop mode, ctl given),
 // or plain extraction with policy / FP64 certificate residual into res64 (ctl null).  SL:
 // defer takes U2(s) (its backup with the self-transition solve).  Outside loop mode,
@@ -854,6 +995,7 @@ struct Batch {
     unsigned int* kr_ticket = nullptr;
     long long* kr_max_d = nullptr;
     // in-block iteration (VC_ITER_BLOCK): tiles of whole blocks of at most blk_threads states
+    bool pairs = false;  // every tile of d_tiles starts and ends on an even state (paired loop kernels)
     int blk_threads = 512;
     int blk_passes = 4;
     int blk_grid = 0;
@@ -992,6 +1134,10 @@ static int build_tiles(Batch* b, cudaStream_t st) {
         }
     }
     b->ntiles = (int)tiles.size();
+    // the paired loop kernels need every tile to start and end on an even state (tile sizes
+    // and instance sizes 2(Q+1)(C+1)^H are even; checked rather than assumed)
+    b->pairs = true;
+    for (const BatchTile& t : tiles) b->pairs = b->pairs && (t.start % 2 == 0) && (t.count % 2 == 0);
     std::vector<int> first(b->n, 0);
     for (int i = 1; i < b->n; i++) first[i] = first[i - 1] + b->h_tiles_of[i - 1];
     if (b->d_tiles) cudaFree(b->d_tiles);
@@ -1115,6 +1261,13 @@ static int join_small(Batch* b, cudaStream_t st) {
 
 // Kernels in one pass of each loop body (two sweeps per pass); the launch counter adds
 // passes x this after every graph launch, since the graph runs them without a host call.
+// The paired loop kernels serve batches whose tiles are all even and whose largest H is
+// at most 5 (above it pass 1's pair of states no longer fits its register budget).
+template <int MH>
+static bool pairs_ok(const Batch* b) {
+    return b->pairs && MH <= 5;
+}
+
 constexpr int kViBodyKernels = 5;
 constexpr int kCorrBodyKernels = 3;
 constexpr int kKryBodyKernels = 6;      // one BiCGSTAB iteration per pass
@@ -1123,6 +1276,15 @@ constexpr long long kKrylovMaxIter = 1000;
 template <int MH, bool SL>
 static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
     const BatchCtl c = ctl_of(b);
+    if (!SL && pairs_ok<MH>(b)) {
+        // Eq. 18's loop over pairs of states (every tile starts and ends on an even state)
+        k_bpost_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U);
+        k_bmax_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 0, b->U, b->Va, b->Vb);
+        k_bpost_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U);
+        k_bmax_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, b->U, b->Vb, b->Va);
+        k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
+        return;
+    }
     float* U2 = SL ? b->U2 : nullptr;
     k_bpost<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U, U2);
     k_bmax<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 0, b->U, U2, b->Va,
@@ -1295,8 +1457,11 @@ static int reset_loop(Batch* b, double tol, long long max_sweeps, cudaStream_t s
 
 template <int MH>
 static void enqueue_extract(Batch* b, const float* V, int32_t* pi, cudaStream_t st) {
-    k_bpost<MH, float, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U,
-                                                            nullptr);
+    if (pairs_ok<MH>(b))
+        k_bpost_pair<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U);
+    else
+        k_bpost<MH, float, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U,
+                                                                nullptr);
     k_bmax<MH, float, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, ctl_of(b), 0, 0, b->U,
                                                            nullptr, V, nullptr, pi, nullptr);
 }
