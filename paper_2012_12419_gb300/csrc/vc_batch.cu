@@ -244,14 +244,56 @@ __device__ __forceinline__ float b_expect_from(const Model& md, const Coef<float
     return vx + acc;
 }
 
+// post_and_defer from gathered values: U and W of one post-decision state, the same
+// operations in the same order (the self-transition loop's pass 1).
+template <int MH>
+__device__ __forceinline__ void b_post_defer_from(const Model& md, const Coef<float>& c, const Digits& d, float vx,
+                                                  const float* v1, const float* v0, float va, float vf, float rx,
+                                                  float& U, float& W) {
+    float acc = 0.0f, sm = 0.0f, pm = 0.0f;
+#pragma unroll
+    for (int k = 0; k < MH; k++) {
+        if (k < md.H) {
+            const int o = d.occ[k];
+            if (o == 1) {
+                const float p = c.pc[k] + c.pd[k];
+                acc += p * (v1[k] - vx);
+                sm = fmaf(p, v1[k], sm);
+                pm += p;
+            } else if (o > 1) {
+                const float p1 = c.pc[k] * (float)o;
+                acc += p1 * (v1[k] - vx) + c.pd[k] * (v0[k] - vx);
+                sm = fmaf(p1, v1[k], sm);
+                sm = fmaf(c.pd[k], v0[k], sm);
+                pm += p1;
+                pm += c.pd[k];
+            }
+        }
+    }
+    if (d.q < md.Q) {
+        acc += c.pa * (va - vx);
+        sm = fmaf(c.pa, va, sm);
+        pm += c.pa;
+    }
+    const float pf = d.ph ? c.pf1 : c.pf0;
+    acc += pf * (vf - vx);
+    sm = fmaf(pf, vf, sm);
+    pm += pf;
+    U = rx + c.gamma * (vx + acc);
+    W = __fdiv_rn(fmaf(c.gamma, sm, rx), fmaf(c.gamma, pm, 1.0f - c.gamma));
+}
+
 // Pass 1 of Eq. 18's FP32 loop over pairs of states x (even, channel phase 0) and x + 1
 // (phase 1), which share their digits and their reward; every value they read comes in
 // 8-byte-aligned pairs (tile starts, tile lengths, instance sizes and offsets are even, and
 // so are the strides).  One decode, one reward, paired loads and stores; each state's
 // value is k_bpost's bit for bit.
-template <int MH>
+// SL: the self-transition loop's pass 1, U and W (defer's value with its self-transition
+// solved) of both states, as post_and_defer computes them.
+template <int MH, bool SL>
 __global__ void __launch_bounds__(kThreads, 3) k_bpost_pair(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
-                             const int* __restrict__ done, const float* __restrict__ V, float* __restrict__ U) {
+                             const int* __restrict__ done, const float* __restrict__ V, float* __restrict__ U,
+                             float* __restrict__ U2) {
     __shared__ InstDesc sd;
     __shared__ int skip;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -290,9 +332,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_bpost_pair(const InstDesc* __re
                 const float2 va = (d0.q < sd.md.Q) ? *reinterpret_cast<const float2*>(Vi + x + 2)
                                                    : make_float2(0.0f, 0.0f);
                 // the phase flip of x lands on x + 1, that of x + 1 on x
-                const float e0 = b_expect_from<MH>(sd.md, c, d0, vx.x, v1a, v0a, va.x, vx.y);
-                const float e1 = b_expect_from<MH>(sd.md, c, d1, vx.y, v1b, v0b, va.y, vx.x);
-                *reinterpret_cast<float2*>(Ui + x) = make_float2(rx + c.gamma * e0, rx + c.gamma * e1);
+                if constexpr (SL) {
+                    float u0, w0, u1, w1;
+                    b_post_defer_from<MH>(sd.md, c, d0, vx.x, v1a, v0a, va.x, vx.y, rx, u0, w0);
+                    b_post_defer_from<MH>(sd.md, c, d1, vx.y, v1b, v0b, va.y, vx.x, rx, u1, w1);
+                    *reinterpret_cast<float2*>(Ui + x) = make_float2(u0, u1);
+                    *reinterpret_cast<float2*>(U2 + sd.off + x) = make_float2(w0, w1);
+                } else {
+                    const float e0 = b_expect_from<MH>(sd.md, c, d0, vx.x, v1a, v0a, va.x, vx.y);
+                    const float e1 = b_expect_from<MH>(sd.md, c, d1, vx.y, v1b, v0b, va.y, vx.x);
+                    *reinterpret_cast<float2*>(Ui + x) = make_float2(rx + c.gamma * e0, rx + c.gamma * e1);
+                }
             }
         }
         __syncthreads();
@@ -303,10 +353,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_bpost_pair(const InstDesc* __re
 // for both states (phase 0's feasible placements are a subset of phase 1's), paired
 // stores; each state's maximum is k_bmax's, and a tile's residual closes the instance as
 // there.
-template <int MH>
+// SL: defer takes U2 (its value with the self-transition solved), as in k_bmax.
+template <int MH, bool SL>
 __global__ void k_bmax_pair(const InstDesc* __restrict__ descs, const BatchTile* __restrict__ tiles, int ntiles,
-                            BatchCtl c, int parity, const float* __restrict__ U, const float* __restrict__ V_in,
-                            float* __restrict__ V_out) {
+                            BatchCtl c, int parity, const float* __restrict__ U, const float* __restrict__ U2,
+                            const float* __restrict__ V_in, float* __restrict__ V_out) {
     __shared__ InstDesc sd;
     __shared__ int skip;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -338,7 +389,7 @@ __global__ void k_bmax_pair(const InstDesc* __restrict__ descs, const BatchTile*
                 uk0[k] = f0 ? u2.x : -INFINITY;
                 uk1[k] = f1 ? u2.y : -INFINITY;
             }
-            const float2 ud = *reinterpret_cast<const float2*>(Ui + s);
+            const float2 ud = *reinterpret_cast<const float2*>(SL ? U2 + sd.off + s : Ui + s);
             const float2 vin = *reinterpret_cast<const float2*>(Vi + s);
             float b0 = -INFINITY, b1 = -INFINITY;
 #pragma unroll
@@ -1276,16 +1327,18 @@ constexpr long long kKrylovMaxIter = 1000;
 template <int MH, bool SL>
 static void enqueue_vi_body(Batch* b, cudaStream_t cs, cudaGraphConditionalHandle h) {
     const BatchCtl c = ctl_of(b);
-    if (!SL && pairs_ok<MH>(b)) {
-        // Eq. 18's loop over pairs of states (every tile starts and ends on an even state)
-        k_bpost_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U);
-        k_bmax_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 0, b->U, b->Va, b->Vb);
-        k_bpost_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U);
-        k_bmax_pair<MH><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, b->U, b->Vb, b->Va);
+    float* U2 = SL ? b->U2 : nullptr;
+    if (pairs_ok<MH>(b)) {
+        // the loop over pairs of states (every tile starts and ends on an even state)
+        k_bpost_pair<MH, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U, U2);
+        k_bmax_pair<MH, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 0, b->U, U2, b->Va,
+                                                          b->Vb);
+        k_bpost_pair<MH, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Vb, b->U, U2);
+        k_bmax_pair<MH, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, b->U, U2, b->Vb,
+                                                          b->Va);
         k_bcond<<<1, 1, 0, cs>>>(h, c, 2);
         return;
     }
-    float* U2 = SL ? b->U2 : nullptr;
     k_bpost<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, b->done, b->Va, b->U, U2);
     k_bmax<MH, float, SL><<<b->grid, kThreads, 0, cs>>>(b->d_desc, b->d_tiles, b->ntiles, c, 1, 0, b->U, U2, b->Va,
                                                          b->Vb, nullptr, nullptr);
@@ -1458,7 +1511,8 @@ static int reset_loop(Batch* b, double tol, long long max_sweeps, cudaStream_t s
 template <int MH>
 static void enqueue_extract(Batch* b, const float* V, int32_t* pi, cudaStream_t st) {
     if (pairs_ok<MH>(b))
-        k_bpost_pair<MH><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U);
+        k_bpost_pair<MH, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U,
+                                                              nullptr);
     else
         k_bpost<MH, float, false><<<b->grid, kThreads, 0, st>>>(b->d_desc, b->d_tiles, b->ntiles, nullptr, V, b->U,
                                                                 nullptr);
