@@ -329,8 +329,11 @@ int vc_block_iteration_info(const vc_mdp* m, int32_t* inner_hosts, int32_t* bloc
  * (4 MiB) plus a residual word and a 1.3 KB control block, present on every GPU that
  * loads the library until the process exits; S above 1,048,576 returns VC_ERR_ARG.  The
  * first call on each device looks up the arrays' device addresses (cudaGetSymbolAddress)
- * with that device current:
- * make that first call before any stream capture.  All calls on a device share the
+ * and the SM count with that device current: make that first call before any stream
+ * capture.  Later calls only enqueue kernels and an asynchronous memset on `stream`, so
+ * they may be captured into a CUDA graph (the bounds-checking build's read-back excepted);
+ * a replay reads V and writes V_out, pi and residual at the addresses captured.  All
+ * calls on a device share the
  * array, so calls that overlap on the GPU (different streams, or different host threads)
  * race and must be ordered by the caller.  The residual word is cleared on every call.
  * In the bounds-checking build (libvcmdp_debug.so) the call also synchronises `stream`

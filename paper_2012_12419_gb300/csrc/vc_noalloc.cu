@@ -22,14 +22,17 @@ static __device__ __align__(256) float g_noalloc_U[kNoAllocMaxStates];
 static __device__ __align__(256) unsigned int g_noalloc_res[64];
 static __device__ __align__(256) Ctl g_noalloc_ctl;
 
-// Device addresses of the static arrays, looked up once per device.  In host code the
-// array names are host-side stand-ins, never device addresses: only these pointers are
-// passed to kernels.
+// Device addresses of the static arrays and the SM count, looked up once per device by the
+// first call there.  A later call makes no CUDA call but launches, an asynchronous memset and
+// error queries, so it may run while the stream is being captured.  In host code the array
+// names are host-side stand-ins, never device addresses: only these pointers are passed to
+// kernels.
 struct NoAllocScratch {
     bool ready = false;
     float* U = nullptr;
     unsigned int* res = nullptr;
     Ctl* ctl = nullptr;
+    int num_sms = 0;
 };
 
 constexpr int kMaxDevices = 64;
@@ -50,6 +53,7 @@ static int noalloc_scratch(NoAllocScratch* out) {
         s.res = (unsigned int*)p;
         VC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_ctl));
         s.ctl = (Ctl*)p;
+        VC_CUDA(cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev));
         s.ready = true;
     }
     *out = s;
@@ -93,9 +97,7 @@ extern "C" int vc_bellman32_noalloc(const vc_params* p, const float* V, float* V
                                     std::to_string(kNoAllocMaxStates) + " states");
     NoAllocScratch sc;
     if ((rc = noalloc_scratch(&sc))) return rc;
-    int dev = 0;
-    VC_CUDA(cudaGetDevice(&dev));
-    VC_CUDA(cudaDeviceGetAttribute(&m.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    m.num_sms = sc.num_sms;
     m.U32 = sc.U;
     cudaStream_t st = (cudaStream_t)stream;
 #ifdef VC_DEBUG_BOUNDS

@@ -6,8 +6,9 @@ synchronisation, code running under another library's stream capture): it keeps 
 scratch in a static device array instead.  Through the C ABI, two calls in a row with
 different inputs must reproduce vc_bellman32 on a VC_IMPLICIT handle of the same model
 bitwise (same kernels, same arithmetic), return max|V_out - V| as the residual (+infinity
-when a difference is NaN), accept NULL for the optional outputs, and reject models larger
-than the static scratch.  This file is collected last so that a run stopping
+when a difference is NaN), accept NULL for the optional outputs, reject models larger
+than the static scratch, and, once called outside a capture, replay from a CUDA graph
+captured around a call.  This file is collected last so that a run stopping
 at the first failure has already run every other test.
 """
 import ctypes
@@ -98,3 +99,42 @@ def test_noalloc_rejects_models_beyond_its_scratch():
     assert _call(native, p, V, out, pi, res) == native.VC_ERR_ARG
     with pytest.raises(native.VcError):
         native.bellman32_noalloc(p, V, out, pi, res)
+
+
+def test_noalloc_call_replays_from_a_captured_graph():
+    """Stream capture by another library: after one call on the device (which looks up the
+    static scratch's addresses), a call captured into a CUDA graph replays as a plain call.
+    Each replay on new values in the captured V equals the handle sweep bitwise, policy
+    and residual included."""
+    native = native_or_skip()
+    import torch
+
+    p = inputs.workload("tiny")
+    m = native.MDP.build(p, fmt="implicit")
+    S = m.S
+    g = torch.Generator(device="cuda").manual_seed(11)
+    V = torch.rand(S, device="cuda", generator=g) * 60
+    V_out = torch.empty_like(V)
+    pi = torch.empty(S, dtype=torch.int32, device="cuda")
+    res = torch.empty(1, device="cuda")
+    assert _call(native, p, V, V_out, pi, res) == native.VC_OK  # first call: outside any capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rc = _call(native, p, V, V_out, pi, res)
+    assert rc == native.VC_OK
+    ref = torch.empty_like(V)
+    ref_pi = torch.empty_like(pi)
+    for k in range(2):
+        V.copy_(torch.rand(S, device="cuda", generator=g) * (40 + 25 * k))
+        V_out.fill_(float("nan"))
+        pi.fill_(-1)
+        res.fill_(-1.0)
+        graph.replay()
+        m.bellman32(V, ref, ref_pi)
+        torch.cuda.synchronize()
+        assert torch.equal(V_out, ref)
+        assert torch.equal(pi, ref_pi)
+        assert res.item() == (V_out - V).abs().max().item()
+    del graph
+    m.close()
